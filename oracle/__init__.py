@@ -1,0 +1,201 @@
+"""CPU oracle for exact Sauvola / Niblack binarization -- TEST INFRASTRUCTURE.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline / reference
+arm of ``bench.py`` may import this package.  The product path (the CUDA
+library and its binding) never does.  The oracle is plain C (``bnzref.c``),
+compiled with gcc at ``-O2 -ffp-contract=off`` so that every fp64 operation
+is a single IEEE-rounded step in the order the C source states:
+
+* gray conversion, Eq. 1 (Sec. 1), integer round-half-up reading
+  ``(299 r + 587 g + 114 b + 500) // 1000``;
+* clipped W x W window sums (Sec. 2), exact int64, by two independent paths:
+  naive O(W^2) per pixel and the O(W)-per-pixel sliding scheme (Sec. 3);
+* m, s and the Sauvola threshold of Eq. 4 or the Niblack threshold in fp64;
+* the decision of Eq. 3, with ties ``|f - t| < 1e-9`` counted.
+
+Pins (tests/test_oracle_*.py) tie it to things other than itself: brute force
+on tiny images, a library box filter, exact rational arithmetic, closed forms
+(constant image, step edge, impulse) and symmetry invariants.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "bnzref.c")
+_HDR = os.path.join(_HERE, "bnzref.h")
+_LIB = os.path.join(_HERE, "libbnzref.so")
+
+SAUVOLA = 0
+NIBLACK = 1
+NAIVE = 0
+SLIDING = 1
+
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile ``libbnzref.so`` next to the source (gcc, no fast-math, no FMA contraction)."""
+    stale = (not os.path.exists(_LIB)) or any(
+        os.path.getmtime(p) > os.path.getmtime(_LIB) for p in (_SRC, _HDR))
+    if force or stale:
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread",
+               "-ffp-contract=off", "-fno-fast-math", "-fexcess-precision=standard",
+               "-Wall", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        build()
+        lib = ctypes.CDLL(_LIB)
+        P = ctypes.c_void_p
+        i, ll, d = ctypes.c_int, ctypes.c_longlong, ctypes.c_double
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        lib.bnzref_gray.argtypes = [P, i, i, i, ll, P]
+        lib.bnzref_window_sums_naive.argtypes = [P, i, i, i, P, P, P]
+        lib.bnzref_window_sums_sliding.argtypes = [P, i, i, i, P, P, P]
+        lib.bnzref_threshold_value.argtypes = [ctypes.c_int64] * 3 + [i, d, d]
+        lib.bnzref_threshold_value.restype = d
+        lib.bnzref_decide.argtypes = [i, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, i, d, d,
+                                      ctypes.POINTER(i), ctypes.POINTER(d)]
+        lib.bnzref_threshold.argtypes = [P, P, P, P, i, i, i, d, d, P, i64p]
+        lib.bnzref_binarize.argtypes = [P, i, i, i, ll, i, i, d, d, i, P, ll, i64p, i]
+        lib.bnzref_pixel.argtypes = [P, i, i, i, ll, i, i, d, d, i, i, ctypes.POINTER(i),
+                                     ctypes.POINTER(d)]
+        lib.bnzref_integral.argtypes = [P, i, i, P, P]
+        lib.bnzref_pack.argtypes = [P, i, i, ll, P, ll]
+        _lib = lib
+        return lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _img(src: np.ndarray):
+    src = np.ascontiguousarray(src, dtype=np.uint8)
+    if src.ndim == 2:
+        h, w = src.shape
+        ch = 1
+    elif src.ndim == 3 and src.shape[2] == 3:
+        h, w, ch = src.shape
+    else:
+        raise ValueError("image must be HxW gray or HxWx3 RGB uint8")
+    return src, h, w, ch
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise ValueError(f"oracle call failed with status {rc}")
+
+
+def gray(src: np.ndarray) -> np.ndarray:
+    """Eq. 1 gray conversion (integer round-half-up reading)."""
+    src, h, w, ch = _img(src)
+    out = np.empty((h, w), np.uint8)
+    _check(_load().bnzref_gray(_ptr(src), h, w, ch, w * ch, _ptr(out)))
+    return out
+
+
+def window_sums(f: np.ndarray, W: int, method: int = SLIDING):
+    """Exact clipped-window (n, S1, S2) for every pixel of a gray image."""
+    f = np.ascontiguousarray(f, dtype=np.uint8)
+    h, w = f.shape
+    n = np.empty((h, w), np.int64)
+    a = np.empty((h, w), np.int64)
+    b = np.empty((h, w), np.int64)
+    fn = _load().bnzref_window_sums_naive if method == NAIVE else _load().bnzref_window_sums_sliding
+    _check(fn(_ptr(f), h, w, int(W), _ptr(n), _ptr(a), _ptr(b)))
+    return n, a, b
+
+
+def threshold_value(n: int, s1: int, s2: int, rule: int, k: float, R: float = 128.0) -> float:
+    """fp64 threshold t of Eq. 4 (Sauvola) or Niblack, fixed operation order."""
+    return _load().bnzref_threshold_value(int(n), int(s1), int(s2), int(rule), float(k), float(R))
+
+
+def decide(f: int, n: int, s1: int, s2: int, rule: int, k: float, R: float = 128.0):
+    """Eq. 3 decision for one pixel: returns (g, tie, t)."""
+    tie = ctypes.c_int(0)
+    t = ctypes.c_double(0.0)
+    g = _load().bnzref_decide(int(f), int(n), int(s1), int(s2), int(rule), float(k), float(R),
+                              ctypes.byref(tie), ctypes.byref(t))
+    return g, bool(tie.value), t.value
+
+
+def threshold(f: np.ndarray, n, s1, s2, rule: int, k: float, R: float = 128.0):
+    f = np.ascontiguousarray(f, dtype=np.uint8)
+    h, w = f.shape
+    n, s1, s2 = (np.ascontiguousarray(v, dtype=np.int64) for v in (n, s1, s2))
+    out = np.empty((h, w), np.uint8)
+    ties = ctypes.c_int64(0)
+    _check(_load().bnzref_threshold(_ptr(f), _ptr(n), _ptr(s1), _ptr(s2), h, w, int(rule),
+                                    float(k), float(R), _ptr(out), ctypes.byref(ties)))
+    return out, int(ties.value)
+
+
+def binarize(src: np.ndarray, W: int, rule: int, k: float, R: float = 128.0,
+             method: int = SLIDING, threads: int = 1, packed: bool = False):
+    """Full oracle pipeline; returns (mask, ties).  mask is {0,255} bytes or packed bits."""
+    src, h, w, ch = _img(src)
+    out = np.empty((h, w), np.uint8)
+    ties = ctypes.c_int64(0)
+    _check(_load().bnzref_binarize(_ptr(src), h, w, ch, w * ch, int(W), int(rule), float(k),
+                                   float(R), int(method), _ptr(out), w, ctypes.byref(ties),
+                                   int(threads)))
+    if packed:
+        out = pack(out)
+    return out, int(ties.value)
+
+
+def sauvola(src, W, k=0.5, R=128.0, **kw):
+    return binarize(src, W, SAUVOLA, k, R, **kw)
+
+
+def niblack(src, W, k=-0.2, **kw):
+    return binarize(src, W, NIBLACK, k, 128.0, **kw)
+
+
+def pixel(src: np.ndarray, W: int, rule: int, k: float, R: float, y: int, x: int):
+    """One output pixel by the naive definition: returns (g, tie, t)."""
+    src, h, w, ch = _img(src)
+    tie = ctypes.c_int(0)
+    t = ctypes.c_double(0.0)
+    g = _load().bnzref_pixel(_ptr(src), h, w, ch, w * ch, int(W), int(rule), float(k), float(R),
+                             int(y), int(x), ctypes.byref(tie), ctypes.byref(t))
+    if g < 0:
+        raise ValueError("bad pixel query")
+    return g, bool(tie.value), t.value
+
+
+def integral(f: np.ndarray):
+    """(h+1)x(w+1) int64 summed-area tables of f and f^2."""
+    f = np.ascontiguousarray(f, dtype=np.uint8)
+    h, w = f.shape
+    I1 = np.empty((h + 1, w + 1), np.int64)
+    I2 = np.empty((h + 1, w + 1), np.int64)
+    _check(_load().bnzref_integral(_ptr(f), h, w, _ptr(I1), _ptr(I2)))
+    return I1, I2
+
+
+def pack(mask: np.ndarray) -> np.ndarray:
+    """1 bit per pixel, LSB = leftmost pixel, bit set <=> 255."""
+    mask = np.ascontiguousarray(mask, dtype=np.uint8)
+    h, w = mask.shape
+    pb = (w + 7) // 8
+    out = np.empty((h, pb), np.uint8)
+    _check(_load().bnzref_pack(_ptr(mask), h, w, w, _ptr(out), pb))
+    return out
