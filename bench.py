@@ -1,0 +1,325 @@
+#!/usr/bin/env python3
+"""Throughput bench: exact Sauvola/Niblack binarization of a 4096x4096 RGB page.
+
+One step = the whole hot path over one page for both threshold rules
+(Sauvola k=0.5 R=128, Niblack k=-0.2) and every window W in {15, 31, 61, 101}:
+eight launches of the fused kernel, each reading the RGB page (3 B/px) and
+writing the byte mask (1 B/px).  Inputs are seeded synthetic pages with
+stains and blotches, resident in HBM; each launch reads its own copy of the
+page (8 copies, 400 MB, more than the 129 MB L2), so no launch finds its
+input in L2.
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle
+(the sliding-window scheme) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+H, W_IMG, CH, SEED = 4096, 4096, 3, 2
+RUNS = [(W, "sauvola", 0.5, 128.0) for W in (15, 31, 61, 101)] + \
+       [(W, "niblack", -0.2, 128.0) for W in (15, 31, 61, 101)]
+METRIC = "Mpixel/s and % HBM roofline per W (15–101); served pages/s at p50/p99 latency"
+WORKLOAD = "page 4096x4096 RGB (stains, blotches, sigma 8), fused RGB->gray, Sauvola k=0.5 R=128 and " \
+           "Niblack k=-0.2, W in {15,31,61,101}, byte mask"
+BYTES_PER_PX = CH + 1           # compulsory traffic: RGB input + byte mask output
+NCOPY = len(RUNS)
+
+
+def env_rank():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), \
+        int(os.environ.get("LOCAL_RANK", 0))
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def fused_source_hash():
+    h = hashlib.sha256()
+    for f in ("fused.cu", "ptx.cuh", "internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_1210_3165_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this kernel source."""
+    p = os.path.join(ROOT, "profiles", "fused_traffic.json")
+    try:
+        d = json.load(open(p))
+        if d.get("source_sha") == fused_source_hash():
+            return d.get("dram_bytes_per_launch")
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms while the timed region runs."""
+    Q = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active," \
+        "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown," \
+        "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=5)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+_PAGE = {}
+
+
+def host_page():
+    import synth
+    if "p" not in _PAGE:
+        _PAGE["p"] = synth.page(H, W_IMG, SEED, synth.STAINS, CH)
+    return _PAGE["p"]
+
+
+def cpu_oracle_sample(rows: int, threads: int):
+    """Time the oracle's sliding-window path on a rows x 4096 crop of the page, all 8 runs."""
+    import oracle
+    img = host_page()[:rows].copy()
+    t0 = time.perf_counter()
+    for W, rule, k, R in RUNS:
+        oracle.binarize(img, W, oracle.SAUVOLA if rule == "sauvola" else oracle.NIBLACK, k, R,
+                        method=oracle.SLIDING, threads=threads)
+    dt = time.perf_counter() - t0
+    return rows * W_IMG * len(RUNS) / dt / 1e6, dt
+
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return 0
+    threads = os.cpu_count() or 1
+    rows = 512
+    for _ in range(args.warmup):
+        cpu_oracle_sample(rows, threads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        cpu_oracle_sample(rows, threads)
+    dt = time.perf_counter() - t0
+    value = args.steps * rows * W_IMG * len(RUNS) / dt / 1e6
+    sample = f"{rows}x4096 RGB crop of the page per step, all 8 (rule, W) runs, oracle sliding path"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Mpixel/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / max(args.steps, 1) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic", "config": {"workload": WORKLOAD + " (CPU oracle on a crop)"},
+        "cpu_baseline": {"value": value, "unit": "Mpixel/s", "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "Mpixel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    import paper_1210_3165_gb300 as bnz
+
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    bnz.load()
+    dev = torch.device("cuda", local)
+    page = host_page()
+    srcs = []
+    for _ in range(NCOPY):
+        srcs.append(bnz.to_device_pitched(page, dev))
+    outs = [bnz.alloc_pitched(H, W_IMG, dev) for _ in range(NCOPY)]
+    stream = torch.cuda.Stream(device=dev)
+    rule_id = {"sauvola": bnz.BNZ_SAUVOLA, "niblack": bnz.BNZ_NIBLACK}
+
+    def step(evs=None):
+        for j, (W, rule, k, R) in enumerate(RUNS):
+            if evs is not None:
+                evs[j].record(stream)
+            bnz.bnz_binarize_dev(srcs[j], W, rule_id[rule], k, R, outs[j], stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    stream.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+
+    # timed region: K steps, an event before every launch and one at the end
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(RUNS))] for _ in range(args.steps)]
+    end = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    with torch.cuda.stream(stream):
+        for s in range(args.steps):
+            step(evs[s])
+        end.record(stream)
+    stream.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    total_ms = evs[0][0].elapsed_time(end)
+    per_launch = {j: [] for j in range(len(RUNS))}
+    for s in range(args.steps):
+        for j in range(len(RUNS)):
+            nxt = evs[s][j + 1] if j + 1 < len(RUNS) else (evs[s + 1][0] if s + 1 < args.steps else end)
+            per_launch[j].append(evs[s][j].elapsed_time(nxt))
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+
+    px_step = H * W_IMG * len(RUNS)
+    value = world * args.steps * px_step / (total_ms / 1e3) / 1e6
+    peak, peak_kind = measured_peak()
+    bytes_launch = H * W_IMG * BYTES_PER_PX
+    avg_launch_ms = statistics.mean(sum(v) / len(v) for v in per_launch.values())
+    achieved = bytes_launch / (avg_launch_ms / 1e3) / 1e9
+    per_w = {}
+    for j, (W, rule, k, R) in enumerate(RUNS):
+        ms = sorted(per_launch[j])[len(per_launch[j]) // 2]
+        gbs = bytes_launch / (ms / 1e3) / 1e9
+        per_w[f"{rule}_W{W}"] = {"us": round(ms * 1e3, 2), "Mpixel/s": round(H * W_IMG / (ms / 1e3) / 1e6, 1),
+                                 "GB/s": round(gbs, 1), "frac": round(gbs / peak, 4)}
+
+    result = {
+        "metric": METRIC, "value": value, "unit": "Mpixel/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "h": H, "w": W_IMG, "channels": CH, "runs_per_step": len(RUNS),
+                   "l2": "each launch reads its own input copy (8 copies, 400 MB > 129 MB L2)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": ncu_traffic(),
+                     "kernel": "fused_kernel", "algorithmic_bytes_per_launch": bytes_launch,
+                     "peak_kind": peak_kind},
+        "per_W": per_w,
+        "gpu_launches": args.steps * len(RUNS),
+        "clocks": clk,
+    }
+
+    if rank == 0 and not args.no_e2e:
+        result["e2e"] = e2e_host_api(bnz, page, min(args.steps, 3))
+    if rank == 0 and world == 1 and not args.no_cpu:
+        threads = os.cpu_count() or 1
+        v, dt = cpu_oracle_sample(1024, threads)
+        result["cpu_baseline"] = {"value": v, "unit": "Mpixel/s", "cores": threads, "kind": "oracle",
+                                  "sample": f"1024x4096 crop of the page, all 8 runs, {dt:.1f} s wall"}
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(result))
+    return 0
+
+
+def e2e_host_api(bnz, page, steps):
+    """Same metric through the host-pointer C ABI: pinned host page in, host mask out, copies timed."""
+    import numpy as np
+    import torch
+    src = torch.empty(page.shape, dtype=torch.uint8, pin_memory=True)
+    src.numpy()[...] = page
+    dst = torch.empty((H, W_IMG), dtype=torch.uint8, pin_memory=True)
+    lib = bnz.load()
+    sp, dp = src.numpy(), dst.numpy()
+
+    def one():
+        for W, rule, k, R in RUNS:
+            if rule == "sauvola":
+                rc = lib.bnz_sauvola(sp.ctypes.data, H, W_IMG, CH, W, k, R, dp.ctypes.data)
+            else:
+                rc = lib.bnz_niblack(sp.ctypes.data, H, W_IMG, CH, W, k, dp.ctypes.data)
+            if rc != 0:
+                raise RuntimeError(bnz.bnz_last_error())
+    one()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        one()
+    dt = time.perf_counter() - t0
+    return {"value": steps * H * W_IMG * len(RUNS) / dt / 1e6, "unit": "Mpixel/s",
+            "h2d_bytes_per_step": H * W_IMG * CH * len(RUNS), "d2h_bytes_per_step": H * W_IMG * len(RUNS),
+            "api": "bnz_sauvola / bnz_niblack (host pointers, pinned)", "steps": steps}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

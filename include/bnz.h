@@ -1,0 +1,141 @@
+/*
+ * bnz.h -- C ABI of the GB300 (sm_103a) locally adaptive binarization library.
+ *
+ * The library computes, for every pixel (x, y) of a uint8 page, the exact
+ * integer sums S1 = sum f and S2 = sum f^2 over the W x W window around the
+ * pixel (Sec. 2 of the paper: the window set S, "the most time consuming
+ * operation"), the local mean m = S1/n and standard deviation
+ * s = sqrt(n*S2 - S1^2)/n, the threshold t, and the binary value of Eq. 3:
+ *     g(x, y) = 0 if f(x, y) < t(x, y), else 255.
+ * Threshold rules:
+ *     Sauvola, Eq. 4:  t = m * (1 + k * (s / R - 1))
+ *     Niblack (cited in Sec. 1; formula not printed there): t = m + k * s
+ * Colour input is converted with Eq. 1 (f = 0.299 r + 0.587 g + 0.114 b)
+ * using the integer round-half-up rule f = (299 r + 587 g + 114 b + 500) / 1000.
+ *
+ * Conventions shared by every entry point:
+ *   - Images are row-major.  `channels` is 1 (gray) or 3 (interleaved r,g,b).
+ *     `height` = number of rows (M in the paper), `width` = columns (N).
+ *   - W >= 1 is the full window side.  Odd W is centred; even W spans W/2
+ *     pixels before the centre and W/2 - 1 after it (rows and columns).
+ *     W <= BNZ_MAX_W.
+ *   - Borders: the window is clipped to the image and n counts the pixels
+ *     actually inside (no padding, no reflection).
+ *   - m, s and t are decided exactly as an IEEE fp64 evaluation in the order
+ *     m = S1/n, s = sqrt(V)/n, then the rule's formula left to right, would
+ *     decide them.  The kernels filter with fp32 and a proven error margin and
+ *     re-evaluate that fp64 sequence for the few pixels inside the margin, so
+ *     every output byte equals that fp64 decision.
+ *   - Output: a byte mask with values {0, 255} (dst_pitch >= width), or, with
+ *     packed = 1, one bit per pixel: byte x/8 of a row holds pixel x in bit
+ *     x%8 (LSB = leftmost), bit set <=> 255, unused trailing bits are 0
+ *     (dst_pitch >= (width + 7) / 8).
+ *   - Ownership: the caller owns every buffer.  The library keeps no pointer
+ *     after a synchronous call returns, or after the stream passes an
+ *     asynchronous call.
+ *   - Errors: every call returns a bnz_status and never aborts the process.
+ *     bnz_last_error() returns a message for the calling thread's last
+ *     failure.  There is no CPU fallback: without a CUDA device the calls
+ *     return BNZ_ENODEV.
+ *   - Statistics (optional, `d_stats`): device pointer to 4 unsigned 64-bit
+ *     counters that the kernels add to (the caller zeroes them):
+ *       [0] pixels re-evaluated in fp64 (inside the fp32 margin),
+ *       [1] ties: pixels with |f - t| < 1e-9,
+ *       [2] bounded waits that timed out (a CTA that gives up writes no output
+ *           and the call reports BNZ_ETIMEOUT on the next synchronous call),
+ *       [3] reserved, 0.
+ */
+#ifndef BNZ_H
+#define BNZ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define BNZ_API __attribute__((visibility("default")))
+#else
+#define BNZ_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BNZ_OK = 0,
+    BNZ_EINVAL = 1,   /* bad argument (message in bnz_last_error) */
+    BNZ_ENOMEM = 2,   /* device allocation failed or budget exhausted */
+    BNZ_ECUDA = 3,    /* a CUDA runtime/driver call failed */
+    BNZ_ETIMEOUT = 4, /* a bounded device-side wait gave up */
+    BNZ_ENODEV = 5    /* no usable CUDA device */
+} bnz_status;
+
+typedef enum { BNZ_SAUVOLA = 0, BNZ_NIBLACK = 1 } bnz_rule;
+
+#define BNZ_MAX_W 255
+#define BNZ_STATS_FALLBACKS 0
+#define BNZ_STATS_TIES 1
+#define BNZ_STATS_TIMEOUTS 2
+
+/* Optional tile shape for the fused kernel (autotuner hook).  Zero fields
+ * mean "library default".  tile_w: output columns per strip, 256 or 512.
+ * tile_h: approximate rows of work per CTA (sets the grid size).
+ * chunk: rows per TMA load, 8 or 16. */
+typedef struct {
+    int tile_w;
+    int tile_h;
+    int chunk;
+    int reserved;
+} bnz_tile;
+
+/* ---- synchronous host-pointer API (Eq. 3 with Eq. 4 / Niblack) ---------- */
+
+/* src: height rows of width*channels bytes, tightly packed, host memory.
+ * dst: height*width bytes, {0,255}, host memory.  Blocks until done.
+ * k: any finite value; R > 0 (the paper's "dynamic range of standard
+ * deviation", Sec. 1 after Eq. 4). */
+BNZ_API int bnz_sauvola(const uint8_t *src, int height, int width, int channels, int W, double k, double R,
+                uint8_t *dst);
+
+/* Niblack rule t = m + k*s (k may be negative, e.g. -0.2). */
+BNZ_API int bnz_niblack(const uint8_t *src, int height, int width, int channels, int W, double k, uint8_t *dst);
+
+/* ---- asynchronous device-pointer API -------------------------------------
+ * d_src: device pointer, 16-byte aligned, rows src_pitch bytes apart,
+ *   src_pitch a multiple of 16 and >= width*channels (TMA requirement).
+ * d_dst: device pointer, rows dst_pitch bytes apart (>= width, or
+ *   >= (width+7)/8 when packed).
+ * stream: a cudaStream_t (NULL = legacy default stream).
+ * d_stats: nullable device pointer to 4 uint64 counters (see above).
+ * Returns after enqueueing; argument errors are reported immediately. */
+BNZ_API int bnz_sauvola_dev(const uint8_t *d_src, size_t src_pitch, int height, int width, int channels, int W,
+                    double k, double R, uint8_t *d_dst, size_t dst_pitch, int packed, void *stream,
+                    unsigned long long *d_stats);
+
+BNZ_API int bnz_niblack_dev(const uint8_t *d_src, size_t src_pitch, int height, int width, int channels, int W,
+                    double k, uint8_t *d_dst, size_t dst_pitch, int packed, void *stream,
+                    unsigned long long *d_stats);
+
+/* Generic form of the two calls above with an explicit rule and optional
+ * tile shape (tile may be NULL).  R is ignored for BNZ_NIBLACK. */
+BNZ_API int bnz_binarize_dev(const uint8_t *d_src, size_t src_pitch, int height, int width, int channels, int W,
+                     int rule, double k, double R, uint8_t *d_dst, size_t dst_pitch, int packed,
+                     const bnz_tile *tile, void *stream, unsigned long long *d_stats);
+
+/* ---- library state ------------------------------------------------------ */
+
+/* Message for the calling thread's most recent failure ("" if none). */
+BNZ_API const char *bnz_last_error(void);
+
+/* Library ABI version (major*10000 + minor*100 + patch). */
+BNZ_API int bnz_version(void);
+
+/* Shared memory bytes and grid size the fused kernel would use for this
+ * problem (no launch; for planning and autotuning).  Returns BNZ_OK. */
+BNZ_API int bnz_fused_plan(int height, int width, int channels, int W, const bnz_tile *tile, size_t *smem_bytes,
+                   int *grid_ctas, int *tile_w, int *tile_h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BNZ_H */

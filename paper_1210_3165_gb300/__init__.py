@@ -1,0 +1,232 @@
+"""Python binding of the GB300 locally adaptive binarization library (``libbnz.so``).
+
+Thin ctypes layer with the same names as the C ABI in ``include/bnz.h``.  It
+only marshals arguments: every pixel is computed by the library's CUDA
+kernels.  PyTorch supplies device memory and streams.  There is no CPU path:
+if the compiled library is missing, importing the binding raises, and on a
+machine without a GPU the calls return ``BNZ_ENODEV``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+BNZ_OK, BNZ_EINVAL, BNZ_ENOMEM, BNZ_ECUDA, BNZ_ETIMEOUT, BNZ_ENODEV = range(6)
+BNZ_SAUVOLA, BNZ_NIBLACK = 0, 1
+BNZ_MAX_W = 255
+STATUS_NAMES = {0: "BNZ_OK", 1: "BNZ_EINVAL", 2: "BNZ_ENOMEM", 3: "BNZ_ECUDA", 4: "BNZ_ETIMEOUT",
+                5: "BNZ_ENODEV"}
+
+LIB_PATH = _build.LIB
+
+
+class BnzError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class bnz_tile(ctypes.Structure):
+    _fields_ = [("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int), ("chunk", ctypes.c_int),
+                ("reserved", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load ``libbnz.so`` (building it first if it is absent); raise if it cannot be loaded."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        if not build_if_missing:
+            raise RuntimeError(f"{LIB_PATH} is missing: run paper_1210_3165_gb300._build.build()")
+        _build.build()
+    lib = ctypes.CDLL(LIB_PATH)
+    P, i, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    lib.bnz_sauvola.argtypes = [P, i, i, i, i, d, d, P]
+    lib.bnz_niblack.argtypes = [P, i, i, i, i, d, P]
+    lib.bnz_sauvola_dev.argtypes = [P, sz, i, i, i, i, d, d, P, sz, i, P, P]
+    lib.bnz_niblack_dev.argtypes = [P, sz, i, i, i, i, d, P, sz, i, P, P]
+    lib.bnz_binarize_dev.argtypes = [P, sz, i, i, i, i, i, d, d, P, sz, i, P, P, P]
+    lib.bnz_last_error.restype = ctypes.c_char_p
+    lib.bnz_last_error.argtypes = []
+    lib.bnz_version.argtypes = []
+    lib.bnz_fused_plan.argtypes = [i, i, i, i, P, ctypes.POINTER(sz), ctypes.POINTER(i), ctypes.POINTER(i),
+                                   ctypes.POINTER(i)]
+    for name in ("bnz_sauvola", "bnz_niblack", "bnz_sauvola_dev", "bnz_niblack_dev", "bnz_binarize_dev",
+                 "bnz_version", "bnz_fused_plan"):
+        getattr(lib, name).restype = ctypes.c_int
+    _optional_symbols(lib)
+    _lib = lib
+    return lib
+
+
+def _optional_symbols(lib):
+    """Entry points added by later parts of the library (integral images, batches)."""
+    P, i, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    table = {
+        "bnz_integral_scratch_bytes": ([i, i], ctypes.c_size_t),
+        "bnz_binarize_integral_dev": ([P, sz, i, i, i, i, i, d, d, P, sz, i, P, sz, P, P], ctypes.c_int),
+        "bnz_window_sums_dev": ([P, sz, i, i, i, i, P, P, P, P], ctypes.c_int),
+    }
+    for name, (args, res) in table.items():
+        if hasattr(lib, name):
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+
+
+def bnz_last_error() -> str:
+    return load().bnz_last_error().decode(errors="replace")
+
+
+def bnz_version() -> int:
+    return load().bnz_version()
+
+
+def _check(rc: int):
+    if rc != BNZ_OK:
+        raise BnzError(rc, bnz_last_error())
+
+
+# ---------------------------------------------------------------------------
+# host-pointer calls (numpy in, numpy out)
+# ---------------------------------------------------------------------------
+
+def _host_img(src):
+    src = np.ascontiguousarray(src, dtype=np.uint8)
+    if src.ndim == 2:
+        return src, src.shape[0], src.shape[1], 1
+    if src.ndim == 3 and src.shape[2] == 3:
+        return src, src.shape[0], src.shape[1], 3
+    raise ValueError("image must be HxW or HxWx3 uint8")
+
+
+def bnz_sauvola(src, W: int, k: float = 0.5, R: float = 128.0) -> np.ndarray:
+    """Synchronous Sauvola binarization of a host image; returns the {0,255} mask."""
+    src, h, w, ch = _host_img(src)
+    dst = np.empty((h, w), np.uint8)
+    _check(load().bnz_sauvola(src.ctypes.data, h, w, ch, int(W), float(k), float(R), dst.ctypes.data))
+    return dst
+
+
+def bnz_niblack(src, W: int, k: float = -0.2) -> np.ndarray:
+    src, h, w, ch = _host_img(src)
+    dst = np.empty((h, w), np.uint8)
+    _check(load().bnz_niblack(src.ctypes.data, h, w, ch, int(W), float(k), dst.ctypes.data))
+    return dst
+
+
+# ---------------------------------------------------------------------------
+# device-pointer calls (torch CUDA tensors)
+# ---------------------------------------------------------------------------
+
+def alloc_pitched(height: int, row_bytes: int, device="cuda", align: int = 16):
+    """uint8 CUDA tensor view of shape (height, row_bytes) whose row stride is a multiple of ``align``."""
+    import torch
+    pitch = (row_bytes + align - 1) // align * align
+    base = torch.empty((max(height, 1), pitch), dtype=torch.uint8, device=device)
+    return base[:height, :row_bytes]
+
+
+def _dev_img(t):
+    """(ptr, pitch, h, w, ch) of a uint8 CUDA tensor laid out HxW or HxWx3 with unit inner strides."""
+    import torch
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.uint8 or not t.is_cuda:
+        raise TypeError("expected a uint8 CUDA tensor")
+    if t.dim() == 2:
+        if t.stride(1) != 1:
+            raise ValueError("inner stride must be 1")
+        return t.data_ptr(), t.stride(0), t.shape[0], t.shape[1], 1
+    if t.dim() == 3 and t.shape[2] == 3:
+        if t.stride(2) != 1 or t.stride(1) != 3:
+            raise ValueError("RGB tensor must be interleaved (strides (pitch, 3, 1))")
+        return t.data_ptr(), t.stride(0), t.shape[0], t.shape[1], 3
+    raise ValueError("image must be HxW or HxWx3")
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _out_pitch(dst, w, packed):
+    if dst.dim() != 2 or dst.stride(1) != 1 or dst.dtype.itemsize != 1:
+        raise ValueError("dst must be a 2-D uint8 tensor with unit inner stride")
+    need = (w + 7) // 8 if packed else w
+    if dst.shape[1] < need:
+        raise ValueError(f"dst rows must hold {need} bytes")
+    return dst.stride(0)
+
+
+def bnz_binarize_dev(d_src, W: int, rule: int, k: float, R: float, d_dst, packed: bool = False,
+                     tile: bnz_tile | None = None, stream=None, d_stats=None) -> None:
+    """Enqueue one binarization on ``stream`` (default: torch's current stream)."""
+    ptr, pitch, h, w, ch = _dev_img(d_src)
+    dp = _out_pitch(d_dst, w, packed)
+    _check(load().bnz_binarize_dev(ptr, pitch, h, w, ch, int(W), int(rule), float(k), float(R),
+                                   d_dst.data_ptr(), dp, 1 if packed else 0,
+                                   ctypes.byref(tile) if tile is not None else None,
+                                   _stream_ptr(stream), d_stats.data_ptr() if d_stats is not None else None))
+
+
+def bnz_sauvola_dev(d_src, W: int, k: float, R: float, d_dst, packed: bool = False, stream=None,
+                    d_stats=None) -> None:
+    ptr, pitch, h, w, ch = _dev_img(d_src)
+    dp = _out_pitch(d_dst, w, packed)
+    _check(load().bnz_sauvola_dev(ptr, pitch, h, w, ch, int(W), float(k), float(R), d_dst.data_ptr(), dp,
+                                  1 if packed else 0, _stream_ptr(stream),
+                                  d_stats.data_ptr() if d_stats is not None else None))
+
+
+def bnz_niblack_dev(d_src, W: int, k: float, d_dst, packed: bool = False, stream=None, d_stats=None) -> None:
+    ptr, pitch, h, w, ch = _dev_img(d_src)
+    dp = _out_pitch(d_dst, w, packed)
+    _check(load().bnz_niblack_dev(ptr, pitch, h, w, ch, int(W), float(k), d_dst.data_ptr(), dp,
+                                  1 if packed else 0, _stream_ptr(stream),
+                                  d_stats.data_ptr() if d_stats is not None else None))
+
+
+def bnz_fused_plan(h: int, w: int, ch: int, W: int, tile: bnz_tile | None = None) -> dict:
+    smem = ctypes.c_size_t(0)
+    grid, tw, th = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    _check(load().bnz_fused_plan(h, w, ch, W, ctypes.byref(tile) if tile is not None else None,
+                                 ctypes.byref(smem), ctypes.byref(grid), ctypes.byref(tw), ctypes.byref(th)))
+    return dict(smem=smem.value, grid=grid.value, tile_w=tw.value, rows_per_cta=th.value)
+
+
+# ---------------------------------------------------------------------------
+# convenience wrapper used by tests, bench and the server
+# ---------------------------------------------------------------------------
+
+def to_device_pitched(img: np.ndarray, device="cuda"):
+    """Copy a host HxW / HxWx3 uint8 image into a 16-byte-pitched CUDA tensor view."""
+    import torch
+    img = np.ascontiguousarray(img, dtype=np.uint8)
+    h, w = img.shape[:2]
+    ch = 1 if img.ndim == 2 else 3
+    t = alloc_pitched(h, w * ch, device)
+    t.copy_(torch.from_numpy(img.reshape(h, w * ch)))
+    return t if ch == 1 else t.unflatten(1, (w, 3))
+
+
+def binarize(d_src, W: int, rule: str | int = "sauvola", k: float | None = None, R: float = 128.0,
+             packed: bool = False, out=None, tile: bnz_tile | None = None, stream=None, d_stats=None):
+    """Binarize a pitched uint8 CUDA image; returns the (pitched) output tensor view."""
+    if isinstance(rule, str):
+        rule = {"sauvola": BNZ_SAUVOLA, "niblack": BNZ_NIBLACK}[rule.lower()]
+    if k is None:
+        k = 0.5 if rule == BNZ_SAUVOLA else -0.2
+    _, _, h, w, _ = _dev_img(d_src)
+    if out is None:
+        out = alloc_pitched(h, (w + 7) // 8 if packed else w, d_src.device)
+    bnz_binarize_dev(d_src, W, rule, k, R, out, packed, tile, stream, d_stats)
+    return out

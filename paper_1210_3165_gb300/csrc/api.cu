@@ -1,0 +1,311 @@
+// api.cu -- the C ABI declared in include/bnz.h: argument checks, error
+// messages, TMA descriptor encoding, device bookkeeping and the synchronous
+// host-pointer calls.  All pixel work happens in the CUDA kernels.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "internal.h"
+
+namespace bnz {
+
+static thread_local std::string t_err;
+
+int fail(int rc, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    t_err = buf;
+    return rc;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    const int rc = (e == cudaErrorMemoryAllocation) ? BNZ_ENOMEM
+                   : (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver) ? BNZ_ENODEV
+                                                                                   : BNZ_ECUDA;
+    return fail(rc, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static std::mutex g_mu;
+static EncodeTiledFn g_encode = nullptr;
+static const int kMaxDev = 64;
+static int g_sms[kMaxDev];
+static unsigned int *g_err[kMaxDev];
+
+int encode_u8_map(CUtensorMap *map, const void *base, uint64_t inner_bytes, uint64_t rows, uint64_t pitch,
+                  uint32_t box_inner, uint32_t box_rows)
+{
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (!g_encode) {
+            void *fn = nullptr;
+            cudaDriverEntryPointQueryResult q;
+            cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                             cudaEnableDefault, &q);
+            if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+                return fail(BNZ_ECUDA, "cuTensorMapEncodeTiled entry point unavailable");
+            g_encode = reinterpret_cast<EncodeTiledFn>(fn);
+        }
+    }
+    cuuint64_t dims[2] = {(cuuint64_t)inner_bytes, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)pitch};
+    cuuint32_t box[2] = {box_inner, box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void *>(base), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+        return fail(BNZ_EINVAL, "cuTensorMapEncodeTiled failed (%d): base=%p inner=%llu rows=%llu pitch=%llu",
+                    (int)r, base, (unsigned long long)inner_bytes, (unsigned long long)rows,
+                    (unsigned long long)pitch);
+    return BNZ_OK;
+}
+
+static int current_device(int *dev)
+{
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess || n < 1) {
+        cudaGetLastError();
+        return fail(BNZ_ENODEV, "no CUDA device available (%s); this library has no CPU path",
+                    e == cudaSuccess ? "device count 0" : cudaGetErrorName(e));
+    }
+    e = cudaGetDevice(dev);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaGetDevice");
+    if (*dev < 0 || *dev >= kMaxDev)
+        return fail(BNZ_ENODEV, "device ordinal %d out of range", *dev);
+    return BNZ_OK;
+}
+
+int device_sm_count(int *sms)
+{
+    int dev = 0;
+    int rc = current_device(&dev);
+    if (rc != BNZ_OK)
+        return rc;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_sms[dev]) {
+        int v = 0;
+        cudaError_t e = cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "cudaDeviceGetAttribute(SM count)");
+        g_sms[dev] = v;
+    }
+    *sms = g_sms[dev];
+    return BNZ_OK;
+}
+
+int device_err_flag(unsigned int **flag)
+{
+    int dev = 0;
+    int rc = current_device(&dev);
+    if (rc != BNZ_OK)
+        return rc;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_err[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaMalloc(&p, 256);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "cudaMalloc(error word)");
+        e = cudaMemset(p, 0, 256);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "cudaMemset(error word)");
+        g_err[dev] = static_cast<unsigned int *>(p);
+    }
+    *flag = g_err[dev];
+    return BNZ_OK;
+}
+
+static int check_common(const void *src, size_t src_pitch, int height, int width, int channels, int W, int rule,
+                        double k, double R, const void *dst, size_t dst_pitch, int packed)
+{
+    if (!src || !dst)
+        return fail(BNZ_EINVAL, "null image pointer");
+    if (height < 1 || width < 1)
+        return fail(BNZ_EINVAL, "height and width must be >= 1 (got %d x %d)", height, width);
+    if (channels != 1 && channels != 3)
+        return fail(BNZ_EINVAL, "channels must be 1 or 3 (got %d)", channels);
+    if (W < 1 || W > BNZ_MAX_W)
+        return fail(BNZ_EINVAL, "window size W must be in [1, %d] (got %d)", BNZ_MAX_W, W);
+    if (rule != BNZ_SAUVOLA && rule != BNZ_NIBLACK)
+        return fail(BNZ_EINVAL, "unknown rule %d", rule);
+    if (!std::isfinite(k))
+        return fail(BNZ_EINVAL, "k must be finite");
+    if (rule == BNZ_SAUVOLA && !(R > 0.0 && std::isfinite(R)))
+        return fail(BNZ_EINVAL, "R must be finite and > 0 for Sauvola (got %g)", R);
+    if (src_pitch < (size_t)width * channels)
+        return fail(BNZ_EINVAL, "src_pitch %zu < width*channels %zu", src_pitch, (size_t)width * channels);
+    const size_t row_out = packed ? ((size_t)width + 7) / 8 : (size_t)width;
+    if (dst_pitch < row_out)
+        return fail(BNZ_EINVAL, "dst_pitch %zu < %zu bytes per output row", dst_pitch, row_out);
+    if ((size_t)width * channels > ((size_t)1 << 31) || (size_t)height > ((size_t)1 << 31))
+        return fail(BNZ_EINVAL, "image too large");
+    return BNZ_OK;
+}
+
+static int binarize_dev(const uint8_t *d_src, size_t src_pitch, int height, int width, int channels, int W,
+                        int rule, double k, double R, uint8_t *d_dst, size_t dst_pitch, int packed,
+                        const bnz_tile *tile, void *stream, unsigned long long *d_stats)
+{
+    int rc = check_common(d_src, src_pitch, height, width, channels, W, rule, k, R, d_dst, dst_pitch, packed);
+    if (rc != BNZ_OK)
+        return rc;
+    if ((reinterpret_cast<uintptr_t>(d_src) & 15u) || (src_pitch & 15u))
+        return fail(BNZ_EINVAL, "d_src must be 16-byte aligned with src_pitch a multiple of 16 (TMA)");
+    if (rule == BNZ_NIBLACK)
+        R = 1.0;
+    unsigned int *err = nullptr;
+    rc = device_err_flag(&err);
+    if (rc != BNZ_OK)
+        return rc;
+    return launch_fused(d_src, src_pitch, height, width, channels, W, rule, k, R, d_dst, dst_pitch, packed ? 1 : 0,
+                        tile, static_cast<cudaStream_t>(stream), d_stats, err);
+}
+
+// Synchronous host-pointer path: stream-ordered device buffers, copies in and
+// out, one launch, then a check of the device error word.
+static int binarize_host(const uint8_t *src, int height, int width, int channels, int W, int rule, double k,
+                         double R, uint8_t *dst)
+{
+    int rc = check_common(src, (size_t)width * channels, height, width, channels, W, rule, k, R, dst,
+                          (size_t)width, 0);
+    if (rc != BNZ_OK)
+        return rc;
+    int dev = 0;
+    rc = current_device(&dev);
+    if (rc != BNZ_OK)
+        return rc;
+    unsigned int *err = nullptr;
+    rc = device_err_flag(&err);
+    if (rc != BNZ_OK)
+        return rc;
+    cudaStream_t s = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaStreamCreate");
+    const size_t sp = ((size_t)width * channels + 15) & ~size_t(15);
+    const size_t dp = ((size_t)width + 15) & ~size_t(15);
+    void *d_src = nullptr, *d_dst = nullptr;
+    unsigned int before = 0, after = 0;
+    rc = BNZ_OK;
+    do {
+        if ((e = cudaMemcpyAsync(&before, err, sizeof before, cudaMemcpyDeviceToHost, s)) != cudaSuccess) {
+            rc = cuda_fail(e, "read error word");
+            break;
+        }
+        if ((e = cudaMallocAsync(&d_src, sp * height, s)) != cudaSuccess) {
+            rc = cuda_fail(e, "cudaMallocAsync(src)");
+            break;
+        }
+        if ((e = cudaMallocAsync(&d_dst, dp * height, s)) != cudaSuccess) {
+            rc = cuda_fail(e, "cudaMallocAsync(dst)");
+            break;
+        }
+        if ((e = cudaMemcpy2DAsync(d_src, sp, src, (size_t)width * channels, (size_t)width * channels, height,
+                                   cudaMemcpyHostToDevice, s)) != cudaSuccess) {
+            rc = cuda_fail(e, "copy input to device");
+            break;
+        }
+        rc = binarize_dev(static_cast<const uint8_t *>(d_src), sp, height, width, channels, W, rule, k, R,
+                          static_cast<uint8_t *>(d_dst), dp, 0, nullptr, s, nullptr);
+        if (rc != BNZ_OK)
+            break;
+        if ((e = cudaMemcpy2DAsync(dst, (size_t)width, d_dst, dp, (size_t)width, height, cudaMemcpyDeviceToHost,
+                                   s)) != cudaSuccess) {
+            rc = cuda_fail(e, "copy result to host");
+            break;
+        }
+        if ((e = cudaMemcpyAsync(&after, err, sizeof after, cudaMemcpyDeviceToHost, s)) != cudaSuccess) {
+            rc = cuda_fail(e, "read error word");
+            break;
+        }
+    } while (0);
+    if (d_src)
+        cudaFreeAsync(d_src, s);
+    if (d_dst)
+        cudaFreeAsync(d_dst, s);
+    e = cudaStreamSynchronize(s);
+    if (rc == BNZ_OK && e != cudaSuccess)
+        rc = cuda_fail(e, "cudaStreamSynchronize");
+    cudaStreamDestroy(s);
+    if (rc == BNZ_OK && after != before)
+        rc = fail(BNZ_ETIMEOUT, "a device-side wait timed out; output incomplete");
+    return rc;
+}
+
+} // namespace bnz
+
+using namespace bnz;
+
+extern "C" {
+
+int bnz_sauvola(const uint8_t *src, int height, int width, int channels, int W, double k, double R, uint8_t *dst)
+{
+    return binarize_host(src, height, width, channels, W, BNZ_SAUVOLA, k, R, dst);
+}
+
+int bnz_niblack(const uint8_t *src, int height, int width, int channels, int W, double k, uint8_t *dst)
+{
+    return binarize_host(src, height, width, channels, W, BNZ_NIBLACK, k, 1.0, dst);
+}
+
+int bnz_sauvola_dev(const uint8_t *d_src, size_t src_pitch, int height, int width, int channels, int W, double k,
+                    double R, uint8_t *d_dst, size_t dst_pitch, int packed, void *stream,
+                    unsigned long long *d_stats)
+{
+    return binarize_dev(d_src, src_pitch, height, width, channels, W, BNZ_SAUVOLA, k, R, d_dst, dst_pitch, packed,
+                        nullptr, stream, d_stats);
+}
+
+int bnz_niblack_dev(const uint8_t *d_src, size_t src_pitch, int height, int width, int channels, int W, double k,
+                    uint8_t *d_dst, size_t dst_pitch, int packed, void *stream, unsigned long long *d_stats)
+{
+    return binarize_dev(d_src, src_pitch, height, width, channels, W, BNZ_NIBLACK, k, 1.0, d_dst, dst_pitch,
+                        packed, nullptr, stream, d_stats);
+}
+
+int bnz_binarize_dev(const uint8_t *d_src, size_t src_pitch, int height, int width, int channels, int W, int rule,
+                     double k, double R, uint8_t *d_dst, size_t dst_pitch, int packed, const bnz_tile *tile,
+                     void *stream, unsigned long long *d_stats)
+{
+    return binarize_dev(d_src, src_pitch, height, width, channels, W, rule, k, R, d_dst, dst_pitch, packed, tile,
+                        stream, d_stats);
+}
+
+const char *bnz_last_error(void) { return t_err.c_str(); }
+
+int bnz_version(void) { return 100; }
+
+int bnz_fused_plan(int height, int width, int channels, int W, const bnz_tile *tile, size_t *smem_bytes,
+                   int *grid_ctas, int *tile_w, int *tile_h)
+{
+    if (height < 1 || width < 1 || (channels != 1 && channels != 3) || W < 1 || W > BNZ_MAX_W)
+        return fail(BNZ_EINVAL, "bad plan arguments");
+    FusedPlan pl;
+    int rc = plan_fused(height, width, channels, W, tile, &pl);
+    if (rc != BNZ_OK)
+        return rc;
+    if (smem_bytes)
+        *smem_bytes = pl.smem;
+    if (grid_ctas)
+        *grid_ctas = pl.tiles_y;
+    if (tile_w)
+        *tile_w = pl.TW;
+    if (tile_h)
+        *tile_h = pl.TH;
+    return BNZ_OK;
+}
+
+} // extern "C"

@@ -1,0 +1,68 @@
+// internal.h -- declarations shared by the library's translation units
+// (kernel launch parameters, tile plans, error reporting).  Not installed.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "../../include/bnz.h"
+
+namespace bnz {
+
+// Sets the calling thread's last-error message (printf-style) and returns rc.
+int fail(int rc, const char *fmt, ...);
+// Maps a CUDA runtime error to BNZ_ECUDA with a message naming `what`.
+int cuda_fail(cudaError_t e, const char *what);
+
+// Encodes a 2-D uint8 tensor map through the driver entry point.
+int encode_u8_map(CUtensorMap *map, const void *base, uint64_t inner_bytes, uint64_t rows, uint64_t pitch,
+                  uint32_t box_inner, uint32_t box_rows);
+
+int device_sm_count(int *sms);
+
+// ---- fused tile kernel -----------------------------------------------------
+
+// Shape of one launch of the fused kernel (host-side plan).
+struct FusedPlan {
+    int L;          // outputs per lane per row (tile_w = 32 * L)
+    int TW, TH, CH; // tile width/height, rows per TMA chunk
+    int NS;         // ring slots (chunks) of gray rows in shared memory
+    int NSS;        // staging slots for RGB chunks (0 for gray)
+    int PWP;        // panel width in pixels (one TMA box per panel per chunk)
+    int NPAN, SWP;  // panels per span, span width in pixels
+    int RS;         // row stride of the column-sum buffer (uint2 units, odd)
+    int ring_rows;  // NS * CH
+    int o;          // span start offset: (x0 - r_lo) - floor16(x0 - r_lo)
+    int tiles_x, tiles_y;
+    uint32_t off_ring, off_stage, off_cb;
+    size_t smem;
+};
+
+struct FusedParams {
+    uint8_t *dst;
+    long long dst_pitch;
+    unsigned long long *stats;
+    unsigned int *err_flag; // library-owned device word, counts CTAs that gave up
+    int h, w, W, r_lo, r_hi, o;
+    int TW, TH, CH, NS, NSS, NPAN, SWP, RS, ring_rows, tiles_x;
+    uint32_t off_ring, off_stage, off_cb;
+    double k, R;
+    float kf, invRf, E, invn;
+    int vec_ok; // dst and dst_pitch 16-byte aligned
+    long long timeout_cycles;
+};
+
+int plan_fused(int h, int w, int ch, int W, const bnz_tile *tile, FusedPlan *plan);
+int launch_fused(const uint8_t *d_src, size_t src_pitch, int h, int w, int ch, int W, int rule, double k,
+                 double R, uint8_t *d_dst, size_t dst_pitch, int packed, const bnz_tile *tile,
+                 cudaStream_t stream, unsigned long long *d_stats, unsigned int *d_err);
+
+// Library-owned per-device error word (allocated on first use).
+int device_err_flag(unsigned int **flag);
+
+// fp32 decision margin: an upper bound (with a factor-2 safety) on
+// |t32 - t64| for any window of uint8 values, plus 1e-6.
+float decision_margin(int rule, double k, double R);
+
+} // namespace bnz

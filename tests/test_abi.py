@@ -1,0 +1,80 @@
+"""The C ABI library loads, exports every function include/bnz.h declares, and
+rejects bad arguments / reports a missing GPU without computing anything (CPU)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1210_3165_gb300 as bnz
+from paper_1210_3165_gb300 import _build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(bnz_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return bnz.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared_functions()
+    assert "bnz_sauvola" in names and "bnz_niblack" in names
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_version_and_error_string(lib):
+    assert bnz.bnz_version() >= 100
+    assert isinstance(bnz.bnz_last_error(), str)
+
+
+@pytest.mark.parametrize("args,fragment", [
+    (dict(W=0), "window size"),
+    (dict(W=256), "window size"),
+    (dict(R=0.0), "R must be"),
+    (dict(k=float("nan")), "k must be finite"),
+    (dict(channels=2), "channels"),
+    (dict(h=0), "height and width"),
+])
+def test_argument_errors(lib, args, fragment):
+    a = dict(h=8, w=9, channels=1, W=3, k=0.5, R=128.0)
+    a.update(args)
+    src = np.zeros(max(a["h"], 1) * a["w"] * 3, np.uint8)
+    dst = np.zeros(max(a["h"], 1) * a["w"], np.uint8)
+    rc = lib.bnz_sauvola(src.ctypes.data, a["h"], a["w"], a["channels"], a["W"], a["k"], a["R"],
+                         dst.ctypes.data)
+    assert rc == bnz.BNZ_EINVAL
+    assert fragment in bnz.bnz_last_error()
+
+
+def test_null_pointer_rejected(lib):
+    rc = lib.bnz_niblack(None, 4, 4, 1, 3, -0.2, None)
+    assert rc == bnz.BNZ_EINVAL
+
+
+def test_no_gpu_means_no_result():
+    """Without a CUDA device the library reports BNZ_ENODEV: there is no CPU path."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    lib = bnz.load()
+    src = np.full((16, 16), 100, np.uint8)
+    dst = np.zeros((16, 16), np.uint8)
+    rc = lib.bnz_sauvola(src.ctypes.data, 16, 16, 1, 5, 0.5, 128.0, dst.ctypes.data)
+    assert rc == bnz.BNZ_ENODEV
+    assert (dst == 0).all()
+    with pytest.raises(bnz.BnzError):
+        bnz.bnz_sauvola(src, 5)

@@ -1,0 +1,157 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle, element
+by element, on seeded synthetic pages.  Window sums are exact integers, so
+the masks must match bit for bit; tie counts must match the oracle's."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+NTHREADS = os.cpu_count() or 4
+
+
+@pytest.fixture(scope="module")
+def bnz():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1210_3165_gb300 as b
+    b.load()
+    return b
+
+
+def run_gpu(bnz, img, W, rule, k, R=128.0, packed=False, tile=None):
+    d = bnz.to_device_pitched(img)
+    stats = torch.zeros(4, dtype=torch.int64, device="cuda")
+    out = bnz.binarize(d, W, rule, k, R, packed=packed, tile=tile, d_stats=stats)
+    torch.cuda.synchronize()
+    st = stats.cpu().numpy()
+    assert st[2] == 0, "device wait timed out"
+    return out.cpu().numpy(), int(st[0]), int(st[1])
+
+
+def check(bnz, img, W, rule, k, R=128.0, packed=False, tile=None):
+    rid = oracle.SAUVOLA if rule == "sauvola" else oracle.NIBLACK
+    ref, ties = oracle.binarize(img, W, rid, k, R, threads=NTHREADS, packed=packed)
+    got, nfb, nties = run_gpu(bnz, img, W, rule, k, R, packed, tile)
+    if not np.array_equal(got, ref):
+        bad = np.argwhere(got != ref)
+        y, x = bad[0]
+        raise AssertionError(f"{len(bad)} mismatches (W={W} {rule} packed={packed}); first at {y},{x}: "
+                             f"gpu={got[y, x]} oracle={ref[y, x]}")
+    assert nties == ties
+    return nfb
+
+
+def test_config_512_gray_sauvola(bnz):
+    img = synth.page(512, 512, 1)
+    check(bnz, img, 15, "sauvola", 0.5)
+
+
+SHAPES = [(1, 1), (1, 37), (37, 1), (5, 7), (17, 300), (300, 17), (129, 257), (263, 531)]
+
+
+@pytest.mark.parametrize("h,w", SHAPES)
+@pytest.mark.parametrize("ch", [1, 3])
+def test_small_and_ragged_shapes(bnz, h, w, ch):
+    rng = np.random.default_rng(h * 1000 + w + ch)
+    img = synth.page(h, w, h + w, synth.STAINS if ch == 3 else synth.DOC, ch)
+    for W in (1, 2, 3, 8, 15, 64, 101):
+        rule = "sauvola" if rng.random() < 0.5 else "niblack"
+        k = 0.5 if rule == "sauvola" else -0.2
+        check(bnz, img, W, rule, k, packed=bool(rng.random() < 0.3))
+
+
+@pytest.mark.parametrize("W", [15, 31, 61, 101])
+@pytest.mark.parametrize("ch", [1, 3])
+def test_multi_tile_ragged_tail(bnz, W, ch):
+    img = synth.page(1031, 2063, 77 + W, synth.STAINS if ch == 3 else synth.VIGNETTE, ch)
+    check(bnz, img, W, "sauvola", 0.5)
+    check(bnz, img, W, "niblack", -0.2, packed=True)
+
+
+@pytest.mark.parametrize("W", [15, 31, 61, 101])
+def test_config_4096_rgb_full(bnz, W):
+    img = synth.page(4096, 4096, 2, synth.STAINS, 3)
+    check(bnz, img, W, "sauvola", 0.5)
+    check(bnz, img, W, "niblack", -0.2)
+
+
+def test_config_16384_gray_w101_full(bnz):
+    img = synth.page(16384, 16384, 3, synth.VIGNETTE, 1)
+    nfb = check(bnz, img, 101, "sauvola", 0.34)
+    assert nfb < img.size * 1e-3
+
+
+def test_large_and_even_windows(bnz):
+    img = synth.page(700, 900, 5, synth.DOC, 1)
+    for W in (128, 200, 254, 255):
+        check(bnz, img, W, "sauvola", 0.5)
+    rgb = synth.page(300, 1100, 6, synth.STAINS, 3)
+    check(bnz, rgb, 255, "niblack", -0.2, packed=True)
+
+
+def test_window_larger_than_image(bnz):
+    img = synth.page(40, 60, 8)
+    for W in (81, 121, 255):
+        check(bnz, img, W, "sauvola", 0.5)
+        check(bnz, img, W, "niblack", 0.3)
+
+
+def test_constant_image_ties(bnz):
+    for c in (0, 77, 255):
+        img = np.full((300, 700), c, np.uint8)
+        got, _, nties = run_gpu(bnz, img, 31, "niblack", -0.2)
+        assert (got == 255).all() and nties == img.size     # t = c exactly: every pixel a tie
+        got, _, nties = run_gpu(bnz, img, 31, "sauvola", 0.5)
+        assert (got == 255).all() and nties == (img.size if c == 0 else 0)
+
+
+def test_other_parameters(bnz):
+    img = synth.page(613, 811, 9, synth.STAINS, 3)
+    for k, R in ((0.0, 128.0), (0.2, 64.0), (0.9, 255.0), (1.5, 30.0), (-0.3, 128.0)):
+        check(bnz, img, 25, "sauvola", k, R)
+    for k in (0.0, -1.0, 0.7):
+        check(bnz, img, 25, "niblack", k)
+
+
+def test_explicit_tile_shapes_agree(bnz):
+    img = synth.page(900, 1500, 10, synth.DOC, 1)
+    for tw in (256, 512):
+        for chunk in (8, 16):
+            for th in (0, 7, 50):
+                tile = bnz.bnz_tile(tw, th, chunk, 0)
+                check(bnz, img, 45, "sauvola", 0.5, tile=tile)
+
+
+def test_host_pointer_api(bnz):
+    img = synth.page(333, 444, 11, synth.STAINS, 3)
+    ref, _ = oracle.sauvola(img, 21, 0.5, 128.0)
+    np.testing.assert_array_equal(bnz.bnz_sauvola(img, 21, 0.5, 128.0), ref)
+    ref, _ = oracle.niblack(img, 21, -0.2)
+    np.testing.assert_array_equal(bnz.bnz_niblack(img, 21, -0.2), ref)
+
+
+def test_unaligned_pitch_rejected(bnz):
+    t = torch.zeros((10, 33), dtype=torch.uint8, device="cuda")[:, :30]   # pitch 33
+    out = torch.zeros((10, 30), dtype=torch.uint8, device="cuda")
+    with pytest.raises(bnz.BnzError) as e:
+        bnz.bnz_sauvola_dev(t, 5, 0.5, 128.0, out)
+    assert e.value.status == bnz.BNZ_EINVAL
+
+
+def test_stream_async_and_repeatable(bnz):
+    img = synth.page(1200, 1600, 12, synth.DOC, 1)
+    d = bnz.to_device_pitched(img)
+    s = torch.cuda.Stream()
+    outs = []
+    with torch.cuda.stream(s):
+        for _ in range(3):
+            outs.append(bnz.binarize(d, 31, "sauvola", 0.5, stream=s))
+    s.synchronize()
+    ref, _ = oracle.sauvola(img, 31, threads=NTHREADS)
+    for o in outs:
+        np.testing.assert_array_equal(o.cpu().numpy(), ref)
