@@ -135,6 +135,12 @@ BNZ_API int bnz_version(void);
 BNZ_API int bnz_fused_plan(int height, int width, int channels, int W, const bnz_tile *tile, size_t *smem_bytes,
                    int *grid_ctas, int *tile_w, int *tile_h);
 
+/* Device self-test of the hardware square-root approximation the fused
+ * kernel's fp32 margin assumes (relative error <= 2^-21): writes to
+ * *max_rel_err an upper bound on |sqrt.approx(x) - sqrt(x)| / sqrt(x) over
+ * every float x in [lo, hi).  Synchronous; for tests and diagnostics. */
+BNZ_API int bnz_selftest_sqrt_approx(float lo, float hi, double *max_rel_err);
+
 #ifdef __cplusplus
 }
 #endif

@@ -71,6 +71,8 @@ def _optional_symbols(lib):
     """Entry points added by later parts of the library (integral images, batches)."""
     P, i, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
     table = {
+        "bnz_selftest_sqrt_approx": ([ctypes.c_float, ctypes.c_float, ctypes.POINTER(ctypes.c_double)],
+                                     ctypes.c_int),
         "bnz_integral_scratch_bytes": ([i, i], ctypes.c_size_t),
         "bnz_binarize_integral_dev": ([P, sz, i, i, i, i, i, d, d, P, sz, i, P, sz, P, P], ctypes.c_int),
         "bnz_window_sums_dev": ([P, sz, i, i, i, i, P, P, P, P], ctypes.c_int),
@@ -140,14 +142,20 @@ def _dev_img(t):
     import torch
     if not isinstance(t, torch.Tensor) or t.dtype != torch.uint8 or not t.is_cuda:
         raise TypeError("expected a uint8 CUDA tensor")
+    # strides of size-1 dimensions carry no information: a single row gets the
+    # smallest 16-byte multiple as its pitch (no other row is ever addressed)
     if t.dim() == 2:
-        if t.stride(1) != 1:
+        h, w = t.shape
+        if w > 1 and t.stride(1) != 1:
             raise ValueError("inner stride must be 1")
-        return t.data_ptr(), t.stride(0), t.shape[0], t.shape[1], 1
+        pitch = t.stride(0) if h > 1 else (w + 15) // 16 * 16
+        return t.data_ptr(), pitch, h, w, 1
     if t.dim() == 3 and t.shape[2] == 3:
-        if t.stride(2) != 1 or t.stride(1) != 3:
+        h, w = t.shape[:2]
+        if t.stride(2) != 1 or (w > 1 and t.stride(1) != 3):
             raise ValueError("RGB tensor must be interleaved (strides (pitch, 3, 1))")
-        return t.data_ptr(), t.stride(0), t.shape[0], t.shape[1], 3
+        pitch = t.stride(0) if h > 1 else (3 * w + 15) // 16 * 16
+        return t.data_ptr(), pitch, h, w, 3
     raise ValueError("image must be HxW or HxWx3")
 
 
@@ -159,12 +167,12 @@ def _stream_ptr(stream):
 
 
 def _out_pitch(dst, w, packed):
-    if dst.dim() != 2 or dst.stride(1) != 1 or dst.dtype.itemsize != 1:
+    if dst.dim() != 2 or (dst.shape[1] > 1 and dst.stride(1) != 1) or dst.dtype.itemsize != 1:
         raise ValueError("dst must be a 2-D uint8 tensor with unit inner stride")
     need = (w + 7) // 8 if packed else w
     if dst.shape[1] < need:
         raise ValueError(f"dst rows must hold {need} bytes")
-    return dst.stride(0)
+    return dst.stride(0) if dst.shape[0] > 1 else max(dst.shape[1], 1)
 
 
 def bnz_binarize_dev(d_src, W: int, rule: int, k: float, R: float, d_dst, packed: bool = False,
@@ -215,7 +223,9 @@ def to_device_pitched(img: np.ndarray, device="cuda"):
     ch = 1 if img.ndim == 2 else 3
     t = alloc_pitched(h, w * ch, device)
     t.copy_(torch.from_numpy(img.reshape(h, w * ch)))
-    return t if ch == 1 else t.unflatten(1, (w, 3))
+    if ch == 1:
+        return t
+    return torch.as_strided(t, (h, w, 3), (t.stride(0), 3, 1))
 
 
 def binarize(d_src, W: int, rule: str | int = "sauvola", k: float | None = None, R: float = 128.0,

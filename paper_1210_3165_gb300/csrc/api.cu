@@ -300,11 +300,11 @@ int bnz_fused_plan(int height, int width, int channels, int W, const bnz_tile *t
     if (smem_bytes)
         *smem_bytes = pl.smem;
     if (grid_ctas)
-        *grid_ctas = pl.tiles_y;
+        *grid_ctas = pl.grid;
     if (tile_w)
         *tile_w = pl.TW;
     if (tile_h)
-        *tile_h = pl.TH;
+        *tile_h = pl.rows_per_cta;
     return BNZ_OK;
 }
 

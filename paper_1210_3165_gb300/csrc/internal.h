@@ -25,17 +25,18 @@ int device_sm_count(int *sms);
 
 // Shape of one launch of the fused kernel (host-side plan).
 struct FusedPlan {
-    int L;          // outputs per lane per row (tile_w = 32 * L)
-    int TW, TH, CH; // tile width/height, rows per TMA chunk
+    int TW, CH;     // strip width (32 lanes x 16 outputs), rows per TMA chunk
     int NS;         // ring slots (chunks) of gray rows in shared memory
     int NSS;        // staging slots for RGB chunks (0 for gray)
     int PWP;        // panel width in pixels (one TMA box per panel per chunk)
     int NPAN, SWP;  // panels per span, span width in pixels
-    int RS;         // row stride of the column-sum buffer (uint2 units, odd)
+    int RSW;        // row stride (32-bit words) of each column-sum array
     int ring_rows;  // NS * CH
     int o;          // span start offset: (x0 - r_lo) - floor16(x0 - r_lo)
-    int tiles_x, tiles_y;
-    uint32_t off_ring, off_stage, off_cb;
+    int tiles_x;    // strips across the image
+    int grid;       // persistent CTAs
+    int rows_per_cta;
+    uint32_t off_ring, off_stage, off_c1, off_c2;
     size_t smem;
 };
 
@@ -45,11 +46,19 @@ struct FusedParams {
     unsigned long long *stats;
     unsigned int *err_flag; // library-owned device word, counts CTAs that gave up
     int h, w, W, r_lo, r_hi, o;
-    int TW, TH, CH, NS, NSS, NPAN, SWP, RS, ring_rows, tiles_x;
-    uint32_t off_ring, off_stage, off_cb;
-    double k, R;
-    float kf, invRf, E, invn;
-    int vec_ok; // dst and dst_pitch 16-byte aligned
+    int TW, CH, NS, NSS, NPAN, SWP, RSW, ring_rows, tiles_x;
+    uint32_t off_ring, off_stage, off_c1, off_c2;
+    int packed;     // 1: one bit per pixel
+    int vec_ok;     // dst and dst_pitch 16-byte aligned
+    int s1_magic;   // S1 < 2^23 for every window: exact int->float by bit tricks
+    uint32_t nW;    // W*W
+    double k, R;    // the caller's parameters, for the fp64 re-evaluation
+    // fp32 constants of the filter for unclipped windows (n = W*W):
+    //   Sauvola d = f - S1 * (omkn + kRn2 * sqrt(V)),  omkn = (1-k)/n, kRn2 = k/(R n^2)
+    //   Niblack d = f - S1 * invn - kn * sqrt(V),      invn = 1/n,     kn = k/n
+    float omkn, kRn2, invn, kn;
+    float kf, omk, kR; // k, 1-k, k/R for clipped windows
+    float E;           // proven bound on |d32 - (f - t)|, with safety factor
     long long timeout_cycles;
 };
 
@@ -61,8 +70,10 @@ int launch_fused(const uint8_t *d_src, size_t src_pitch, int h, int w, int ch, i
 // Library-owned per-device error word (allocated on first use).
 int device_err_flag(unsigned int **flag);
 
-// fp32 decision margin: an upper bound (with a factor-2 safety) on
-// |t32 - t64| for any window of uint8 values, plus 1e-6.
+// Relative error bound assumed for sqrt.approx.f32 (checked on the device by the tests).
+constexpr double kSqrtApproxRelErr = 1.0 / (1 << 21);
+
+// fp32 decision margin E (see fused.cu for the derivation).
 float decision_margin(int rule, double k, double R);
 
 } // namespace bnz

@@ -1,0 +1,60 @@
+// selftest.cu -- device check of the one hardware approximation the fused
+// kernel's error bound relies on: the relative error of sqrt.approx.f32.
+#include <cstring>
+
+#include "internal.h"
+
+namespace bnz {
+namespace {
+
+__global__ void sqrt_approx_err_kernel(uint32_t first_bits, uint64_t count, unsigned int *max_err_bits)
+{
+    float worst = 0.0f;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+        const float x = __uint_as_float(first_bits + (uint32_t)i);
+        float a;
+        asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(a) : "f"(x));
+        // r is the correctly rounded root (|r - sqrt(x)| <= 2^-24 r); the caller adds 2^-24
+        const float r = __fsqrt_rn(x);
+        worst = fmaxf(worst, __fdiv_rn(fabsf(a - r), r));
+    }
+    for (int off = 16; off; off >>= 1)
+        worst = fmaxf(worst, __shfl_xor_sync(0xffffffffu, worst, off));
+    if ((threadIdx.x & 31) == 0)
+        atomicMax(max_err_bits, __float_as_uint(worst)); // non-negative floats order like their bits
+}
+
+} // namespace
+} // namespace bnz
+
+extern "C" BNZ_API int bnz_selftest_sqrt_approx(float lo, float hi, double *max_rel_err)
+{
+    using namespace bnz;
+    if (!max_rel_err || !(lo > 0.0f) || !(hi > lo))
+        return fail(BNZ_EINVAL, "need 0 < lo < hi and a result pointer");
+    unsigned int *d = nullptr;
+    cudaError_t e = cudaMalloc(&d, sizeof(unsigned int));
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaMalloc(selftest)");
+    unsigned int h = 0;
+    do {
+        if ((e = cudaMemset(d, 0, sizeof(unsigned int))) != cudaSuccess)
+            break;
+        uint32_t a, b;
+        memcpy(&a, &lo, 4);
+        memcpy(&b, &hi, 4);
+        sqrt_approx_err_kernel<<<1216, 256>>>(a, (uint64_t)(b - a), d);
+        if ((e = cudaGetLastError()) != cudaSuccess)
+            break;
+        if ((e = cudaMemcpy(&h, d, sizeof h, cudaMemcpyDeviceToHost)) != cudaSuccess)
+            break;
+    } while (0);
+    cudaFree(d);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "sqrt.approx self-test");
+    float f;
+    memcpy(&f, &h, 4);
+    *max_rel_err = (double)f * (1.0 + 1e-6) + 1.0 / 16777216.0; // bound vs the exact root
+    return BNZ_OK;
+}

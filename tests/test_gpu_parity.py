@@ -120,7 +120,7 @@ def test_other_parameters(bnz):
 
 def test_explicit_tile_shapes_agree(bnz):
     img = synth.page(900, 1500, 10, synth.DOC, 1)
-    for tw in (256, 512):
+    for tw in (0, 256, 512):
         for chunk in (8, 16):
             for th in (0, 7, 50):
                 tile = bnz.bnz_tile(tw, th, chunk, 0)
@@ -155,3 +155,12 @@ def test_stream_async_and_repeatable(bnz):
     ref, _ = oracle.sauvola(img, 31, threads=NTHREADS)
     for o in outs:
         np.testing.assert_array_equal(o.cpu().numpy(), ref)
+
+
+def test_sqrt_approx_error_within_margin_assumption(bnz):
+    """The fp32 margin assumes sqrt.approx.f32 has relative error <= 2^-21 on [1, 2^44)."""
+    import ctypes
+    err = ctypes.c_double(0.0)
+    rc = bnz.load().bnz_selftest_sqrt_approx(1.0, float(2 ** 44), ctypes.byref(err))
+    assert rc == 0, bnz.bnz_last_error()
+    assert 0.0 < err.value <= 2.0 ** -21, err.value
