@@ -78,9 +78,9 @@ typedef enum { BNZ_SAUVOLA = 0, BNZ_NIBLACK = 1 } bnz_rule;
 #define BNZ_STATS_TIMEOUTS 2
 
 /* Optional tile shape for the fused kernel (autotuner hook).  Zero fields
- * mean "library default".  tile_w: output columns per strip, 256 or 512.
+ * mean "library default".  tile_w: output columns per strip, 128, 256 or 512.
  * tile_h: approximate rows of work per CTA (sets the grid size).
- * chunk: rows per TMA load, 8 or 16. */
+ * chunk: rows per TMA load (8). */
 typedef struct {
     int tile_w;
     int tile_h;
@@ -140,6 +140,10 @@ BNZ_API int bnz_fused_plan(int height, int width, int channels, int W, const bnz
  * *max_rel_err an upper bound on |sqrt.approx(x) - sqrt(x)| / sqrt(x) over
  * every float x in [lo, hi).  Synchronous; for tests and diagnostics. */
 BNZ_API int bnz_selftest_sqrt_approx(float lo, float hi, double *max_rel_err);
+
+/* Same for the hardware reciprocal approximation over the integers
+ * n_lo <= n < n_hi (the clipped window counts; assumed <= 2^-22). */
+BNZ_API int bnz_selftest_rcp_approx(unsigned int n_lo, unsigned int n_hi, double *max_rel_err);
 
 #ifdef __cplusplus
 }

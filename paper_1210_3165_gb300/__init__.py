@@ -73,6 +73,8 @@ def _optional_symbols(lib):
     table = {
         "bnz_selftest_sqrt_approx": ([ctypes.c_float, ctypes.c_float, ctypes.POINTER(ctypes.c_double)],
                                      ctypes.c_int),
+        "bnz_selftest_rcp_approx": ([ctypes.c_uint, ctypes.c_uint, ctypes.POINTER(ctypes.c_double)],
+                                    ctypes.c_int),
         "bnz_integral_scratch_bytes": ([i, i], ctypes.c_size_t),
         "bnz_binarize_integral_dev": ([P, sz, i, i, i, i, i, d, d, P, sz, i, P, sz, P, P], ctypes.c_int),
         "bnz_window_sums_dev": ([P, sz, i, i, i, i, P, P, P, P], ctypes.c_int),

@@ -1,36 +1,40 @@
 // fused.cu -- the fused tile kernel for exact Sauvola / Niblack binarization.
 //
-// One persistent CTA walks a contiguous range of "strip rows": the image is
-// cut into vertical strips of 512 output columns, the strips are laid end to
-// end (strip-major), and the total is split evenly over the grid.  For each
-// run of rows it owns in a strip the CTA
-//   a1  loads the strip plus its halo (W-1 columns, 16-aligned on the left)
-//       row-chunk by row-chunk with 2-D TMA boxes into a shared-memory ring
-//       that holds the last W + 2*chunk rows, so every input byte comes from
-//       global memory once per strip;
-//   a2  for RGB input converts each chunk to gray in shared memory with the
+// One persistent CTA of 16 warps walks a contiguous range of "strip rows":
+// the image is cut into vertical strips of 512 output columns (256 for very
+// large W), the strips are laid end to end (strip-major) and the total is
+// split evenly over the grid.  Warps 0-7 (producers) and 8-15 (consumers)
+// work on consecutive row chunks at the same time, handing over column sums
+// through two shared-memory buffers guarded by named barriers.
+//
+// Producers, for each chunk of rows of a strip segment:
+//   a1  load the strip plus its halo (W-1 columns, 16-aligned on the left)
+//       chunk by chunk with 2-D TMA boxes into a shared-memory ring holding
+//       the last W + 3 chunks of rows, so each input byte comes from global
+//       memory once per strip;
+//   a2  for RGB input convert each chunk to gray in shared memory with the
 //       integer rule of Eq. 1, f = (299 r + 587 g + 114 b + 500) / 1000
 //       (two byte dot products and a multiply-high per pixel);
-//   a3  keeps exact column sums c1 = sum f and c2 = sum f^2 over the W window
-//       rows in registers (4 columns per thread), publishes them for the
-//       current row, then adds the entering row and drops the leaving one;
-//   a4  forms the horizontal window sums S1, S2 from the published column
-//       sums: each lane slides over 16 consecutive outputs (128-bit loads,
-//       realigned at compile time), the lanes' partial sums are joined with a
-//       warp scan, and a warp reduction gives the first window of the row;
-//   a5  takes n = W*W for windows inside the image and the clipped count at
-//       the borders;
-//   a6  decides f < t (Eq. 3) for Sauvola (Eq. 4) or Niblack with an fp32
+//   a3  keep exact column sums c1 = sum f and c2 = sum f^2 over the W window
+//       rows in registers (4 columns per thread), publish them for each row
+//       of the chunk, adding the entering row and dropping the leaving one.
+// Consumers, one output row per warp:
+//   a4  form the horizontal window sums S1, S2: each lane slides over 16
+//       consecutive outputs (128-bit loads realigned at compile time), the
+//       lanes' partial sums are joined by a warp scan, and a warp reduction
+//       gives the row's first window;
+//   a5  use n = W*W, or, in warps that touch the image border, the clipped
+//       count of each pixel;
+//   a6  decide f < t (Eq. 3) for Sauvola (Eq. 4) or Niblack with an fp32
 //       filter whose error is bounded (decision_margin); pixels inside the
 //       bound re-run the fp64 sequence m = S1/n, s = sqrt(V)/n, t = ..., so
 //       every output equals that fp64 decision;
-//   a7  writes the byte mask {0,255} or the packed 1-bit mask.
-// The sums are never rounded: S1 < 2^24 and S2 < 2^32 for W <= 255, and
+//   a7  write the byte mask {0,255} or the packed 1-bit mask.
+// The sums are exact: S1 < 2^24 and S2 < 2^32 for W <= 255, and
 // V = n*S2 - S1^2 is formed in 64-bit integers.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
-#include <type_traits>
 
 #include "internal.h"
 #include "ptx.cuh"
@@ -38,46 +42,42 @@
 namespace bnz {
 namespace {
 
-constexpr int NT = 256;
-constexpr int NWARP = NT / 32;
-constexpr int L = 16;  // outputs per lane per row; a strip is 32 * L = 512 columns wide
-constexpr int TW = 32 * L; // widest strip; 256 is used when the ring would not fit
+constexpr int NTP = 256;            // producer threads (warps 0-7)
+constexpr int NTQ = 256;            // consumer threads (warps 8-15), one row each
+constexpr int NT = NTP + NTQ;
+constexpr int L = 16;               // outputs per consumer lane per row
+constexpr int TW = 32 * L;          // widest strip; 256 is used when the ring would not fit
+constexpr int BAR_FULL = 1;         // named barriers 1,2: column-sum buffer b is ready
+constexpr int BAR_EMPTY = 3;        // named barriers 3,4: column-sum buffer b may be refilled
+constexpr int BAR_PROD = 5;         // producers only
+constexpr int kL2 = 6;              // chunks of L2 prefetch lead beyond the shared-memory loads
+constexpr int CH = 8;               // rows per chunk (TMA box height, one consumer warp per row)
+constexpr int kLeadGray = 3;        // gray: chunks loaded ahead of the ones in use
 constexpr int MAX_DYN_SMEM = 232448 - 1024; // 227 KB opt-in limit, minus slack
 
-template <int CIN>
-struct PanelWidth;
-template <>
-struct PanelWidth<1> {
-    static constexpr int PWP = 128; // one 128-byte TMA box per panel
-};
-template <>
-struct PanelWidth<3> {
-    static constexpr int PWP = 80; // 240-byte boxes: whole r,g,b triples
-};
+// Panel widths in pixels (one TMA box per panel and chunk): gray 128 (or 64
+// when shared memory is tight), RGB 80 (240-byte boxes, whole r,g,b triples).
 
-__device__ __forceinline__ uint32_t byte_of(uint32_t w, int k)
+__device__ __forceinline__ void bar_sync(int id, int n)
 {
-    return (w >> (8 * k)) & 0xffu;
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
 
-// Position of span column c in a column-sum row: 4 words of padding after
-// every 16 columns keep the lanes' 128-bit loads free of bank conflicts.
-__device__ __forceinline__ int cpos(int c)
+__device__ __forceinline__ void bar_arrive(int id, int n)
 {
-    return c + ((c >> 4) << 2);
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
 
-// exact uint -> float for v < 2^23: 2^23 + v has v in its mantissa
-__device__ __forceinline__ float u23_to_float(uint32_t v)
-{
-    return __fsub_rn(__uint_as_float(v | 0x4B000000u), 8388608.0f);
-}
-
-// byte J of `word` as an exact float (same trick, byte moved by a permute)
+// byte J of w, zero-extended (one permute)
 template <int J>
-__device__ __forceinline__ float byte_to_float(uint32_t word)
+__device__ __forceinline__ uint32_t byte_at(uint32_t w)
 {
-    return __fsub_rn(__uint_as_float(__byte_perm(word, 0x4B000000u, 0x7440u | J)), 8388608.0f);
+    return __byte_perm(w, 0u, 0x4440u | J);
+}
+
+__device__ __forceinline__ uint32_t byte_dyn(uint32_t w, int j)
+{
+    return (w >> (8 * j)) & 0xffu;
 }
 
 // PTX prmt (default mode): a selector nibble with bit 3 set yields the sign
@@ -96,12 +96,31 @@ __device__ __forceinline__ float sqrt_approx(float x)
     return r;
 }
 
-// V (< 2^48) as float: high word exact, low word rounded, one more rounding
-// in the fma -- relative error <= 2u (u = 2^-24); no 64-bit conversion, which
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// V (< 2^48) as float: high word exact, low word rounded, one more rounding in
+// the fma -- relative error <= 2u (u = 2^-24).  A 64-bit integer conversion
 // would run on the fp64 pipe.
 __device__ __forceinline__ float v_to_float(unsigned long long V)
 {
     return __fmaf_rn(__uint2float_rn((uint32_t)(V >> 32)), 4294967296.0f, __uint2float_rn((uint32_t)V));
+}
+
+// Position of span column c in a column-sum row: 4 words of padding after
+// every 16 columns keep the lanes' 128-bit loads free of bank conflicts.
+__device__ __forceinline__ int cpos(int c)
+{
+    return c + ((c >> 4) << 2);
+}
+
+__device__ __forceinline__ uint4 ld_group(const uint32_t *C, int a) // columns 4a..4a+3
+{
+    return *reinterpret_cast<const uint4 *>(C + 4 * a + ((a >> 2) << 2));
 }
 
 // Eq. 1 for one pixel whose r, g, b are bytes 0..2 of px (byte 3 ignored):
@@ -124,39 +143,30 @@ __device__ __forceinline__ uint32_t gray4(uint32_t w0, uint32_t w1, uint32_t w2)
     return g0 | (g1 << 8) | (g2 << 16) | (g3 << 24);
 }
 
-// fp32 filter value d ~ f - t for a window of n = W*W pixels.
+// fp32 filter d ~ f - t, n = W*W (constants from the host in double, rounded once)
 template <int RULE>
-__device__ __forceinline__ float filter_d(float ff, float S1f, float sq, const FusedParams &p)
+__device__ __forceinline__ float filter_int(float ff, float S1f, float sq, const FusedParams &p)
 {
     if (RULE == BNZ_SAUVOLA)
         return __fmaf_rn(-S1f, __fmaf_rn(p.kRn2, sq, p.omkn), ff);
     return __fmaf_rn(-p.kn, sq, __fmaf_rn(-p.invn, S1f, ff));
 }
 
-// Exact decision for one pixel whose window may be clipped or whose fp32
-// value fell inside the margin.  Returns g | 0x100 (fp64 used) | 0x200 (tie).
+// fp32 filter d ~ f - t for a pixel with its own n (invn ~ 1/n from rcp.approx)
 template <int RULE>
-__device__ __noinline__ uint32_t slow_decide(uint32_t f, uint32_t S1, uint32_t S2, int y, int xg,
-                                             const FusedParams &p)
+__device__ __forceinline__ float filter_n(float ff, float S1f, float sq, float invn, const FusedParams &p)
 {
-    const int nr = min(y + p.r_hi, p.h - 1) - max(y - p.r_lo, 0) + 1;
-    const int nc = min(xg + p.r_hi, p.w - 1) - max(xg - p.r_lo, 0) + 1;
-    const uint32_t n = (uint32_t)(nr * nc);
+    if (RULE == BNZ_SAUVOLA)
+        return __fmaf_rn(-S1f, __fmaf_rn(__fmul_rn(__fmul_rn(p.kR, invn), invn), sq, __fmul_rn(p.omk, invn)), ff);
+    return __fmaf_rn(-__fmul_rn(p.kf, invn), sq, __fmaf_rn(-invn, S1f, ff));
+}
+
+// The fp64 sequence of the definition, same order, no contraction.
+// Returns g | 0x200 if |f - t| < 1e-9 (a tie).
+template <int RULE>
+__device__ __noinline__ uint32_t decide_fp64(uint32_t f, uint32_t n, uint32_t S1, uint32_t S2, const FusedParams &p)
+{
     const unsigned long long V = (unsigned long long)n * S2 - (unsigned long long)S1 * S1;
-    const float sq = sqrt_approx(v_to_float(V));
-    const float invn = __frcp_rn(__uint2float_rn(n));
-    const float S1f = __uint2float_rn(S1), ff = __uint2float_rn(f);
-    float d;
-    if (RULE == BNZ_SAUVOLA) {
-        const float a = __fmul_rn(p.omk, invn);
-        const float b = __fmul_rn(__fmul_rn(p.kR, invn), invn);
-        d = __fmaf_rn(-S1f, __fmaf_rn(b, sq, a), ff);
-    } else {
-        d = __fmaf_rn(-__fmul_rn(p.kf, invn), sq, __fmaf_rn(-invn, S1f, ff));
-    }
-    if (fabsf(d) >= p.E)
-        return d < 0.0f ? 0u : 255u;
-    // the fp64 sequence of the definition, same order, no contraction
     const double nd = (double)n;
     const double md = __ddiv_rn((double)S1, nd);
     const double sd = __ddiv_rn(__dsqrt_rn(__ull2double_rn(V)), nd);
@@ -167,13 +177,422 @@ __device__ __noinline__ uint32_t slow_decide(uint32_t f, uint32_t S1, uint32_t S
         td = __dadd_rn(md, __dmul_rn(p.k, sd));
     const double fd = (double)f;
     const uint32_t tie = fabs(__dsub_rn(fd, td)) < 1e-9 ? 0x200u : 0u;
-    return (fd < td ? 0u : 255u) | 0x100u | tie;
+    return (fd < td ? 0u : 255u) | tie;
 }
 
-// 16-byte load of 4 column sums (group a = columns 4a..4a+3)
-__device__ __forceinline__ uint4 ld_group(const uint32_t *C, int a)
+struct Segment {
+    int x0, y0, th_eff, xs, ys, nchk, nk;
+};
+
+// ---------------------------------------------------------------------------
+// producers: TMA ring, RGB->gray, column sums (a1-a3)
+// ---------------------------------------------------------------------------
+template <int CIN>
+__device__ __forceinline__ void produce(const CUtensorMap *tmap, const FusedParams &p, const Segment &sg,
+                                        uint8_t *smem, uint64_t &phase, volatile int *s_abort)
 {
-    return *reinterpret_cast<const uint4 *>(C + 4 * a + ((a >> 2) << 2));
+    const int PWP = p.PWP;
+    const int PWB = PWP * CIN;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
+    uint8_t *ring = smem + p.off_ring;
+    uint8_t *stage = smem + p.off_stage;
+    uint32_t *cb = reinterpret_cast<uint32_t *>(smem + p.off_cb);
+    const int tid = threadIdx.x; // 0..NTP-1
+    const int W = p.W;
+    const int D = (CH + W - 1) / CH;
+    const int nbar = CIN == 1 ? p.NS : p.NSS;
+    const uint32_t chunk_bytes = (uint32_t)(p.NPAN * CH * PWB);
+    const bool owner = tid < (p.SWP >> 2);
+    const int gcol = tid * 4;
+    const int gpn = gcol / PWP, gip = gcol - gpn * PWP;
+    const int gpos = cpos(gcol);
+    uint8_t *gbase = ring + (size_t)gpn * p.ring_rows * PWP + gip; // this thread's 4 columns, ring row 0
+    const uint8_t *sbase = stage + (size_t)gpn * CH * PWB + 3 * gip;  // the same columns in staging slot 0
+    const int ring_bytes = p.ring_rows * PWP;                     // one panel of the ring
+
+    int issued = 0, waited = 0;
+    bool good = !*s_abort;
+    // L2 prefetch of the chunk kL2 ahead of each shared-memory load, so the
+    // loads find their rows in L2 (the ring has room for only a few chunks)
+    auto prefetch = [&](int j) {
+        if (j < sg.nchk)
+            for (int pn = 0; pn < p.NPAN; ++pn)
+                tma_prefetch_l2_2d(tmap, (sg.xs + pn * PWP) * CIN, sg.ys + j * CH);
+    };
+    auto issue = [&](int j) { // thread 0 only
+        const int slot = j % nbar;
+        uint64_t *bar = &bars[slot];
+        mbar_arrive_expect_tx(bar, chunk_bytes);
+        for (int pn = 0; pn < p.NPAN; ++pn) {
+            uint8_t *dst = (CIN == 1) ? ring + (size_t)pn * p.ring_rows * PWP + (size_t)slot * CH * PWP
+                                      : stage + ((size_t)slot * p.NPAN + pn) * CH * PWB;
+            tma_load_2d(dst, tmap, (sg.xs + pn * PWP) * CIN, sg.ys + j * CH, bar);
+        }
+        prefetch(j + kL2);
+    };
+    // every producer waits for itself; a wait that gives up flags the CTA
+    // (the barrier protocol goes on, so no thread is left waiting)
+    auto wait_one = [&]() {
+        const int slot = waited % nbar;
+        if (!mbar_wait_bounded(&bars[slot], (uint32_t)((phase >> slot) & 1ull), p.timeout_cycles)) {
+            good = false;
+            *s_abort = 1;
+        }
+        phase ^= 1ull << slot;
+        ++waited;
+    };
+    // RGB: this thread's 4 columns of chunk j, staging slot -> gray ring slot (Eq. 1)
+    auto convert = [&](int j) {
+        if (!owner)
+            return;
+        const uint8_t *src = sbase + (size_t)(j % p.NSS) * p.NPAN * CH * PWB;
+        uint8_t *dst = gbase + (size_t)(j % p.NS) * CH * PWP;
+        uint32_t wv[CH][3];
+#pragma unroll
+        for (int r = 0; r < CH; ++r) {
+            const uint32_t *s32 = reinterpret_cast<const uint32_t *>(src + r * PWB);
+            wv[r][0] = s32[0];
+            wv[r][1] = s32[1];
+            wv[r][2] = s32[2];
+        }
+#pragma unroll
+        for (int r = 0; r < CH; ++r)
+            *reinterpret_cast<uint32_t *>(dst + r * PWP) = gray4(wv[r][0], wv[r][1], wv[r][2]);
+    };
+
+    // prologue: gray loads chunks 0..D+lead-1 straight into the ring; RGB fills its staging slots
+    const int lead = p.NS - D - 2; // gray: chunks in flight beyond the ones in use
+    if (good) {
+        const int pre = CIN == 1 ? min(sg.nchk, D + lead) : min(sg.nchk, p.NSS);
+        if (tid == 0) {
+            for (int j = pre; j < pre + kL2; ++j)
+                prefetch(j);
+            for (int j = 0; j < pre; ++j)
+                issue(j);
+        }
+        issued = pre;
+    }
+    // warm-up: chunks 0..D-1 hold rows 0..W-1, the window of the segment's first output row
+    for (int j = 0; j < D; ++j) {
+        if (good)
+            wait_one();
+        if (CIN == 3) {
+            if (good)
+                convert(j);
+            bar_sync(BAR_PROD, NTP); // staging slot j is free
+            if (good && issued < sg.nchk) {
+                if (tid == 0)
+                    issue(issued);
+                ++issued;
+            }
+        }
+    }
+    uint32_t c1[4] = {0u, 0u, 0u, 0u}, c2[4] = {0u, 0u, 0u, 0u};
+    if (good && owner) {
+        int off = 0;
+        for (int r = 0; r < W; ++r) {
+            const uint32_t v = *reinterpret_cast<const uint32_t *>(gbase + off);
+            c1[0] += byte_at<0>(v);
+            c1[1] += byte_at<1>(v);
+            c1[2] += byte_at<2>(v);
+            c1[3] += byte_at<3>(v);
+            c2[0] += byte_at<0>(v) * byte_at<0>(v);
+            c2[1] += byte_at<1>(v) * byte_at<1>(v);
+            c2[2] += byte_at<2>(v) * byte_at<2>(v);
+            c2[3] += byte_at<3>(v) * byte_at<3>(v);
+            off += PWP;
+            if (off == ring_bytes)
+                off = 0;
+        }
+    }
+    int off_in = (W % p.ring_rows) * PWP; // ring offset of row i + W (entering for output row i + 1)
+    int off_out = 0;                      // ring offset of row i (leaving), chunk-aligned
+
+    for (int k = 0; k < sg.nk; ++k) {
+        const int b = k & 1;
+        if (k >= 2)
+            bar_sync(BAR_EMPTY + b, NT); // consumers are done with chunk k-2
+        const int need = min(k + D, sg.nchk - 1);
+        if (CIN == 1) {
+            if (good && issued < sg.nchk) { // keep `lead` chunks in flight
+                if (tid == 0)
+                    issue(issued);
+                ++issued;
+            }
+            while (good && waited <= need)
+                wait_one();
+        } else {
+            while (good && waited <= need) {
+                const int j = waited;
+                wait_one();
+                if (good)
+                    convert(j); // own columns only: no barrier before the column sums
+            }
+        }
+        const int rows_k = min(CH, sg.th_eff - k * CH);
+        if (good && owner) {
+            const bool last = (k + 1 == sg.nk);
+            uint32_t *C1 = cb + (size_t)(2 * b) * CH * p.RSW + gpos;
+            uint32_t *C2 = C1 + (size_t)CH * p.RSW;
+            uint32_t vi[CH], vo[CH];
+#pragma unroll
+            for (int r = 0; r < CH; ++r) { // load first, then add: no smem latency per row
+                int oi = off_in + r * PWP;
+                if (oi >= ring_bytes)
+                    oi -= ring_bytes;
+                vi[r] = *reinterpret_cast<const uint32_t *>(gbase + oi);
+                vo[r] = *reinterpret_cast<const uint32_t *>(gbase + off_out + r * PWP);
+            }
+#pragma unroll
+            for (int r = 0; r < CH; ++r) {
+                if (r < rows_k) {
+                    *reinterpret_cast<uint4 *>(C1 + r * p.RSW) = make_uint4(c1[0], c1[1], c1[2], c1[3]);
+                    *reinterpret_cast<uint4 *>(C2 + r * p.RSW) = make_uint4(c2[0], c2[1], c2[2], c2[3]);
+                    if (!(last && r + 1 == rows_k)) { // slide to the next row
+                        const uint32_t a = vi[r], o = vo[r];
+                        c1[0] = c1[0] + byte_at<0>(a) - byte_at<0>(o);
+                        c1[1] = c1[1] + byte_at<1>(a) - byte_at<1>(o);
+                        c1[2] = c1[2] + byte_at<2>(a) - byte_at<2>(o);
+                        c1[3] = c1[3] + byte_at<3>(a) - byte_at<3>(o);
+                        c2[0] = c2[0] + byte_at<0>(a) * byte_at<0>(a) - byte_at<0>(o) * byte_at<0>(o);
+                        c2[1] = c2[1] + byte_at<1>(a) * byte_at<1>(a) - byte_at<1>(o) * byte_at<1>(o);
+                        c2[2] = c2[2] + byte_at<2>(a) * byte_at<2>(a) - byte_at<2>(o) * byte_at<2>(o);
+                        c2[3] = c2[3] + byte_at<3>(a) * byte_at<3>(a) - byte_at<3>(o) * byte_at<3>(o);
+                    }
+                }
+            }
+        }
+        off_in += CH * PWP;
+        if (off_in >= ring_bytes)
+            off_in -= ring_bytes;
+        off_out += CH * PWP;
+        if (off_out >= ring_bytes)
+            off_out -= ring_bytes;
+        bar_arrive(BAR_FULL + b, NT); // always, so consumers never wait forever
+        if (CIN == 3) {
+            bar_sync(BAR_PROD, NTP); // every producer is past the conversions of this step
+            while (good && issued < min(sg.nchk, waited + p.NSS)) {
+                if (tid == 0)
+                    issue(issued);
+                ++issued;
+            }
+        }
+    }
+    // drain this segment's copies (bounded) before the ring is reused
+    while (waited < issued) {
+        const int slot = waited % nbar;
+        mbar_wait_bounded(&bars[slot], (uint32_t)((phase >> slot) & 1ull), p.timeout_cycles);
+        phase ^= 1ull << slot;
+        ++waited;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// consumers: horizontal sums, threshold, output (a4-a7)
+// ---------------------------------------------------------------------------
+template <int CIN, int RULE, int WM8>
+__device__ __forceinline__ void consume(const FusedParams &p, const Segment &sg, uint8_t *smem, uint32_t &nfb,
+                                        uint32_t &nties, volatile int *s_abort)
+{
+    const int PWP = p.PWP;
+    // o = (-r_lo) mod 16 and r_lo = W/2: the misalignments of the leaving
+    // (span column o + x) and entering (o + W + x) streams depend on W mod 8
+    constexpr int KO = (4 - ((WM8 >> 1) & 3)) & 3;
+    constexpr int KI = (KO + WM8) & 3;
+    const uint8_t *ring = smem + p.off_ring;
+    const uint32_t *cb = reinterpret_cast<const uint32_t *>(smem + p.off_cb);
+    const int q = threadIdx.x - NTP;
+    const int lane = q & 31, ii = q >> 5; // this warp's row within each chunk
+    const int W = p.W;
+    const bool active = lane * L < p.TW; // 256-wide strips leave lanes 16..31 idle
+    // centre pixels of this lane's 16 outputs start at span column lane*16 + o + r_lo (a multiple of 16)
+    const int fcol = active ? lane * L + p.o + p.r_lo : 0;
+    const int fpn = fcol / PWP;
+    const uint8_t *fbase = ring + (size_t)fpn * p.ring_rows * PWP + (fcol - fpn * PWP);
+    const int xg0 = sg.x0 + lane * L;
+    const bool xclip = xg0 < p.r_lo || xg0 + L - 1 + p.r_hi > p.w - 1; // some window of the lane leaves the image
+
+    int rc = (ii + p.r_lo) % p.ring_rows; // ring row of this warp's centre row in chunk k
+    for (int k = 0; k < sg.nk; ++k, rc = (rc + CH < p.ring_rows) ? rc + CH : rc + CH - p.ring_rows) {
+        const int b = k & 1;
+        bar_sync(BAR_FULL + b, NT);
+        const int rows_k = min(CH, sg.th_eff - k * CH);
+        if (ii < rows_k && !*s_abort) {
+            const int i = k * CH + ii;
+            const int y = sg.y0 + i;
+            const uint32_t *C1 = cb + (size_t)(2 * b) * CH * p.RSW + ii * p.RSW;
+            const uint32_t *C2 = C1 + (size_t)CH * p.RSW;
+            const int cw = lane * L + p.o; // leaving-stream start; entering = cw + W
+            const int ao = cw >> 2, ai = (cw + W) >> 2;
+
+            uint32_t d1[L], d2[L];
+            uint32_t a1 = 0, a2 = 0;
+            if (active) {
+                uint4 o1 = ld_group(C1, ao), o2 = ld_group(C2, ao);
+                uint4 i1 = ld_group(C1, ai), i2 = ld_group(C2, ai);
+#pragma unroll
+                for (int j = 0; j < L / 4; ++j) {
+                    uint4 o1n = make_uint4(0, 0, 0, 0), o2n = o1n, i1n = o1n, i2n = o1n;
+                    if (KO != 0 || j + 1 < L / 4) {
+                        o1n = ld_group(C1, ao + j + 1);
+                        o2n = ld_group(C2, ao + j + 1);
+                    }
+                    if (KI != 0 || j + 1 < L / 4) {
+                        i1n = ld_group(C1, ai + j + 1);
+                        i2n = ld_group(C2, ai + j + 1);
+                    }
+                    const uint32_t vo1[8] = {o1.x, o1.y, o1.z, o1.w, o1n.x, o1n.y, o1n.z, o1n.w};
+                    const uint32_t vo2[8] = {o2.x, o2.y, o2.z, o2.w, o2n.x, o2n.y, o2n.z, o2n.w};
+                    const uint32_t vi1[8] = {i1.x, i1.y, i1.z, i1.w, i1n.x, i1n.y, i1n.z, i1n.w};
+                    const uint32_t vi2[8] = {i2.x, i2.y, i2.z, i2.w, i2n.x, i2n.y, i2n.z, i2n.w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        d1[4 * j + e] = a1;
+                        d2[4 * j + e] = a2;
+                        a1 = a1 + vi1[e + KI] - vo1[e + KO];
+                        a2 = a2 + vi2[e + KI] - vo2[e + KO];
+                    }
+                    o1 = o1n;
+                    o2 = o2n;
+                    i1 = i1n;
+                    i2 = i2n;
+                }
+            } else {
+#pragma unroll
+                for (int t = 0; t < L; ++t)
+                    d1[t] = d2[t] = 0u;
+            }
+            // the window of the strip's first output: span columns [o, o + W)
+            uint32_t s1 = 0, s2 = 0;
+            for (int c = p.o + lane; c < p.o + W; c += 32) {
+                const int qc = cpos(c);
+                s1 += C1[qc];
+                s2 += C2[qc];
+            }
+            s1 = __reduce_add_sync(0xffffffffu, s1);
+            s2 = __reduce_add_sync(0xffffffffu, s2);
+            uint32_t x1 = a1, x2 = a2;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const uint32_t t1 = __shfl_up_sync(0xffffffffu, x1, off);
+                const uint32_t t2 = __shfl_up_sync(0xffffffffu, x2, off);
+                if (lane >= off) {
+                    x1 += t1;
+                    x2 += t2;
+                }
+            }
+            const uint32_t base1 = s1 + x1 - a1, base2 = s2 + x2 - a2;
+
+            const uint4 fv = *reinterpret_cast<const uint4 *>(fbase + (size_t)rc * PWP);
+            const uint32_t fw[4] = {fv.x, fv.y, fv.z, fv.w};
+            const bool yclip = (y < p.r_lo) || (y + p.r_hi > p.h - 1);
+            const bool lane_clip = active && xg0 < p.w && (yclip || xclip);
+            uint32_t outw[4];
+            bool amb = false;
+            if (!__any_sync(0xffffffffu, lane_clip)) {
+                // every window of the warp is W x W: shared constants
+                // n*S2 = n*base2 + n*d2 (mod 2^64, d2 taken as a signed offset)
+                const unsigned long long nb2 = (unsigned long long)p.nW * base2;
+#pragma unroll
+                for (int qq = 0; qq < 4; ++qq) {
+                    float dd[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int t = 4 * qq + e;
+                        const uint32_t S1 = base1 + d1[t];
+                        const unsigned long long V = nb2 + (unsigned long long)((long long)p.nW * (int)d2[t]) -
+                                                     (unsigned long long)S1 * S1;
+                        const float ff = __uint2float_rn(byte_dyn(fw[qq], e));
+                        dd[e] = filter_int<RULE>(ff, __uint2float_rn(S1), sqrt_approx(v_to_float(V)), p);
+                        amb = amb || (fabsf(dd[e]) < p.E);
+                    }
+                    // byte = 0xFF where d >= +0, 0x00 where d < 0 (sign bit replicated)
+                    const uint32_t lo = prmt(__float_as_uint(dd[0]), __float_as_uint(dd[1]), 0xFBu);
+                    const uint32_t hi = prmt(__float_as_uint(dd[2]), __float_as_uint(dd[3]), 0xFBu);
+                    outw[qq] = ~prmt(lo, hi, 0x5410u);
+                }
+            } else {
+                // border warp: each pixel with its own clipped count n = nr * nc
+                const int nr = min(y + p.r_hi, p.h - 1) - max(y - p.r_lo, 0) + 1;
+#pragma unroll
+                for (int qq = 0; qq < 4; ++qq) {
+                    float dd[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int t = 4 * qq + e;
+                        const int xg = xg0 + t;
+                        const int nc = min(xg + p.r_hi, p.w - 1) - max(xg - p.r_lo, 0) + 1;
+                        const uint32_t n = (uint32_t)(nr * nc);
+                        const uint32_t S1 = base1 + d1[t], S2 = base2 + d2[t];
+                        const unsigned long long V = (unsigned long long)n * S2 - (unsigned long long)S1 * S1;
+                        const float ff = __uint2float_rn(byte_dyn(fw[qq], e));
+                        const float invn = rcp_approx(__uint2float_rn(n));
+                        dd[e] = filter_n<RULE>(ff, __uint2float_rn(S1), sqrt_approx(v_to_float(V)), invn, p);
+                        amb = amb || (xg < p.w && fabsf(dd[e]) < p.E);
+                    }
+                    const uint32_t lo = prmt(__float_as_uint(dd[0]), __float_as_uint(dd[1]), 0xFBu);
+                    const uint32_t hi = prmt(__float_as_uint(dd[2]), __float_as_uint(dd[3]), 0xFBu);
+                    outw[qq] = ~prmt(lo, hi, 0x5410u);
+                }
+            }
+            if (amb && active) { // rare: a value inside the fp32 margin -> fp64 for those pixels
+                const int nr = min(y + p.r_hi, p.h - 1) - max(y - p.r_lo, 0) + 1;
+                for (int t = 0; t < L; ++t) {
+                    const int xg = xg0 + t;
+                    if (xg >= p.w)
+                        break;
+                    const int nc = min(xg + p.r_hi, p.w - 1) - max(xg - p.r_lo, 0) + 1;
+                    const uint32_t n = (uint32_t)(nr * nc);
+                    uint32_t S1 = base1, S2 = base2;
+#pragma unroll
+                    for (int u = 0; u < L; ++u) // register arrays: select, never index dynamically
+                        if (u == t) {
+                            S1 += d1[u];
+                            S2 += d2[u];
+                        }
+                    const uint32_t f = byte_dyn(fw[t >> 2], t & 3);
+                    const unsigned long long V = (unsigned long long)n * S2 - (unsigned long long)S1 * S1;
+                    const float sq = sqrt_approx(v_to_float(V));
+                    const float d = (n == p.nW)
+                                        ? filter_int<RULE>(__uint2float_rn(f), __uint2float_rn(S1), sq, p)
+                                        : filter_n<RULE>(__uint2float_rn(f), __uint2float_rn(S1), sq,
+                                                         rcp_approx(__uint2float_rn(n)), p);
+                    if (fabsf(d) < p.E) {
+                        const uint32_t r = decide_fp64<RULE>(f, n, S1, S2, p);
+                        ++nfb;
+                        nties += (r >> 9) & 1u;
+                        const int sh = 8 * (t & 3);
+                        outw[t >> 2] = (outw[t >> 2] & ~(0xffu << sh)) | ((r & 0xffu) << sh);
+                    }
+                }
+            }
+            if (active && xg0 < p.w) {
+                if (!p.packed) {
+                    uint8_t *drow = p.dst + (size_t)y * p.dst_pitch + xg0;
+                    if (p.vec_ok && xg0 + L <= p.w) {
+                        *reinterpret_cast<uint4 *>(drow) = make_uint4(outw[0], outw[1], outw[2], outw[3]);
+                    } else {
+                        for (int t = 0; t < L && xg0 + t < p.w; ++t)
+                            drow[t] = (uint8_t)byte_dyn(outw[t >> 2], t & 3);
+                    }
+                } else {
+                    uint32_t bits = 0; // bit t <-> pixel xg0 + t: the msb of each byte
+#pragma unroll
+                    for (int qq = 0; qq < 4; ++qq)
+                        bits |= ((((outw[qq] >> 7) & 0x01010101u) * 0x01020408u) >> 24) << (4 * qq);
+                    const int valid = p.w - xg0;
+                    if (valid < L)
+                        bits &= (1u << valid) - 1u;
+                    uint8_t *drow = p.dst + (size_t)y * p.dst_pitch + (xg0 >> 3);
+                    drow[0] = (uint8_t)(bits & 0xffu);
+                    if (valid > 8)
+                        drow[1] = (uint8_t)(bits >> 8);
+                }
+            }
+        }
+        if (k + 2 < sg.nk)
+            bar_arrive(BAR_EMPTY + b, NT);
+    }
 }
 
 template <int CIN, int RULE, int WM8>
@@ -181,383 +600,55 @@ __global__ void __launch_bounds__(NT, 1)
     fused_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ FusedParams p)
 {
     extern __shared__ __align__(128) uint8_t smem[];
-    constexpr int PWP = PanelWidth<CIN>::PWP;
-    constexpr int PWB = PWP * CIN;
-    // o = (-r_lo) mod 16 and r_lo = W/2, so the misalignments of the leaving
-    // (span column o + x) and entering (o + W + x) streams are fixed by W mod 8
-    constexpr int KO = (4 - ((WM8 >> 1) & 3)) & 3;
-    constexpr int KI = (KO + WM8) & 3;
-
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
-    uint8_t *ring = smem + p.off_ring;
-    uint8_t *stage = smem + p.off_stage;
-    uint32_t *cb1 = reinterpret_cast<uint32_t *>(smem + p.off_c1);
-    uint32_t *cb2 = reinterpret_cast<uint32_t *>(smem + p.off_c2);
-
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int CH = p.CH;
-    const int W = p.W;
-    const int D = (CH + W - 1) / CH; // chunks ahead of the current one that its outputs need
+    __shared__ int s_abort;
+    const int tid = threadIdx.x;
+    const bool producer = tid < NTP;
     const int nbar = CIN == 1 ? p.NS : p.NSS;
-    const uint32_t chunk_bytes = (uint32_t)(p.NPAN * CH * PWB);
-    const int ng = p.SWP >> 2;
-    const long long limit = p.timeout_cycles;
-
     if (tid == 0) {
+        uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
         for (int i = 0; i < nbar; ++i)
             mbar_init(&bars[i], 1);
         fence_mbar_init();
         fence_proxy_async_smem();
         prefetch_tmap(&tmap);
+        s_abort = 0;
     }
     __syncthreads();
 
-    uint64_t phase = 0; // bit i: parity to wait for next on barrier i (uniform)
+    uint64_t phase = 0; // producers: bit i = parity to wait for next on barrier i
     uint32_t nfb = 0, nties = 0;
-    bool ok = true;
-
-    // column-owner geometry (a3): 4 consecutive span columns per thread
-    const bool owner = tid < ng;
-    const int gcol = tid * 4;
-    const int gpn = gcol / PWP, gip = gcol - gpn * PWP;
-    const int gpos = cpos(gcol);
-
-    // centre-pixel geometry (a6): the lane's 16 outputs start at span column
-    // lane*16 + o + r_lo, a multiple of 16 because o + r_lo = 0 (mod 16)
-    // (a strip may be 256 wide for very large W: lanes 16..31 then only join the shuffles)
-    const bool active = lane * L < p.TW;
-    const int fcol = active ? lane * L + p.o + p.r_lo : 0;
-    const int fpn = fcol / PWP;
-    const int foff = fpn * p.ring_rows * PWP + (fcol - fpn * PWP);
-
     const long long T = (long long)p.tiles_x * p.h;
     const long long L0 = T * blockIdx.x / gridDim.x, L1 = T * (blockIdx.x + 1) / gridDim.x;
-
-    for (long long cur = L0; cur < L1 && ok;) {
+    for (long long cur = L0; cur < L1;) {
+        Segment sg;
         const int tx = (int)(cur / p.h);
-        const int y0 = (int)(cur - (long long)tx * p.h);
-        const int th_eff = (int)min((long long)(p.h - y0), L1 - cur);
-        cur += th_eff;
-
-        const int x0 = tx * p.TW;
-        const int xs = x0 - p.r_lo - p.o; // span start column (multiple of 16, may be < 0)
-        const int ys = y0 - p.r_lo;       // first input row (may be < 0: zero-filled)
-        const int nchk = (th_eff + W - 1 + CH - 1) / CH;
-        const bool xin = (x0 - p.r_lo >= 0) && (x0 + p.TW - 1 + p.r_hi <= p.w - 1);
-
-        int issued = 0, waited = 0;
-        auto issue = [&](int j) {
-            const int slot = j % nbar;
-            uint64_t *bar = &bars[slot];
-            mbar_arrive_expect_tx(bar, chunk_bytes);
-            for (int pn = 0; pn < p.NPAN; ++pn) {
-                uint8_t *dst = (CIN == 1) ? ring + (size_t)pn * p.ring_rows * PWP + (size_t)slot * CH * PWP
-                                          : stage + ((size_t)slot * p.NPAN + pn) * CH * PWB;
-                tma_load_2d(dst, &tmap, (xs + pn * PWP) * CIN, ys + j * CH, bar);
-            }
-        };
-        auto wait_next = [&]() -> bool { // wait for chunk `waited` and advance
-            const int slot = waited % nbar;
-            const bool r = mbar_wait_bounded(&bars[slot], (uint32_t)((phase >> slot) & 1ull), limit);
-            phase ^= 1ull << slot;
-            ++waited;
-            return r;
-        };
-        auto convert = [&](int j) { // RGB staging slot -> gray ring slot (a2), column group = thread
-            if (!owner)
-                return;
-            const int sslot = j % p.NSS, rslot = j % p.NS;
-            const uint8_t *src = stage + ((size_t)sslot * p.NPAN + gpn) * CH * PWB + 3 * gip;
-            uint8_t *dst = ring + (size_t)gpn * p.ring_rows * PWP + (size_t)rslot * CH * PWP + gip;
-            for (int r = 0; r < CH; ++r) {
-                const uint32_t *s32 = reinterpret_cast<const uint32_t *>(src + r * PWB);
-                *reinterpret_cast<uint32_t *>(dst + r * PWP) = gray4(s32[0], s32[1], s32[2]);
-            }
-        };
-        // Make chunks [0, upto] available as gray rows in the ring.
-        auto acquire = [&](int upto) -> bool {
-            bool good = true;
-            if constexpr (CIN == 1) {
-                while (waited <= upto)
-                    good &= wait_next();
-                return !__syncthreads_or(!good);
-            } else {
-                while (waited <= upto) {
-                    const int j = waited;
-                    good &= wait_next();
-                    if (__syncthreads_or(!good))
-                        return false;
-                    convert(j);
-                    __syncthreads();
-                    if (issued < nchk) {
-                        if (tid == 0)
-                            issue(issued);
-                        ++issued;
-                    }
-                }
-                return true;
-            }
-        };
-
-        // prologue: gray fills chunks 0..D (the ring has D+2 slots); RGB fills its staging slots
-        {
-            const int pre = CIN == 1 ? min(nchk, D + 1) : min(nchk, p.NSS);
-            if (tid == 0)
-                for (int j = 0; j < pre; ++j)
-                    issue(j);
-            issued = pre;
-        }
-        uint32_t c1[4] = {0u, 0u, 0u, 0u}, c2[4] = {0u, 0u, 0u, 0u};
-        const uint8_t *gbase = ring + (size_t)gpn * p.ring_rows * PWP + gip;
-
-        // warm-up: column sums over input rows 0 .. W-1 (the window of output row 0)
-        ok = acquire(min(D - 1, nchk - 1));
-        if (ok && owner) {
-            int rr = 0;
-            for (int r = 0; r < W; ++r) {
-                const uint32_t v = *reinterpret_cast<const uint32_t *>(gbase + (size_t)rr * PWP);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const uint32_t b = byte_of(v, j);
-                    c1[j] += b;
-                    c2[j] += b * b;
-                }
-                if (++rr == p.ring_rows)
-                    rr = 0;
-            }
-        }
-        int rr_in = W % p.ring_rows, rr_out = 0, rr_ctr = p.r_lo % p.ring_rows;
-
-        for (int k = 0; ok && k * CH < th_eff; ++k) {
-            if (CIN == 1 && issued < nchk) { // prefetch the chunk after the ones this step needs
-                if (tid == 0)
-                    issue(issued);
-                ++issued;
-            }
-            if (!acquire(min(k + D, nchk - 1))) {
-                ok = false;
-                break;
-            }
-            const int rows_k = min(CH, th_eff - k * CH);
-
-            // ---- a3: publish column sums of row i, then slide to row i+1 ------------
-            if (owner) {
-                for (int ii = 0; ii < rows_k; ++ii) {
-                    *reinterpret_cast<uint4 *>(cb1 + ii * p.RSW + gpos) = make_uint4(c1[0], c1[1], c1[2], c1[3]);
-                    *reinterpret_cast<uint4 *>(cb2 + ii * p.RSW + gpos) = make_uint4(c2[0], c2[1], c2[2], c2[3]);
-                    if (k * CH + ii + 1 < th_eff) {
-                        const uint32_t vin = *reinterpret_cast<const uint32_t *>(gbase + (size_t)rr_in * PWP);
-                        const uint32_t vout = *reinterpret_cast<const uint32_t *>(gbase + (size_t)rr_out * PWP);
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            const uint32_t bi = byte_of(vin, j), bo = byte_of(vout, j);
-                            c1[j] = c1[j] + bi - bo;
-                            c2[j] = c2[j] + bi * bi - bo * bo;
-                        }
-                    }
-                    if (++rr_in == p.ring_rows)
-                        rr_in = 0;
-                    if (++rr_out == p.ring_rows)
-                        rr_out = 0;
-                }
-            } else {
-                rr_in = (rr_in + rows_k) % p.ring_rows;
-                rr_out = (rr_out + rows_k) % p.ring_rows;
-            }
-            __syncthreads();
-
-            // ---- a4-a7: one warp per output row --------------------------------------
-            for (int ii = warp; ii < rows_k; ii += NWARP) {
-                const int i = k * CH + ii;
-                const int y = y0 + i;
-                const uint32_t *C1 = cb1 + ii * p.RSW;
-                const uint32_t *C2 = cb2 + ii * p.RSW;
-                const int cw = lane * L + p.o; // leaving-stream start; entering = cw + W
-                const int ao = cw >> 2, ai = (cw + W) >> 2;
-
-                uint32_t d1[L], d2[L];
-                uint32_t a1 = 0, a2 = 0;
-                if (active) {
-                    uint4 o1 = ld_group(C1, ao), o2 = ld_group(C2, ao);
-                    uint4 i1 = ld_group(C1, ai), i2 = ld_group(C2, ai);
-#pragma unroll
-                    for (int j = 0; j < L / 4; ++j) {
-                        uint4 o1n = make_uint4(0, 0, 0, 0), o2n = o1n, i1n = o1n, i2n = o1n;
-                        if (KO != 0 || j + 1 < L / 4) {
-                            o1n = ld_group(C1, ao + j + 1);
-                            o2n = ld_group(C2, ao + j + 1);
-                        }
-                        if (KI != 0 || j + 1 < L / 4) {
-                            i1n = ld_group(C1, ai + j + 1);
-                            i2n = ld_group(C2, ai + j + 1);
-                        }
-                        const uint32_t vo1[8] = {o1.x, o1.y, o1.z, o1.w, o1n.x, o1n.y, o1n.z, o1n.w};
-                        const uint32_t vo2[8] = {o2.x, o2.y, o2.z, o2.w, o2n.x, o2n.y, o2n.z, o2n.w};
-                        const uint32_t vi1[8] = {i1.x, i1.y, i1.z, i1.w, i1n.x, i1n.y, i1n.z, i1n.w};
-                        const uint32_t vi2[8] = {i2.x, i2.y, i2.z, i2.w, i2n.x, i2n.y, i2n.z, i2n.w};
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            d1[4 * j + e] = a1;
-                            d2[4 * j + e] = a2;
-                            a1 = a1 + vi1[e + KI] - vo1[e + KO];
-                            a2 = a2 + vi2[e + KI] - vo2[e + KO];
-                        }
-                        o1 = o1n;
-                        o2 = o2n;
-                        i1 = i1n;
-                        i2 = i2n;
-                    }
-                } else {
-#pragma unroll
-                    for (int t = 0; t < L; ++t)
-                        d1[t] = d2[t] = 0;
-                }
-                // window of the strip's first output: span columns [o, o + W)
-                uint32_t s1 = 0, s2 = 0;
-                for (int c = p.o + lane; c < p.o + W; c += 32) {
-                    const int q = cpos(c);
-                    s1 += C1[q];
-                    s2 += C2[q];
-                }
-#pragma unroll
-                for (int off = 16; off; off >>= 1) {
-                    s1 += __shfl_xor_sync(0xffffffffu, s1, off);
-                    s2 += __shfl_xor_sync(0xffffffffu, s2, off);
-                }
-                uint32_t i1s = a1, i2s = a2;
-#pragma unroll
-                for (int off = 1; off < 32; off <<= 1) {
-                    const uint32_t t1 = __shfl_up_sync(0xffffffffu, i1s, off);
-                    const uint32_t t2 = __shfl_up_sync(0xffffffffu, i2s, off);
-                    if (lane >= off) {
-                        i1s += t1;
-                        i2s += t2;
-                    }
-                }
-                const uint32_t base1 = s1 + i1s - a1, base2 = s2 + i2s - a2;
-
-                int rc = rr_ctr + ii;
-                if (rc >= p.ring_rows)
-                    rc -= p.ring_rows;
-                const uint4 fv = *reinterpret_cast<const uint4 *>(ring + foff + rc * PWP);
-                const uint32_t fw[4] = {fv.x, fv.y, fv.z, fv.w};
-
-                const int xg0 = x0 + lane * L;
-                // a window is clipped when it leaves the image on any side
-                const bool yclip = (y < p.r_lo) || (y + p.r_hi > p.h - 1);
-                bool amb = yclip || (!xin && (xg0 < p.r_lo || xg0 + L - 1 + p.r_hi > p.w - 1));
-                uint32_t outw[4];
-                auto fast_block = [&](auto magic) {
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        float dd[4];
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const int t = 4 * q + e;
-                            const uint32_t S1 = base1 + d1[t], S2 = base2 + d2[t];
-                            const unsigned long long V = (unsigned long long)p.nW * S2 -
-                                                         (unsigned long long)S1 * S1;
-                            const float sq = sqrt_approx(v_to_float(V));
-                            const float S1f = decltype(magic)::value ? u23_to_float(S1) : __uint2float_rn(S1);
-                            float ff;
-                            if (e == 0)
-                                ff = byte_to_float<0>(fw[q]);
-                            else if (e == 1)
-                                ff = byte_to_float<1>(fw[q]);
-                            else if (e == 2)
-                                ff = byte_to_float<2>(fw[q]);
-                            else
-                                ff = byte_to_float<3>(fw[q]);
-                            dd[e] = filter_d<RULE>(ff, S1f, sq, p);
-                            amb = amb || (fabsf(dd[e]) < p.E);
-                        }
-                        // byte = 0xFF where d >= +0, 0x00 where d < 0 (sign bit replicated)
-                        const uint32_t lo = prmt(__float_as_uint(dd[0]), __float_as_uint(dd[1]), 0xFBu);
-                        const uint32_t hi = prmt(__float_as_uint(dd[2]), __float_as_uint(dd[3]), 0xFBu);
-                        outw[q] = ~prmt(lo, hi, 0x5410u);
-                    }
-                };
-                if (p.s1_magic)
-                    fast_block(std::true_type{});
-                else
-                    fast_block(std::false_type{});
-
-                if (!active)
-                    continue; // (after the warp-wide shuffles above)
-                if (amb) { // rare: clipped windows, or values inside the fp32 margin
-#pragma unroll
-                    for (int t = 0; t < L; ++t) {
-                        const int xg = xg0 + t;
-                        if (xg >= p.w)
-                            continue;
-                        const uint32_t S1 = base1 + d1[t], S2 = base2 + d2[t];
-                        const uint32_t f = byte_of(fw[t >> 2], t & 3);
-                        bool need = yclip || xg < p.r_lo || xg + p.r_hi > p.w - 1;
-                        if (!need) {
-                            const unsigned long long V = (unsigned long long)p.nW * S2 -
-                                                         (unsigned long long)S1 * S1;
-                            const float d = filter_d<RULE>(__uint2float_rn(f), __uint2float_rn(S1),
-                                                           sqrt_approx(v_to_float(V)), p);
-                            need = fabsf(d) < p.E;
-                        }
-                        if (need) {
-                            const uint32_t r = slow_decide<RULE>(f, S1, S2, y, xg, p);
-                            nfb += (r >> 8) & 1u;
-                            nties += (r >> 9) & 1u;
-                            const int sh = 8 * (t & 3);
-                            outw[t >> 2] = (outw[t >> 2] & ~(0xffu << sh)) | ((r & 0xffu) << sh);
-                        }
-                    }
-                }
-
-                if (!p.packed) {
-                    uint8_t *drow = p.dst + (size_t)y * p.dst_pitch + xg0;
-                    if (p.vec_ok && xg0 + L <= p.w) {
-                        *reinterpret_cast<uint4 *>(drow) = make_uint4(outw[0], outw[1], outw[2], outw[3]);
-                    } else {
-#pragma unroll
-                        for (int t = 0; t < L; ++t)
-                            if (xg0 + t < p.w)
-                                drow[t] = (uint8_t)byte_of(outw[t >> 2], t & 3);
-                    }
-                } else {
-                    // gather the msb of each byte: bit t <-> pixel xg0 + t
-                    uint32_t bits = 0;
-#pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        bits |= ((((outw[q] >> 7) & 0x01010101u) * 0x01020408u) >> 24) << (4 * q);
-                    const int valid = p.w - xg0; // pixels of this lane inside the image
-                    if (valid < L)
-                        bits &= (valid <= 0) ? 0u : ((1u << valid) - 1u);
-                    uint8_t *drow = p.dst + (size_t)y * p.dst_pitch + (xg0 >> 3);
-                    const int nbytes_row = (p.w + 7) >> 3;
-                    if ((xg0 >> 3) < nbytes_row)
-                        drow[0] = (uint8_t)(bits & 0xffu);
-                    if ((xg0 >> 3) + 1 < nbytes_row)
-                        drow[1] = (uint8_t)(bits >> 8);
-                }
-            }
-            rr_ctr = (rr_ctr + rows_k) % p.ring_rows;
-            __syncthreads();
-        }
-        if (!ok) {
-            // give up: drain this segment's outstanding copies (bounded) before leaving
-            while (waited < issued)
-                wait_next();
-        }
+        sg.y0 = (int)(cur - (long long)tx * p.h);
+        sg.th_eff = (int)min((long long)(p.h - sg.y0), L1 - cur);
+        cur += sg.th_eff;
+        sg.x0 = tx * p.TW;
+        sg.xs = sg.x0 - p.r_lo - p.o; // span start column (multiple of 16, may be < 0)
+        sg.ys = sg.y0 - p.r_lo;       // first input row (may be < 0: zero-filled)
+        sg.nchk = (sg.th_eff + p.W - 1 + CH - 1) / CH;
+        sg.nk = (sg.th_eff + CH - 1) / CH;
+        if (producer)
+            produce<CIN>(&tmap, p, sg, smem, phase, &s_abort);
+        else
+            consume<CIN, RULE, WM8>(p, sg, smem, nfb, nties, &s_abort);
+        __syncthreads(); // the next segment reuses the ring from slot 0
+        if (s_abort)
+            break;
     }
 
-    // statistics: one atomic per warp
 #pragma unroll
     for (int off = 16; off; off >>= 1) {
         nfb += __shfl_xor_sync(0xffffffffu, nfb, off);
         nties += __shfl_xor_sync(0xffffffffu, nties, off);
     }
-    if (lane == 0 && p.stats && (nfb | nties)) {
+    if ((tid & 31) == 0 && p.stats && (nfb | nties)) {
         atomicAdd(&p.stats[BNZ_STATS_FALLBACKS], (unsigned long long)nfb);
         atomicAdd(&p.stats[BNZ_STATS_TIES], (unsigned long long)nties);
     }
-    if (!ok && tid == 0) {
+    if (s_abort && tid == 0) {
         if (p.stats)
             atomicAdd(&p.stats[BNZ_STATS_TIMEOUTS], 1ull);
         atomicAdd(p.err_flag, 1u);
@@ -589,11 +680,10 @@ const void *kernel_for(int ch, int rule, int W)
 
 size_t round128(size_t v) { return (v + 127) & ~size_t(127); }
 
-// Shared-memory layout for one (CH, NSS) choice; false if it does not fit.
-bool layout(int ch, int W, int tw, int CH, int NSS, FusedPlan *pl)
+// Shared-memory layout for one (strip width, chunk, staging) choice.
+bool layout(int ch, int W, int tw, int PWP, int CH, int NSS, FusedPlan *pl)
 {
     const int r_lo = W / 2;
-    const int PWP = ch == 1 ? PanelWidth<1>::PWP : PanelWidth<3>::PWP;
     const int PWB = PWP * ch;
     pl->TW = tw;
     pl->CH = CH;
@@ -603,12 +693,13 @@ bool layout(int ch, int W, int tw, int CH, int NSS, FusedPlan *pl)
     const int need = pl->o + tw + W + 4;
     pl->NPAN = (need + PWP - 1) / PWP;
     pl->SWP = pl->NPAN * PWP;
-    if (pl->SWP / 4 > NT)
+    if (pl->SWP / 4 > NTP)
         return false;
-    // cpos() of the last group read: (SWP/4 + 1) groups of 4 words, 4 pad words per 4 groups
     pl->RSW = ((pl->SWP + 4) / 16 + 1) * 20;
     const int D = (CH + W - 1) / CH;
-    pl->NS = D + 2;
+    // ring: chunks in use (D + 1), one more because producers run a chunk ahead
+    // of the consumers' centre rows, and for gray the chunks loaded ahead
+    pl->NS = D + 2 + (ch == 1 ? kLeadGray : 1);
     pl->NSS = ch == 3 ? NSS : 0;
     pl->ring_rows = pl->NS * CH;
     const int nbar = std::max(pl->NS, pl->NSS);
@@ -619,27 +710,27 @@ bool layout(int ch, int W, int tw, int CH, int NSS, FusedPlan *pl)
     off = round128(off + (size_t)pl->NPAN * pl->ring_rows * PWP);
     pl->off_stage = (uint32_t)off;
     off = round128(off + (size_t)pl->NSS * pl->NPAN * CH * PWB);
-    pl->off_c1 = (uint32_t)off;
-    off = round128(off + (size_t)CH * pl->RSW * 4);
-    pl->off_c2 = (uint32_t)off;
-    off += (size_t)CH * pl->RSW * 4;
+    pl->off_cb = (uint32_t)off;
+    off += (size_t)4 * CH * pl->RSW * 4; // 2 buffers x {c1, c2}
     pl->smem = off;
     return off <= (size_t)MAX_DYN_SMEM;
 }
 
 } // namespace
 
-// Error bound of the fp32 filter, u = 2^-24, e = relative error of sqrt.approx;
-// V is converted with relative error <= 2u, so sqrt(V) carries <= u + e:
-//   Sauvola, d32 = f - S1 * (a + b * sqrt(V)) with a ~ (1-k)/n, b ~ k/(R n^2)
-//   rounded with relative error <= 3u (a) and <= 5u (b) on every path:
-//     |d32 - (f - t)| <= 4u T + m |k| (s/R) (7u + e) + u (255 + T),
-//     T = m (|1-k| + |k| s/R) >= |t|;
-//   Niblack, d32 = f - S1/n - (k/n) sqrt(V):
-//     |d32 - (f - t)| <= u (255 + 510 + 510 + |k| s_max) + |k| s (4u + e).
-// With m <= 255 and s <= 127.5 this gives Emax; E = 2 Emax + 1e-6 also covers
-// the fp64 definition's own rounding (< 1e-12) and keeps every pixel with
-// |f - t| < 1e-9 inside the margin, so ties are always decided in fp64.
+// Error bound of the fp32 filter (u = 2^-24, e = relative error of sqrt.approx,
+// r = relative error of rcp.approx = 4u).  V reaches fp32 with relative error
+// <= 2u, so sqrt(V) carries <= u + e.
+//   Sauvola, d32 = f - S1 * (a + b * sqrt(V)), a ~ (1-k)/n, b ~ k/(R n^2):
+//     constants from the host carry <= u; per-pixel ones from rcp carry
+//     a: <= r + 2u = 6u, b: <= 2r + 3u = 11u;
+//     |d32 - (f - t)| <= 6u m|1-k| + m|k| (s/R) (12u + e) + u T + u (255 + T),
+//     T = m (|1-k| + |k| s/R) >= |t|.
+//   Niblack, d32 = f - S1 * invn - (k invn) sqrt(V), invn ~ 1/n within 4u:
+//     |d32 - (f - t)| <= 4u m + 510 u + |k| s (7u + e) + u (510 + |k| s).
+// With m <= 255 and s <= 127.5 this gives Emax; E = 2 Emax + 1e-6, which also
+// covers the fp64 definition's own rounding (< 1e-12) and keeps every pixel
+// with |f - t| < 1e-9 inside the margin, so ties are decided in fp64.
 float decision_margin(int rule, double k, double R)
 {
     const double u = 1.0 / 16777216.0;
@@ -649,9 +740,9 @@ float decision_margin(int rule, double k, double R)
     double em;
     if (rule == BNZ_SAUVOLA) {
         const double T = m * (std::fabs(1.0 - k) + ak * smax / R);
-        em = 4.0 * u * T + m * ak * (smax / R) * (7.0 * u + e) + u * (255.0 + T);
+        em = 6.0 * u * m * std::fabs(1.0 - k) + m * ak * (smax / R) * (12.0 * u + e) + u * T + u * (255.0 + T);
     } else {
-        em = u * (255.0 + 510.0 + 510.0 + ak * smax) + ak * smax * (4.0 * u + e);
+        em = 4.0 * u * m + u * 510.0 + ak * smax * (7.0 * u + e) + u * (510.0 + ak * smax);
     }
     double E = 2.0 * em + 1e-6;
     if (!(E < 1e30))
@@ -667,19 +758,22 @@ int plan_fused(int h, int w, int ch, int W, const bnz_tile *tile, FusedPlan *pl)
         return rc;
     const int want_tw = tile ? tile->tile_w : 0;
     const int want_ch = tile && tile->chunk ? tile->chunk : 8;
-    if (want_ch != 8 && want_ch != 16)
-        return fail(BNZ_EINVAL, "bnz_tile.chunk must be 0, 8 or 16 (got %d)", want_ch);
-    if (want_tw && want_tw != TW && want_tw != TW / 2)
-        return fail(BNZ_EINVAL, "bnz_tile.tile_w must be 0, %d or %d (got %d)", TW / 2, TW, want_tw);
+    if (want_ch != 8)
+        return fail(BNZ_EINVAL, "bnz_tile.chunk must be 0 or 8 (got %d)", want_ch);
+    if (want_tw && want_tw != TW && want_tw != TW / 2 && want_tw != TW / 4)
+        return fail(BNZ_EINVAL, "bnz_tile.tile_w must be 0, 128, 256 or 512 (got %d)", want_tw);
+    // widest strip first (least halo work), then narrower panels, then narrower strips
+    const int pw[2] = {ch == 1 ? 128 : 80, ch == 1 ? 64 : 80};
     bool found = false;
-    for (int tw = TW; tw >= TW / 2 && !found; tw /= 2) {
+    for (int tw = TW; tw >= TW / 4 && !found; tw /= 2) {
         if (want_tw && tw != want_tw)
             continue;
-        for (int nss = 3; nss >= 2 && !found; --nss)
-            found = layout(ch, W, tw, want_ch, nss, pl);
+        for (int pi = 0; pi < 2 && !found; ++pi)
+            for (int nss = 3; nss >= 2 && !found; --nss)
+                found = layout(ch, W, tw, pw[pi], want_ch, nss, pl);
     }
     if (!found)
-        return fail(BNZ_EINVAL, "no tile shape fits shared memory for W=%d, chunk=%d", W, want_ch);
+        return fail(BNZ_EINVAL, "no tile shape fits shared memory for W=%d", W);
     pl->tiles_x = (w + pl->TW - 1) / pl->TW;
     int occ = 1;
     const void *fn = kernel_for(ch, BNZ_SAUVOLA, W);
@@ -738,11 +832,11 @@ int launch_fused(const uint8_t *d_src, size_t src_pitch, int h, int w, int ch, i
     p.tiles_x = pl.tiles_x;
     p.off_ring = pl.off_ring;
     p.off_stage = pl.off_stage;
-    p.off_c1 = pl.off_c1;
-    p.off_c2 = pl.off_c2;
+    p.off_cb = pl.off_cb;
+    p.PWP = pl.PWP;
     p.packed = packed ? 1 : 0;
     p.vec_ok = ((reinterpret_cast<uintptr_t>(d_dst) | dst_pitch) & 15u) == 0 ? 1 : 0;
-    p.s1_magic = (long long)W * W * 255 < (1ll << 23) ? 1 : 0;
+    p.s1_magic = 0;
     p.nW = (uint32_t)(W * W);
     p.k = k;
     p.R = R;

@@ -26,7 +26,7 @@ int device_sm_count(int *sms);
 // Shape of one launch of the fused kernel (host-side plan).
 struct FusedPlan {
     int TW, CH;     // strip width (32 lanes x 16 outputs), rows per TMA chunk
-    int NS;         // ring slots (chunks) of gray rows in shared memory
+    int NS;         // ring slots (chunks) of gray rows in shared memory (D + 3)
     int NSS;        // staging slots for RGB chunks (0 for gray)
     int PWP;        // panel width in pixels (one TMA box per panel per chunk)
     int NPAN, SWP;  // panels per span, span width in pixels
@@ -36,7 +36,7 @@ struct FusedPlan {
     int tiles_x;    // strips across the image
     int grid;       // persistent CTAs
     int rows_per_cta;
-    uint32_t off_ring, off_stage, off_c1, off_c2;
+    uint32_t off_ring, off_stage, off_cb; // column sums: 2 buffers x {c1, c2} x CH rows x RSW words
     size_t smem;
 };
 
@@ -46,8 +46,8 @@ struct FusedParams {
     unsigned long long *stats;
     unsigned int *err_flag; // library-owned device word, counts CTAs that gave up
     int h, w, W, r_lo, r_hi, o;
-    int TW, CH, NS, NSS, NPAN, SWP, RSW, ring_rows, tiles_x;
-    uint32_t off_ring, off_stage, off_c1, off_c2;
+    int TW, CH, NS, NSS, PWP, NPAN, SWP, RSW, ring_rows, tiles_x;
+    uint32_t off_ring, off_stage, off_cb;
     int packed;     // 1: one bit per pixel
     int vec_ok;     // dst and dst_pitch 16-byte aligned
     int s1_magic;   // S1 < 2^23 for every window: exact int->float by bit tricks
@@ -57,7 +57,7 @@ struct FusedParams {
     //   Sauvola d = f - S1 * (omkn + kRn2 * sqrt(V)),  omkn = (1-k)/n, kRn2 = k/(R n^2)
     //   Niblack d = f - S1 * invn - kn * sqrt(V),      invn = 1/n,     kn = k/n
     float omkn, kRn2, invn, kn;
-    float kf, omk, kR; // k, 1-k, k/R for clipped windows
+    float kf, omk, kR; // k, 1-k, k/R for windows with a per-pixel n
     float E;           // proven bound on |d32 - (f - t)|, with safety factor
     long long timeout_cycles;
 };
@@ -70,8 +70,11 @@ int launch_fused(const uint8_t *d_src, size_t src_pitch, int h, int w, int ch, i
 // Library-owned per-device error word (allocated on first use).
 int device_err_flag(unsigned int **flag);
 
-// Relative error bound assumed for sqrt.approx.f32 (checked on the device by the tests).
+// Relative error bounds assumed for sqrt.approx.f32 (on [1, 2^48)) and
+// rcp.approx.f32 (on the integers 1..65025); both are measured on the device
+// by bnz_selftest_approx in the tests.
 constexpr double kSqrtApproxRelErr = 1.0 / (1 << 21);
+constexpr double kRcpApproxRelErr = 1.0 / (1 << 22);
 
 // fp32 decision margin E (see fused.cu for the derivation).
 float decision_margin(int rule, double k, double R);

@@ -1,5 +1,6 @@
-// selftest.cu -- device check of the one hardware approximation the fused
-// kernel's error bound relies on: the relative error of sqrt.approx.f32.
+// selftest.cu -- device checks of the hardware approximations the fused
+// kernel's error bound relies on: the relative errors of sqrt.approx.f32 and
+// rcp.approx.f32.
 #include <cstring>
 
 #include "internal.h"
@@ -25,8 +26,52 @@ __global__ void sqrt_approx_err_kernel(uint32_t first_bits, uint64_t count, unsi
         atomicMax(max_err_bits, __float_as_uint(worst)); // non-negative floats order like their bits
 }
 
+__global__ void rcp_approx_err_kernel(uint32_t n_lo, uint32_t n_hi, unsigned int *max_err_bits)
+{
+    float worst = 0.0f;
+    for (uint32_t n = n_lo + blockIdx.x * blockDim.x + threadIdx.x; n < n_hi; n += gridDim.x * blockDim.x) {
+        const float x = __uint2float_rn(n); // exact for n < 2^24
+        float a;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(a) : "f"(x));
+        const float r = __frcp_rn(x); // correctly rounded 1/n
+        worst = fmaxf(worst, __fdiv_rn(fabsf(a - r), r));
+    }
+    for (int off = 16; off; off >>= 1)
+        worst = fmaxf(worst, __shfl_xor_sync(0xffffffffu, worst, off));
+    if ((threadIdx.x & 31) == 0)
+        atomicMax(max_err_bits, __float_as_uint(worst));
+}
+
 } // namespace
 } // namespace bnz
+
+extern "C" BNZ_API int bnz_selftest_rcp_approx(unsigned int n_lo, unsigned int n_hi, double *max_rel_err)
+{
+    using namespace bnz;
+    if (!max_rel_err || n_lo < 1 || n_hi <= n_lo || n_hi > (1u << 24))
+        return fail(BNZ_EINVAL, "need 1 <= n_lo < n_hi <= 2^24 and a result pointer");
+    unsigned int *d = nullptr;
+    cudaError_t e = cudaMalloc(&d, sizeof(unsigned int));
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaMalloc(selftest)");
+    unsigned int h = 0;
+    do {
+        if ((e = cudaMemset(d, 0, sizeof(unsigned int))) != cudaSuccess)
+            break;
+        rcp_approx_err_kernel<<<304, 256>>>(n_lo, n_hi, d);
+        if ((e = cudaGetLastError()) != cudaSuccess)
+            break;
+        if ((e = cudaMemcpy(&h, d, sizeof h, cudaMemcpyDeviceToHost)) != cudaSuccess)
+            break;
+    } while (0);
+    cudaFree(d);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "rcp.approx self-test");
+    float f;
+    memcpy(&f, &h, 4);
+    *max_rel_err = (double)f * (1.0 + 1e-6) + 1.0 / 16777216.0; // bound vs the exact reciprocal
+    return BNZ_OK;
+}
 
 extern "C" BNZ_API int bnz_selftest_sqrt_approx(float lo, float hi, double *max_rel_err)
 {

@@ -120,8 +120,8 @@ def test_other_parameters(bnz):
 
 def test_explicit_tile_shapes_agree(bnz):
     img = synth.page(900, 1500, 10, synth.DOC, 1)
-    for tw in (0, 256, 512):
-        for chunk in (8, 16):
+    for tw in (0, 128, 256, 512):
+        for chunk in (0, 8):
             for th in (0, 7, 50):
                 tile = bnz.bnz_tile(tw, th, chunk, 0)
                 check(bnz, img, 45, "sauvola", 0.5, tile=tile)
@@ -164,3 +164,12 @@ def test_sqrt_approx_error_within_margin_assumption(bnz):
     rc = bnz.load().bnz_selftest_sqrt_approx(1.0, float(2 ** 44), ctypes.byref(err))
     assert rc == 0, bnz.bnz_last_error()
     assert 0.0 < err.value <= 2.0 ** -21, err.value
+
+
+def test_rcp_approx_error_within_margin_assumption(bnz):
+    """Clipped windows use rcp.approx.f32 for 1/n; the margin assumes <= 2^-22 on n = 1..65025."""
+    import ctypes
+    err = ctypes.c_double(0.0)
+    rc = bnz.load().bnz_selftest_rcp_approx(1, 65026, ctypes.byref(err))
+    assert rc == 0, bnz.bnz_last_error()
+    assert 0.0 < err.value <= 2.0 ** -22, err.value
