@@ -122,6 +122,31 @@ BNZ_API int bnz_binarize_dev(const uint8_t *d_src, size_t src_pitch, int height,
                      int rule, double k, double R, uint8_t *d_dst, size_t dst_pitch, int packed,
                      const bnz_tile *tile, void *stream, unsigned long long *d_stats);
 
+/* ---- integral-image comparison variant ------------------------------------
+ * The O(N^2) method with summed-area tables that Sec. 1 cites (Shafait et
+ * al.) and Sec. 3.3 charges 12 S_z bytes of memory: two (h+1) x (w+1) int64
+ * tables of f and f^2 (int64 for both: sums of f over a 16384^2 page exceed
+ * 2^32), then four corner lookups per pixel and the same Eq. 3 decision as
+ * the fused path, so the outputs are identical.  The caller provides the
+ * scratch (device memory, 32-byte aligned, at least
+ * bnz_integral_scratch_bytes(height, width) bytes); height <= 65535. */
+
+/* Scratch bytes the integral-image variant needs (0 for bad sizes). */
+BNZ_API size_t bnz_integral_scratch_bytes(int height, int width);
+
+/* Binarize through the integral images; arguments as bnz_binarize_dev plus
+ * the scratch.  Asynchronous on `stream`. */
+BNZ_API int bnz_binarize_integral_dev(const uint8_t *d_src, size_t src_pitch, int height, int width, int channels,
+                                      int W, int rule, double k, double R, uint8_t *d_dst, size_t dst_pitch,
+                                      int packed, void *d_scratch, size_t scratch_bytes, void *stream,
+                                      unsigned long long *d_stats);
+
+/* Only build the tables: I1 (sum of f over rows < y, columns < x) at
+ * d_scratch and I2 (same for f^2) right after it, each (height+1) rows of
+ * *ld_elems int64 values (row 0 and column 0 are zero). */
+BNZ_API int bnz_integral_images_dev(const uint8_t *d_src, size_t src_pitch, int height, int width, int channels,
+                                    void *d_scratch, size_t scratch_bytes, long long *ld_elems, void *stream);
+
 /* ---- library state ------------------------------------------------------ */
 
 /* Message for the calling thread's most recent failure ("" if none). */

@@ -77,7 +77,7 @@ def _optional_symbols(lib):
                                     ctypes.c_int),
         "bnz_integral_scratch_bytes": ([i, i], ctypes.c_size_t),
         "bnz_binarize_integral_dev": ([P, sz, i, i, i, i, i, d, d, P, sz, i, P, sz, P, P], ctypes.c_int),
-        "bnz_window_sums_dev": ([P, sz, i, i, i, i, P, P, P, P], ctypes.c_int),
+        "bnz_integral_images_dev": ([P, sz, i, i, i, P, sz, ctypes.POINTER(ctypes.c_longlong), P], ctypes.c_int),
     }
     for name, (args, res) in table.items():
         if hasattr(lib, name):
@@ -203,6 +203,41 @@ def bnz_niblack_dev(d_src, W: int, k: float, d_dst, packed: bool = False, stream
     _check(load().bnz_niblack_dev(ptr, pitch, h, w, ch, int(W), float(k), d_dst.data_ptr(), dp,
                                   1 if packed else 0, _stream_ptr(stream),
                                   d_stats.data_ptr() if d_stats is not None else None))
+
+
+def bnz_integral_scratch_bytes(h: int, w: int) -> int:
+    return load().bnz_integral_scratch_bytes(int(h), int(w))
+
+
+def alloc_scratch(nbytes: int, device="cuda"):
+    """Device scratch buffer (torch tensor of int64, 256-byte aligned base)."""
+    import torch
+    return torch.empty(((nbytes + 7) // 8,), dtype=torch.int64, device=device)
+
+
+def bnz_binarize_integral_dev(d_src, W: int, rule: int, k: float, R: float, d_dst, d_scratch, packed=False,
+                              stream=None, d_stats=None) -> None:
+    """Integral-image variant; d_scratch: a CUDA tensor of at least bnz_integral_scratch_bytes bytes."""
+    ptr, pitch, h, w, ch = _dev_img(d_src)
+    dp = _out_pitch(d_dst, w, packed)
+    nbytes = d_scratch.numel() * d_scratch.element_size()
+    _check(load().bnz_binarize_integral_dev(ptr, pitch, h, w, ch, int(W), int(rule), float(k), float(R),
+                                            d_dst.data_ptr(), dp, 1 if packed else 0, d_scratch.data_ptr(),
+                                            nbytes, _stream_ptr(stream),
+                                            d_stats.data_ptr() if d_stats is not None else None))
+
+
+def bnz_integral_images_dev(d_src, d_scratch, stream=None):
+    """Build the two int64 summed-area tables; returns views (I1, I2) of shape (h+1, w+1)."""
+    ptr, pitch, h, w, ch = _dev_img(d_src)
+    nbytes = d_scratch.numel() * d_scratch.element_size()
+    ld = ctypes.c_longlong(0)
+    _check(load().bnz_integral_images_dev(ptr, pitch, h, w, ch, d_scratch.data_ptr(), nbytes,
+                                          ctypes.byref(ld), _stream_ptr(stream)))
+    n = (h + 1) * ld.value
+    I1 = d_scratch[:n].view(h + 1, ld.value)[:, :w + 1]
+    I2 = d_scratch[n:2 * n].view(h + 1, ld.value)[:, :w + 1]
+    return I1, I2
 
 
 def bnz_fused_plan(h: int, w: int, ch: int, W: int, tile: bnz_tile | None = None) -> dict:

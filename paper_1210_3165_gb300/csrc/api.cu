@@ -284,6 +284,50 @@ int bnz_binarize_dev(const uint8_t *d_src, size_t src_pitch, int height, int wid
                         stream, d_stats);
 }
 
+size_t bnz_integral_scratch_bytes(int height, int width) { return integral_scratch_bytes(height, width); }
+
+int bnz_binarize_integral_dev(const uint8_t *d_src, size_t src_pitch, int height, int width, int channels, int W,
+                              int rule, double k, double R, uint8_t *d_dst, size_t dst_pitch, int packed,
+                              void *d_scratch, size_t scratch_bytes, void *stream, unsigned long long *d_stats)
+{
+    int rc = check_common(d_src, src_pitch, height, width, channels, W, rule, k, R, d_dst, dst_pitch, packed);
+    if (rc != BNZ_OK)
+        return rc;
+    if (height > 65535)
+        return fail(BNZ_EINVAL, "the integral-image variant supports height <= 65535 (got %d)", height);
+    const size_t need = integral_scratch_bytes(height, width);
+    if (!d_scratch || scratch_bytes < need)
+        return fail(BNZ_EINVAL, "scratch of %zu bytes needed (got %zu)", need, scratch_bytes);
+    if (reinterpret_cast<uintptr_t>(d_scratch) & 31u)
+        return fail(BNZ_EINVAL, "d_scratch must be 32-byte aligned");
+    int dev = 0;
+    rc = device_sm_count(&dev);
+    if (rc != BNZ_OK)
+        return rc;
+    if (rule == BNZ_NIBLACK)
+        R = 1.0;
+    return launch_integral(d_src, src_pitch, height, width, channels, W, rule, k, R, d_dst, dst_pitch, packed,
+                           d_scratch, static_cast<cudaStream_t>(stream), d_stats);
+}
+
+int bnz_integral_images_dev(const uint8_t *d_src, size_t src_pitch, int height, int width, int channels,
+                            void *d_scratch, size_t scratch_bytes, long long *ld_elems, void *stream)
+{
+    if (!d_src || !d_scratch || !ld_elems)
+        return fail(BNZ_EINVAL, "null pointer");
+    if (height < 1 || width < 1 || (channels != 1 && channels != 3) || src_pitch < (size_t)width * channels)
+        return fail(BNZ_EINVAL, "bad image geometry");
+    const size_t need = integral_scratch_bytes(height, width);
+    if (scratch_bytes < need || (reinterpret_cast<uintptr_t>(d_scratch) & 31u))
+        return fail(BNZ_EINVAL, "scratch of %zu bytes (32-byte aligned) needed", need);
+    int dev = 0;
+    int rc = device_sm_count(&dev);
+    if (rc != BNZ_OK)
+        return rc;
+    return launch_integral_tables(d_src, src_pitch, height, width, channels, d_scratch,
+                                  static_cast<cudaStream_t>(stream), ld_elems);
+}
+
 const char *bnz_last_error(void) { return t_err.c_str(); }
 
 int bnz_version(void) { return 100; }

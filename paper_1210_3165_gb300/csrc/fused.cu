@@ -36,6 +36,7 @@
 #include <cmath>
 #include <cstdio>
 
+#include "decide.cuh"
 #include "internal.h"
 #include "ptx.cuh"
 
@@ -80,37 +81,6 @@ __device__ __forceinline__ uint32_t byte_dyn(uint32_t w, int j)
     return (w >> (8 * j)) & 0xffu;
 }
 
-// PTX prmt (default mode): a selector nibble with bit 3 set yields the sign
-// of the selected byte replicated over the result byte.
-__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel)
-{
-    uint32_t r;
-    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(sel));
-    return r;
-}
-
-__device__ __forceinline__ float sqrt_approx(float x)
-{
-    float r;
-    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-
-__device__ __forceinline__ float rcp_approx(float x)
-{
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-
-// V (< 2^48) as float: high word exact, low word rounded, one more rounding in
-// the fma -- relative error <= 2u (u = 2^-24).  A 64-bit integer conversion
-// would run on the fp64 pipe.
-__device__ __forceinline__ float v_to_float(unsigned long long V)
-{
-    return __fmaf_rn(__uint2float_rn((uint32_t)(V >> 32)), 4294967296.0f, __uint2float_rn((uint32_t)V));
-}
-
 // Position of span column c in a column-sum row: 4 words of padding after
 // every 16 columns keep the lanes' 128-bit loads free of bank conflicts.
 __device__ __forceinline__ int cpos(int c)
@@ -141,43 +111,6 @@ __device__ __forceinline__ uint32_t gray4(uint32_t w0, uint32_t w1, uint32_t w2)
     const uint32_t g2 = gray1(__funnelshift_r(w1, w2, 16));
     const uint32_t g3 = gray1(w2 >> 8);
     return g0 | (g1 << 8) | (g2 << 16) | (g3 << 24);
-}
-
-// fp32 filter d ~ f - t, n = W*W (constants from the host in double, rounded once)
-template <int RULE>
-__device__ __forceinline__ float filter_int(float ff, float S1f, float sq, const FusedParams &p)
-{
-    if (RULE == BNZ_SAUVOLA)
-        return __fmaf_rn(-S1f, __fmaf_rn(p.kRn2, sq, p.omkn), ff);
-    return __fmaf_rn(-p.kn, sq, __fmaf_rn(-p.invn, S1f, ff));
-}
-
-// fp32 filter d ~ f - t for a pixel with its own n (invn ~ 1/n from rcp.approx)
-template <int RULE>
-__device__ __forceinline__ float filter_n(float ff, float S1f, float sq, float invn, const FusedParams &p)
-{
-    if (RULE == BNZ_SAUVOLA)
-        return __fmaf_rn(-S1f, __fmaf_rn(__fmul_rn(__fmul_rn(p.kR, invn), invn), sq, __fmul_rn(p.omk, invn)), ff);
-    return __fmaf_rn(-__fmul_rn(p.kf, invn), sq, __fmaf_rn(-invn, S1f, ff));
-}
-
-// The fp64 sequence of the definition, same order, no contraction.
-// Returns g | 0x200 if |f - t| < 1e-9 (a tie).
-template <int RULE>
-__device__ __noinline__ uint32_t decide_fp64(uint32_t f, uint32_t n, uint32_t S1, uint32_t S2, const FusedParams &p)
-{
-    const unsigned long long V = (unsigned long long)n * S2 - (unsigned long long)S1 * S1;
-    const double nd = (double)n;
-    const double md = __ddiv_rn((double)S1, nd);
-    const double sd = __ddiv_rn(__dsqrt_rn(__ull2double_rn(V)), nd);
-    double td;
-    if (RULE == BNZ_SAUVOLA)
-        td = __dmul_rn(md, __dadd_rn(1.0, __dmul_rn(p.k, __dsub_rn(__ddiv_rn(sd, p.R), 1.0))));
-    else
-        td = __dadd_rn(md, __dmul_rn(p.k, sd));
-    const double fd = (double)f;
-    const uint32_t tie = fabs(__dsub_rn(fd, td)) < 1e-9 ? 0x200u : 0u;
-    return (fd < td ? 0u : 255u) | tie;
 }
 
 struct Segment {
@@ -750,6 +683,28 @@ float decision_margin(int rule, double k, double R)
     return (float)E;
 }
 
+void fill_decision_params(FusedParams *p, int h, int w, int W, int rule, double k, double R)
+{
+    *p = FusedParams{};
+    p->h = h;
+    p->w = w;
+    p->W = W;
+    p->r_lo = W / 2;
+    p->r_hi = W - 1 - W / 2;
+    p->nW = (uint32_t)(W * W);
+    p->k = k;
+    p->R = R;
+    const double n = (double)W * (double)W;
+    p->omkn = (float)((1.0 - k) / n);
+    p->kRn2 = (float)(k / (R * n * n));
+    p->invn = (float)(1.0 / n);
+    p->kn = (float)(k / n);
+    p->kf = (float)k;
+    p->omk = (float)(1.0 - k);
+    p->kR = (float)(k / R);
+    p->E = decision_margin(rule, k, R);
+}
+
 int plan_fused(int h, int w, int ch, int W, const bnz_tile *tile, FusedPlan *pl)
 {
     int sms = 0;
@@ -811,15 +766,11 @@ int launch_fused(const uint8_t *d_src, size_t src_pitch, int h, int w, int ch, i
     if (rc != BNZ_OK)
         return rc;
     FusedParams p;
+    fill_decision_params(&p, h, w, W, rule, k, R);
     p.dst = d_dst;
     p.dst_pitch = (long long)dst_pitch;
     p.stats = d_stats;
     p.err_flag = d_err;
-    p.h = h;
-    p.w = w;
-    p.W = W;
-    p.r_lo = W / 2;
-    p.r_hi = W - 1 - W / 2;
     p.o = pl.o;
     p.TW = pl.TW;
     p.CH = pl.CH;
@@ -837,18 +788,6 @@ int launch_fused(const uint8_t *d_src, size_t src_pitch, int h, int w, int ch, i
     p.packed = packed ? 1 : 0;
     p.vec_ok = ((reinterpret_cast<uintptr_t>(d_dst) | dst_pitch) & 15u) == 0 ? 1 : 0;
     p.s1_magic = 0;
-    p.nW = (uint32_t)(W * W);
-    p.k = k;
-    p.R = R;
-    const double n = (double)W * (double)W;
-    p.omkn = (float)((1.0 - k) / n);
-    p.kRn2 = (float)(k / (R * n * n));
-    p.invn = (float)(1.0 / n);
-    p.kn = (float)(k / n);
-    p.kf = (float)k;
-    p.omk = (float)(1.0 - k);
-    p.kR = (float)(k / R);
-    p.E = decision_margin(rule, k, R);
     p.timeout_cycles = 4000000000ll; // ~2 s at 2 GHz
     const void *fn = kernel_for(ch, rule, W);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);

@@ -79,4 +79,16 @@ constexpr double kRcpApproxRelErr = 1.0 / (1 << 22);
 // fp32 decision margin E (see fused.cu for the derivation).
 float decision_margin(int rule, double k, double R);
 
+// Fills the geometry and threshold constants of `p` shared by every kernel
+// that takes the Eq. 3 decision (window radii, k, R, fp32 constants, margin).
+void fill_decision_params(FusedParams *p, int h, int w, int W, int rule, double k, double R);
+
+// ---- integral-image comparison variant (integral.cu) -----------------------
+size_t integral_scratch_bytes(int h, int w);
+int launch_integral_tables(const uint8_t *d_src, size_t src_pitch, int h, int w, int ch, void *scratch,
+                           cudaStream_t stream, long long *ld_out);
+int launch_integral(const uint8_t *d_src, size_t src_pitch, int h, int w, int ch, int W, int rule, double k,
+                    double R, uint8_t *d_dst, size_t dst_pitch, int packed, void *scratch, cudaStream_t stream,
+                    unsigned long long *d_stats);
+
 } // namespace bnz
