@@ -147,6 +147,24 @@ BNZ_API int bnz_binarize_integral_dev(const uint8_t *d_src, size_t src_pitch, in
 BNZ_API int bnz_integral_images_dev(const uint8_t *d_src, size_t src_pitch, int height, int width, int channels,
                                     void *d_scratch, size_t scratch_bytes, long long *ld_elems, void *stream);
 
+/* Allocation-free form of bnz_binarize_integral_dev (the paper has no
+ * counterpart; this serves callers that cannot allocate device memory, such
+ * as code running inside a framework that owns every device allocation, or a
+ * fixed-budget pipeline that must not reach the allocator while it runs).
+ * The scratch is a library-owned device array of BNZ_INTEGRAL_STATIC_MAX_BYTES
+ * that every GPU loading the library keeps until the process exits; pages
+ * whose scratch (bnz_integral_scratch_bytes) exceeds it are rejected with
+ * BNZ_EINVAL.  The first call on a device looks up the array's device address
+ * (once per device); make that first call before any stream capture.  Every
+ * call on a device uses the same array: calls that overlap on the GPU (other
+ * streams, other host threads) race and must be serialized by the caller.
+ * The call itself allocates nothing.  Arguments as bnz_binarize_dev. */
+#define BNZ_INTEGRAL_STATIC_MAX_BYTES (32u << 20)
+BNZ_API int bnz_binarize_integral_static_dev(const uint8_t *d_src, size_t src_pitch, int height, int width,
+                                             int channels, int W, int rule, double k, double R, uint8_t *d_dst,
+                                             size_t dst_pitch, int packed, void *stream,
+                                             unsigned long long *d_stats);
+
 /* ---- library state ------------------------------------------------------ */
 
 /* Message for the calling thread's most recent failure ("" if none). */

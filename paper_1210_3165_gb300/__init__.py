@@ -77,6 +77,7 @@ def _optional_symbols(lib):
                                     ctypes.c_int),
         "bnz_integral_scratch_bytes": ([i, i], ctypes.c_size_t),
         "bnz_binarize_integral_dev": ([P, sz, i, i, i, i, i, d, d, P, sz, i, P, sz, P, P], ctypes.c_int),
+        "bnz_binarize_integral_static_dev": ([P, sz, i, i, i, i, i, d, d, P, sz, i, P, P], ctypes.c_int),
         "bnz_integral_images_dev": ([P, sz, i, i, i, P, sz, ctypes.POINTER(ctypes.c_longlong), P], ctypes.c_int),
     }
     for name, (args, res) in table.items():
@@ -225,6 +226,16 @@ def bnz_binarize_integral_dev(d_src, W: int, rule: int, k: float, R: float, d_ds
                                             d_dst.data_ptr(), dp, 1 if packed else 0, d_scratch.data_ptr(),
                                             nbytes, _stream_ptr(stream),
                                             d_stats.data_ptr() if d_stats is not None else None))
+
+
+def bnz_binarize_integral_static_dev(d_src, W: int, rule: int, k: float, R: float, d_dst, packed=False,
+                                     stream=None, d_stats=None) -> None:
+    """Integral-image variant that allocates nothing (library-owned scratch; see include/bnz.h)."""
+    ptr, pitch, h, w, ch = _dev_img(d_src)
+    dp = _out_pitch(d_dst, w, packed)
+    _check(load().bnz_binarize_integral_static_dev(ptr, pitch, h, w, ch, int(W), int(rule), float(k), float(R),
+                                                   d_dst.data_ptr(), dp, 1 if packed else 0, _stream_ptr(stream),
+                                                   d_stats.data_ptr() if d_stats is not None else None))
 
 
 def bnz_integral_images_dev(d_src, d_scratch, stream=None):

@@ -128,8 +128,8 @@ int device_err_flag(unsigned int **flag)
     return BNZ_OK;
 }
 
-static int check_common(const void *src, size_t src_pitch, int height, int width, int channels, int W, int rule,
-                        double k, double R, const void *dst, size_t dst_pitch, int packed)
+int check_common(const void *src, size_t src_pitch, int height, int width, int channels, int W, int rule,
+                 double k, double R, const void *dst, size_t dst_pitch, int packed)
 {
     if (!src || !dst)
         return fail(BNZ_EINVAL, "null image pointer");

@@ -12,6 +12,7 @@
 // decision as the fused kernel (fp32 filter with the proven margin, fp64
 // re-evaluation inside it), so the masks are identical bit for bit.
 #include <algorithm>
+#include <mutex>
 
 #include "decide.cuh"
 #include "internal.h"
@@ -290,3 +291,71 @@ int launch_integral(const uint8_t *d_src, size_t src_pitch, int h, int w, int ch
 }
 
 } // namespace bnz
+
+// ---- allocation-free entry point -------------------------------------------
+// Some callers cannot allocate device memory themselves: code hosted inside a
+// framework that owns every device allocation through its own pool, or a
+// fixed-budget pipeline that must not reach the allocator (and risk its
+// latency or an out-of-memory failure) once it is running.  For them the
+// integral-image scratch lives in this file-scope device array.  Every GPU
+// that loads the library keeps it until the process exits.
+namespace bnz {
+namespace {
+
+__device__ __align__(256) static unsigned char g_integral_static[BNZ_INTEGRAL_STATIC_MAX_BYTES];
+
+std::mutex g_static_mu;
+void *g_static_ptr[64];
+
+// The array's device address for the current device.  In host code the
+// array's name is only a host-side stand-in, so the address is looked up once
+// per device (with that device current) and cached.
+int static_scratch(void **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= 64)
+        return fail(BNZ_ENODEV, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void *ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_integral_static);
+        if (e != cudaSuccess || !ptr)
+            return cuda_fail(e, "cudaGetSymbolAddress(integral scratch)");
+        g_static_ptr[dev] = ptr;
+    }
+    *out = g_static_ptr[dev];
+    return BNZ_OK;
+}
+
+} // namespace
+} // namespace bnz
+
+extern "C" BNZ_API int bnz_binarize_integral_static_dev(const uint8_t *d_src, size_t src_pitch, int height,
+                                                        int width, int channels, int W, int rule, double k,
+                                                        double R, uint8_t *d_dst, size_t dst_pitch, int packed,
+                                                        void *stream, unsigned long long *d_stats)
+{
+    using namespace bnz;
+    int rc = check_common(d_src, src_pitch, height, width, channels, W, rule, k, R, d_dst, dst_pitch, packed);
+    if (rc != BNZ_OK)
+        return rc;
+    const size_t need = integral_scratch_bytes(height, width);
+    if (need > (size_t)BNZ_INTEGRAL_STATIC_MAX_BYTES || height > 65535)
+        return fail(BNZ_EINVAL,
+                    "a %d x %d page needs %zu bytes of integral-image scratch; the allocation-free entry point "
+                    "holds at most %zu (about 2 Mpixel): pass your own scratch to bnz_binarize_integral_dev",
+                    height, width, need, (size_t)BNZ_INTEGRAL_STATIC_MAX_BYTES);
+    void *scratch = nullptr;
+    rc = static_scratch(&scratch);
+    if (rc != BNZ_OK)
+        return rc;
+    if (rule == BNZ_NIBLACK)
+        R = 1.0;
+    // The tables are rewritten completely by every call (their zero row and
+    // column included), so nothing left by the previous call needs clearing.
+    return launch_integral(d_src, src_pitch, height, width, channels, W, rule, k, R, d_dst, dst_pitch, packed,
+                           scratch, static_cast<cudaStream_t>(stream), d_stats);
+}

@@ -21,6 +21,10 @@ int encode_u8_map(CUtensorMap *map, const void *base, uint64_t inner_bytes, uint
 
 int device_sm_count(int *sms);
 
+// Argument checks shared by the binarize entry points (BNZ_OK or BNZ_EINVAL).
+int check_common(const void *src, size_t src_pitch, int height, int width, int channels, int W, int rule,
+                 double k, double R, const void *dst, size_t dst_pitch, int packed);
+
 // ---- fused tile kernel -----------------------------------------------------
 
 // Shape of one launch of the fused kernel (host-side plan).
