@@ -122,6 +122,42 @@ BNZ_API int bnz_binarize_dev(const uint8_t *d_src, size_t src_pitch, int height,
                      int rule, double k, double R, uint8_t *d_dst, size_t dst_pitch, int packed,
                      const bnz_tile *tile, void *stream, unsigned long long *d_stats);
 
+/* ---- batches: many uneven pages in one persistent launch -------------------
+ * Every page of a batch is binarized exactly as bnz_binarize_dev would do it
+ * (same kernels, same bits), but all pages' work is split over one persistent
+ * grid per channel count, so small pages do not each pay a launch and a
+ * partly idle GPU.  The device pointers are bound at creation: running the
+ * batch again reads the same d_src buffers and writes the same d_dst
+ * buffers (refill the inputs between runs).  With use_graph != 0 the
+ * launches are captured once into a CUDA graph and bnz_batch_run replays it. */
+typedef struct {
+    const uint8_t *d_src; /* device, 16-byte aligned, src_pitch % 16 == 0 */
+    size_t src_pitch;
+    int height, width, channels; /* channels 1 or 3 */
+    int W, rule, packed;         /* as bnz_binarize_dev */
+    double k, R;
+    uint8_t *d_dst;
+    size_t dst_pitch;
+    int tile_w; /* preferred strip width 128, 256 or 512 (e.g. from an autotuner); 0 or a width that
+                   does not fit shared memory = the widest that fits */
+    int reserved;
+} bnz_page;
+
+typedef struct bnz_batch bnz_batch; /* opaque */
+
+/* Validate and plan n pages, upload their descriptors (device memory owned
+ * by the batch), optionally capture the launches in a CUDA graph.  d_stats:
+ * nullable device counters as for bnz_binarize_dev.  On error *out is NULL. */
+BNZ_API int bnz_batch_create(const bnz_page *pages, int n, int use_graph, unsigned long long *d_stats,
+                             bnz_batch **out);
+/* Enqueue the whole batch on `stream` (one graph launch, or one kernel per channel count). */
+BNZ_API int bnz_batch_run(bnz_batch *b, void *stream);
+/* Pages, kernel launches per run, grid size, shared memory per CTA and total strip-rows. */
+BNZ_API int bnz_batch_info(const bnz_batch *b, int *pages, int *launches, int *grid, size_t *smem,
+                           long long *strip_rows);
+/* Free the batch (after its last run has completed). */
+BNZ_API int bnz_batch_destroy(bnz_batch *b);
+
 /* ---- integral-image comparison variant ------------------------------------
  * The O(N^2) method with summed-area tables that Sec. 1 cites (Shafait et
  * al.) and Sec. 3.3 charges 12 S_z bytes of memory: two (h+1) x (w+1) int64

@@ -30,6 +30,14 @@ class BnzError(RuntimeError):
         self.status = status
 
 
+class bnz_page(ctypes.Structure):
+    _fields_ = [("d_src", ctypes.c_void_p), ("src_pitch", ctypes.c_size_t), ("height", ctypes.c_int),
+                ("width", ctypes.c_int), ("channels", ctypes.c_int), ("W", ctypes.c_int),
+                ("rule", ctypes.c_int), ("packed", ctypes.c_int), ("k", ctypes.c_double),
+                ("R", ctypes.c_double), ("d_dst", ctypes.c_void_p), ("dst_pitch", ctypes.c_size_t),
+                ("tile_w", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+
 class bnz_tile(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int), ("chunk", ctypes.c_int),
                 ("reserved", ctypes.c_int)]
@@ -71,6 +79,11 @@ def _optional_symbols(lib):
     """Entry points added by later parts of the library (integral images, batches)."""
     P, i, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
     table = {
+        "bnz_batch_create": ([P, i, i, P, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+        "bnz_batch_run": ([P, P], ctypes.c_int),
+        "bnz_batch_info": ([P, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(sz),
+                            ctypes.POINTER(ctypes.c_longlong)], ctypes.c_int),
+        "bnz_batch_destroy": ([P], ctypes.c_int),
         "bnz_selftest_sqrt_approx": ([ctypes.c_float, ctypes.c_float, ctypes.POINTER(ctypes.c_double)],
                                      ctypes.c_int),
         "bnz_selftest_rcp_approx": ([ctypes.c_uint, ctypes.c_uint, ctypes.POINTER(ctypes.c_double)],
@@ -249,6 +262,57 @@ def bnz_integral_images_dev(d_src, d_scratch, stream=None):
     I1 = d_scratch[:n].view(h + 1, ld.value)[:, :w + 1]
     I2 = d_scratch[n:2 * n].view(h + 1, ld.value)[:, :w + 1]
     return I1, I2
+
+
+class Batch:
+    """Many pages binarized by one persistent launch per channel count (optionally a CUDA graph).
+
+    pages: dicts with src (pitched uint8 CUDA image), dst (pitched uint8 CUDA output), W, and optional
+    rule ("sauvola"/"niblack"), k, R, packed, tile_w.  The tensors are bound at creation: run() reads
+    the same inputs and writes the same outputs every time.
+    """
+
+    def __init__(self, pages, use_graph: bool = True, d_stats=None):
+        arr = (bnz_page * len(pages))()
+        self._keep = []
+        for i, pg in enumerate(pages):
+            ptr, pitch, h, w, ch = _dev_img(pg["src"])
+            rule = pg.get("rule", "sauvola")
+            if isinstance(rule, str):
+                rule = {"sauvola": BNZ_SAUVOLA, "niblack": BNZ_NIBLACK}[rule.lower()]
+            k = pg.get("k", 0.5 if rule == BNZ_SAUVOLA else -0.2)
+            packed = bool(pg.get("packed", False))
+            dst = pg["dst"]
+            arr[i] = bnz_page(ptr, pitch, h, w, ch, int(pg["W"]), int(rule), 1 if packed else 0, float(k),
+                              float(pg.get("R", 128.0)), dst.data_ptr(), _out_pitch(dst, w, packed),
+                              int(pg.get("tile_w", 0)), 0)
+            self._keep += [pg["src"], dst]
+        self._stats = d_stats
+        h = ctypes.c_void_p(None)
+        _check(load().bnz_batch_create(ctypes.cast(arr, ctypes.c_void_p), len(pages), 1 if use_graph else 0,
+                                       d_stats.data_ptr() if d_stats is not None else None, ctypes.byref(h)))
+        self._h = h
+
+    def run(self, stream=None) -> None:
+        _check(load().bnz_batch_run(self._h, _stream_ptr(stream)))
+
+    def info(self) -> dict:
+        n, l, g = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        sm, rows = ctypes.c_size_t(0), ctypes.c_longlong(0)
+        _check(load().bnz_batch_info(self._h, ctypes.byref(n), ctypes.byref(l), ctypes.byref(g),
+                                     ctypes.byref(sm), ctypes.byref(rows)))
+        return dict(pages=n.value, launches=l.value, grid=g.value, smem=sm.value, strip_rows=rows.value)
+
+    def close(self) -> None:
+        if self._h:
+            load().bnz_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def bnz_fused_plan(h: int, w: int, ch: int, W: int, tile: bnz_tile | None = None) -> dict:

@@ -36,497 +36,10 @@
 #include <cmath>
 #include <cstdio>
 
-#include "decide.cuh"
-#include "internal.h"
-#include "ptx.cuh"
+#include "segment.cuh"
 
 namespace bnz {
 namespace {
-
-constexpr int NTP = 256;            // producer threads (warps 0-7)
-constexpr int NTQ = 256;            // consumer threads (warps 8-15), one row each
-constexpr int NT = NTP + NTQ;
-constexpr int L = 16;               // outputs per consumer lane per row
-constexpr int TW = 32 * L;          // widest strip; 256 is used when the ring would not fit
-constexpr int BAR_FULL = 1;         // named barriers 1,2: column-sum buffer b is ready
-constexpr int BAR_EMPTY = 3;        // named barriers 3,4: column-sum buffer b may be refilled
-constexpr int BAR_PROD = 5;         // producers only
-constexpr int kL2 = 6;              // chunks of L2 prefetch lead beyond the shared-memory loads
-constexpr int CH = 8;               // rows per chunk (TMA box height, one consumer warp per row)
-constexpr int kLeadGray = 3;        // gray: chunks loaded ahead of the ones in use
-constexpr int MAX_DYN_SMEM = 232448 - 1024; // 227 KB opt-in limit, minus slack
-
-// Panel widths in pixels (one TMA box per panel and chunk): gray 128 (or 64
-// when shared memory is tight), RGB 80 (240-byte boxes, whole r,g,b triples).
-
-__device__ __forceinline__ void bar_sync(int id, int n)
-{
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
-}
-
-__device__ __forceinline__ void bar_arrive(int id, int n)
-{
-    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
-}
-
-// byte J of w, zero-extended (one permute)
-template <int J>
-__device__ __forceinline__ uint32_t byte_at(uint32_t w)
-{
-    return __byte_perm(w, 0u, 0x4440u | J);
-}
-
-__device__ __forceinline__ uint32_t byte_dyn(uint32_t w, int j)
-{
-    return (w >> (8 * j)) & 0xffu;
-}
-
-// Position of span column c in a column-sum row: 4 words of padding after
-// every 16 columns keep the lanes' 128-bit loads free of bank conflicts.
-__device__ __forceinline__ int cpos(int c)
-{
-    return c + ((c >> 4) << 2);
-}
-
-__device__ __forceinline__ uint4 ld_group(const uint32_t *C, int a) // columns 4a..4a+3
-{
-    return *reinterpret_cast<const uint4 *>(C + 4 * a + ((a >> 2) << 2));
-}
-
-// Eq. 1 for one pixel whose r, g, b are bytes 0..2 of px (byte 3 ignored):
-// x = 299 r + 587 g + 114 b + 500 = (43 r + 75 g + 114 b) + 256 (r + 2 g) + 500,
-// q = floor(x / 1000) = high word of x * ceil(2^32 / 1000) (exact for x < 6.1e6).
-__device__ __forceinline__ uint32_t gray1(uint32_t px)
-{
-    const uint32_t hi = __dp4a(px, 0x00000201u, 0u);
-    const uint32_t x = __dp4a(px, 0x00724B2Bu, hi * 256u + 500u);
-    return __umulhi(x, 4294968u);
-}
-
-// Four gray pixels from 12 interleaved bytes r0 g0 b0 r1 | g1 b1 r2 g2 | b2 r3 g3 b3.
-__device__ __forceinline__ uint32_t gray4(uint32_t w0, uint32_t w1, uint32_t w2)
-{
-    const uint32_t g0 = gray1(w0);
-    const uint32_t g1 = gray1(__funnelshift_r(w0, w1, 24));
-    const uint32_t g2 = gray1(__funnelshift_r(w1, w2, 16));
-    const uint32_t g3 = gray1(w2 >> 8);
-    return g0 | (g1 << 8) | (g2 << 16) | (g3 << 24);
-}
-
-struct Segment {
-    int x0, y0, th_eff, xs, ys, nchk, nk;
-};
-
-// ---------------------------------------------------------------------------
-// producers: TMA ring, RGB->gray, column sums (a1-a3)
-// ---------------------------------------------------------------------------
-template <int CIN>
-__device__ __forceinline__ void produce(const CUtensorMap *tmap, const FusedParams &p, const Segment &sg,
-                                        uint8_t *smem, uint64_t &phase, volatile int *s_abort)
-{
-    const int PWP = p.PWP;
-    const int PWB = PWP * CIN;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
-    uint8_t *ring = smem + p.off_ring;
-    uint8_t *stage = smem + p.off_stage;
-    uint32_t *cb = reinterpret_cast<uint32_t *>(smem + p.off_cb);
-    const int tid = threadIdx.x; // 0..NTP-1
-    const int W = p.W;
-    const int D = (CH + W - 1) / CH;
-    const int nbar = CIN == 1 ? p.NS : p.NSS;
-    const uint32_t chunk_bytes = (uint32_t)(p.NPAN * CH * PWB);
-    const bool owner = tid < (p.SWP >> 2);
-    const int gcol = tid * 4;
-    const int gpn = gcol / PWP, gip = gcol - gpn * PWP;
-    const int gpos = cpos(gcol);
-    uint8_t *gbase = ring + (size_t)gpn * p.ring_rows * PWP + gip; // this thread's 4 columns, ring row 0
-    const uint8_t *sbase = stage + (size_t)gpn * CH * PWB + 3 * gip;  // the same columns in staging slot 0
-    const int ring_bytes = p.ring_rows * PWP;                     // one panel of the ring
-
-    int issued = 0, waited = 0;
-    bool good = !*s_abort;
-    // L2 prefetch of the chunk kL2 ahead of each shared-memory load, so the
-    // loads find their rows in L2 (the ring has room for only a few chunks)
-    auto prefetch = [&](int j) {
-        if (j < sg.nchk)
-            for (int pn = 0; pn < p.NPAN; ++pn)
-                tma_prefetch_l2_2d(tmap, (sg.xs + pn * PWP) * CIN, sg.ys + j * CH);
-    };
-    auto issue = [&](int j) { // thread 0 only
-        const int slot = j % nbar;
-        uint64_t *bar = &bars[slot];
-        mbar_arrive_expect_tx(bar, chunk_bytes);
-        for (int pn = 0; pn < p.NPAN; ++pn) {
-            uint8_t *dst = (CIN == 1) ? ring + (size_t)pn * p.ring_rows * PWP + (size_t)slot * CH * PWP
-                                      : stage + ((size_t)slot * p.NPAN + pn) * CH * PWB;
-            tma_load_2d(dst, tmap, (sg.xs + pn * PWP) * CIN, sg.ys + j * CH, bar);
-        }
-        prefetch(j + kL2);
-    };
-    // every producer waits for itself; a wait that gives up flags the CTA
-    // (the barrier protocol goes on, so no thread is left waiting)
-    auto wait_one = [&]() {
-        const int slot = waited % nbar;
-        if (!mbar_wait_bounded(&bars[slot], (uint32_t)((phase >> slot) & 1ull), p.timeout_cycles)) {
-            good = false;
-            *s_abort = 1;
-        }
-        phase ^= 1ull << slot;
-        ++waited;
-    };
-    // RGB: this thread's 4 columns of chunk j, staging slot -> gray ring slot (Eq. 1)
-    auto convert = [&](int j) {
-        if (!owner)
-            return;
-        const uint8_t *src = sbase + (size_t)(j % p.NSS) * p.NPAN * CH * PWB;
-        uint8_t *dst = gbase + (size_t)(j % p.NS) * CH * PWP;
-        uint32_t wv[CH][3];
-#pragma unroll
-        for (int r = 0; r < CH; ++r) {
-            const uint32_t *s32 = reinterpret_cast<const uint32_t *>(src + r * PWB);
-            wv[r][0] = s32[0];
-            wv[r][1] = s32[1];
-            wv[r][2] = s32[2];
-        }
-#pragma unroll
-        for (int r = 0; r < CH; ++r)
-            *reinterpret_cast<uint32_t *>(dst + r * PWP) = gray4(wv[r][0], wv[r][1], wv[r][2]);
-    };
-
-    // prologue: gray loads chunks 0..D+lead-1 straight into the ring; RGB fills its staging slots
-    const int lead = p.NS - D - 2; // gray: chunks in flight beyond the ones in use
-    if (good) {
-        const int pre = CIN == 1 ? min(sg.nchk, D + lead) : min(sg.nchk, p.NSS);
-        if (tid == 0) {
-            for (int j = pre; j < pre + kL2; ++j)
-                prefetch(j);
-            for (int j = 0; j < pre; ++j)
-                issue(j);
-        }
-        issued = pre;
-    }
-    // warm-up: chunks 0..D-1 hold rows 0..W-1, the window of the segment's first output row
-    for (int j = 0; j < D; ++j) {
-        if (good)
-            wait_one();
-        if (CIN == 3) {
-            if (good)
-                convert(j);
-            bar_sync(BAR_PROD, NTP); // staging slot j is free
-            if (good && issued < sg.nchk) {
-                if (tid == 0)
-                    issue(issued);
-                ++issued;
-            }
-        }
-    }
-    uint32_t c1[4] = {0u, 0u, 0u, 0u}, c2[4] = {0u, 0u, 0u, 0u};
-    if (good && owner) {
-        int off = 0;
-        for (int r = 0; r < W; ++r) {
-            const uint32_t v = *reinterpret_cast<const uint32_t *>(gbase + off);
-            c1[0] += byte_at<0>(v);
-            c1[1] += byte_at<1>(v);
-            c1[2] += byte_at<2>(v);
-            c1[3] += byte_at<3>(v);
-            c2[0] += byte_at<0>(v) * byte_at<0>(v);
-            c2[1] += byte_at<1>(v) * byte_at<1>(v);
-            c2[2] += byte_at<2>(v) * byte_at<2>(v);
-            c2[3] += byte_at<3>(v) * byte_at<3>(v);
-            off += PWP;
-            if (off == ring_bytes)
-                off = 0;
-        }
-    }
-    int off_in = (W % p.ring_rows) * PWP; // ring offset of row i + W (entering for output row i + 1)
-    int off_out = 0;                      // ring offset of row i (leaving), chunk-aligned
-
-    for (int k = 0; k < sg.nk; ++k) {
-        const int b = k & 1;
-        if (k >= 2)
-            bar_sync(BAR_EMPTY + b, NT); // consumers are done with chunk k-2
-        const int need = min(k + D, sg.nchk - 1);
-        if (CIN == 1) {
-            if (good && issued < sg.nchk) { // keep `lead` chunks in flight
-                if (tid == 0)
-                    issue(issued);
-                ++issued;
-            }
-            while (good && waited <= need)
-                wait_one();
-        } else {
-            while (good && waited <= need) {
-                const int j = waited;
-                wait_one();
-                if (good)
-                    convert(j); // own columns only: no barrier before the column sums
-            }
-        }
-        const int rows_k = min(CH, sg.th_eff - k * CH);
-        if (good && owner) {
-            const bool last = (k + 1 == sg.nk);
-            uint32_t *C1 = cb + (size_t)(2 * b) * CH * p.RSW + gpos;
-            uint32_t *C2 = C1 + (size_t)CH * p.RSW;
-            uint32_t vi[CH], vo[CH];
-#pragma unroll
-            for (int r = 0; r < CH; ++r) { // load first, then add: no smem latency per row
-                int oi = off_in + r * PWP;
-                if (oi >= ring_bytes)
-                    oi -= ring_bytes;
-                vi[r] = *reinterpret_cast<const uint32_t *>(gbase + oi);
-                vo[r] = *reinterpret_cast<const uint32_t *>(gbase + off_out + r * PWP);
-            }
-#pragma unroll
-            for (int r = 0; r < CH; ++r) {
-                if (r < rows_k) {
-                    *reinterpret_cast<uint4 *>(C1 + r * p.RSW) = make_uint4(c1[0], c1[1], c1[2], c1[3]);
-                    *reinterpret_cast<uint4 *>(C2 + r * p.RSW) = make_uint4(c2[0], c2[1], c2[2], c2[3]);
-                    if (!(last && r + 1 == rows_k)) { // slide to the next row
-                        const uint32_t a = vi[r], o = vo[r];
-                        c1[0] = c1[0] + byte_at<0>(a) - byte_at<0>(o);
-                        c1[1] = c1[1] + byte_at<1>(a) - byte_at<1>(o);
-                        c1[2] = c1[2] + byte_at<2>(a) - byte_at<2>(o);
-                        c1[3] = c1[3] + byte_at<3>(a) - byte_at<3>(o);
-                        c2[0] = c2[0] + byte_at<0>(a) * byte_at<0>(a) - byte_at<0>(o) * byte_at<0>(o);
-                        c2[1] = c2[1] + byte_at<1>(a) * byte_at<1>(a) - byte_at<1>(o) * byte_at<1>(o);
-                        c2[2] = c2[2] + byte_at<2>(a) * byte_at<2>(a) - byte_at<2>(o) * byte_at<2>(o);
-                        c2[3] = c2[3] + byte_at<3>(a) * byte_at<3>(a) - byte_at<3>(o) * byte_at<3>(o);
-                    }
-                }
-            }
-        }
-        off_in += CH * PWP;
-        if (off_in >= ring_bytes)
-            off_in -= ring_bytes;
-        off_out += CH * PWP;
-        if (off_out >= ring_bytes)
-            off_out -= ring_bytes;
-        bar_arrive(BAR_FULL + b, NT); // always, so consumers never wait forever
-        if (CIN == 3) {
-            bar_sync(BAR_PROD, NTP); // every producer is past the conversions of this step
-            while (good && issued < min(sg.nchk, waited + p.NSS)) {
-                if (tid == 0)
-                    issue(issued);
-                ++issued;
-            }
-        }
-    }
-    // drain this segment's copies (bounded) before the ring is reused
-    while (waited < issued) {
-        const int slot = waited % nbar;
-        mbar_wait_bounded(&bars[slot], (uint32_t)((phase >> slot) & 1ull), p.timeout_cycles);
-        phase ^= 1ull << slot;
-        ++waited;
-    }
-}
-
-// ---------------------------------------------------------------------------
-// consumers: horizontal sums, threshold, output (a4-a7)
-// ---------------------------------------------------------------------------
-template <int CIN, int RULE, int WM8>
-__device__ __forceinline__ void consume(const FusedParams &p, const Segment &sg, uint8_t *smem, uint32_t &nfb,
-                                        uint32_t &nties, volatile int *s_abort)
-{
-    const int PWP = p.PWP;
-    // o = (-r_lo) mod 16 and r_lo = W/2: the misalignments of the leaving
-    // (span column o + x) and entering (o + W + x) streams depend on W mod 8
-    constexpr int KO = (4 - ((WM8 >> 1) & 3)) & 3;
-    constexpr int KI = (KO + WM8) & 3;
-    const uint8_t *ring = smem + p.off_ring;
-    const uint32_t *cb = reinterpret_cast<const uint32_t *>(smem + p.off_cb);
-    const int q = threadIdx.x - NTP;
-    const int lane = q & 31, ii = q >> 5; // this warp's row within each chunk
-    const int W = p.W;
-    const bool active = lane * L < p.TW; // 256-wide strips leave lanes 16..31 idle
-    // centre pixels of this lane's 16 outputs start at span column lane*16 + o + r_lo (a multiple of 16)
-    const int fcol = active ? lane * L + p.o + p.r_lo : 0;
-    const int fpn = fcol / PWP;
-    const uint8_t *fbase = ring + (size_t)fpn * p.ring_rows * PWP + (fcol - fpn * PWP);
-    const int xg0 = sg.x0 + lane * L;
-    const bool xclip = xg0 < p.r_lo || xg0 + L - 1 + p.r_hi > p.w - 1; // some window of the lane leaves the image
-
-    int rc = (ii + p.r_lo) % p.ring_rows; // ring row of this warp's centre row in chunk k
-    for (int k = 0; k < sg.nk; ++k, rc = (rc + CH < p.ring_rows) ? rc + CH : rc + CH - p.ring_rows) {
-        const int b = k & 1;
-        bar_sync(BAR_FULL + b, NT);
-        const int rows_k = min(CH, sg.th_eff - k * CH);
-        if (ii < rows_k && !*s_abort) {
-            const int i = k * CH + ii;
-            const int y = sg.y0 + i;
-            const uint32_t *C1 = cb + (size_t)(2 * b) * CH * p.RSW + ii * p.RSW;
-            const uint32_t *C2 = C1 + (size_t)CH * p.RSW;
-            const int cw = lane * L + p.o; // leaving-stream start; entering = cw + W
-            const int ao = cw >> 2, ai = (cw + W) >> 2;
-
-            uint32_t d1[L], d2[L];
-            uint32_t a1 = 0, a2 = 0;
-            if (active) {
-                uint4 o1 = ld_group(C1, ao), o2 = ld_group(C2, ao);
-                uint4 i1 = ld_group(C1, ai), i2 = ld_group(C2, ai);
-#pragma unroll
-                for (int j = 0; j < L / 4; ++j) {
-                    uint4 o1n = make_uint4(0, 0, 0, 0), o2n = o1n, i1n = o1n, i2n = o1n;
-                    if (KO != 0 || j + 1 < L / 4) {
-                        o1n = ld_group(C1, ao + j + 1);
-                        o2n = ld_group(C2, ao + j + 1);
-                    }
-                    if (KI != 0 || j + 1 < L / 4) {
-                        i1n = ld_group(C1, ai + j + 1);
-                        i2n = ld_group(C2, ai + j + 1);
-                    }
-                    const uint32_t vo1[8] = {o1.x, o1.y, o1.z, o1.w, o1n.x, o1n.y, o1n.z, o1n.w};
-                    const uint32_t vo2[8] = {o2.x, o2.y, o2.z, o2.w, o2n.x, o2n.y, o2n.z, o2n.w};
-                    const uint32_t vi1[8] = {i1.x, i1.y, i1.z, i1.w, i1n.x, i1n.y, i1n.z, i1n.w};
-                    const uint32_t vi2[8] = {i2.x, i2.y, i2.z, i2.w, i2n.x, i2n.y, i2n.z, i2n.w};
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        d1[4 * j + e] = a1;
-                        d2[4 * j + e] = a2;
-                        a1 = a1 + vi1[e + KI] - vo1[e + KO];
-                        a2 = a2 + vi2[e + KI] - vo2[e + KO];
-                    }
-                    o1 = o1n;
-                    o2 = o2n;
-                    i1 = i1n;
-                    i2 = i2n;
-                }
-            } else {
-#pragma unroll
-                for (int t = 0; t < L; ++t)
-                    d1[t] = d2[t] = 0u;
-            }
-            // the window of the strip's first output: span columns [o, o + W)
-            uint32_t s1 = 0, s2 = 0;
-            for (int c = p.o + lane; c < p.o + W; c += 32) {
-                const int qc = cpos(c);
-                s1 += C1[qc];
-                s2 += C2[qc];
-            }
-            s1 = __reduce_add_sync(0xffffffffu, s1);
-            s2 = __reduce_add_sync(0xffffffffu, s2);
-            uint32_t x1 = a1, x2 = a2;
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const uint32_t t1 = __shfl_up_sync(0xffffffffu, x1, off);
-                const uint32_t t2 = __shfl_up_sync(0xffffffffu, x2, off);
-                if (lane >= off) {
-                    x1 += t1;
-                    x2 += t2;
-                }
-            }
-            const uint32_t base1 = s1 + x1 - a1, base2 = s2 + x2 - a2;
-
-            const uint4 fv = *reinterpret_cast<const uint4 *>(fbase + (size_t)rc * PWP);
-            const uint32_t fw[4] = {fv.x, fv.y, fv.z, fv.w};
-            const bool yclip = (y < p.r_lo) || (y + p.r_hi > p.h - 1);
-            const bool lane_clip = active && xg0 < p.w && (yclip || xclip);
-            uint32_t outw[4];
-            bool amb = false;
-            if (!__any_sync(0xffffffffu, lane_clip)) {
-                // every window of the warp is W x W: shared constants
-                // n*S2 = n*base2 + n*d2 (mod 2^64, d2 taken as a signed offset)
-                const unsigned long long nb2 = (unsigned long long)p.nW * base2;
-#pragma unroll
-                for (int qq = 0; qq < 4; ++qq) {
-                    float dd[4];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int t = 4 * qq + e;
-                        const uint32_t S1 = base1 + d1[t];
-                        const unsigned long long V = nb2 + (unsigned long long)((long long)p.nW * (int)d2[t]) -
-                                                     (unsigned long long)S1 * S1;
-                        const float ff = __uint2float_rn(byte_dyn(fw[qq], e));
-                        dd[e] = filter_int<RULE>(ff, __uint2float_rn(S1), sqrt_approx(v_to_float(V)), p);
-                        amb = amb || (fabsf(dd[e]) < p.E);
-                    }
-                    // byte = 0xFF where d >= +0, 0x00 where d < 0 (sign bit replicated)
-                    const uint32_t lo = prmt(__float_as_uint(dd[0]), __float_as_uint(dd[1]), 0xFBu);
-                    const uint32_t hi = prmt(__float_as_uint(dd[2]), __float_as_uint(dd[3]), 0xFBu);
-                    outw[qq] = ~prmt(lo, hi, 0x5410u);
-                }
-            } else {
-                // border warp: each pixel with its own clipped count n = nr * nc
-                const int nr = min(y + p.r_hi, p.h - 1) - max(y - p.r_lo, 0) + 1;
-#pragma unroll
-                for (int qq = 0; qq < 4; ++qq) {
-                    float dd[4];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int t = 4 * qq + e;
-                        const int xg = xg0 + t;
-                        const int nc = min(xg + p.r_hi, p.w - 1) - max(xg - p.r_lo, 0) + 1;
-                        const uint32_t n = (uint32_t)(nr * nc);
-                        const uint32_t S1 = base1 + d1[t], S2 = base2 + d2[t];
-                        const unsigned long long V = (unsigned long long)n * S2 - (unsigned long long)S1 * S1;
-                        const float ff = __uint2float_rn(byte_dyn(fw[qq], e));
-                        const float invn = rcp_approx(__uint2float_rn(n));
-                        dd[e] = filter_n<RULE>(ff, __uint2float_rn(S1), sqrt_approx(v_to_float(V)), invn, p);
-                        amb = amb || (xg < p.w && fabsf(dd[e]) < p.E);
-                    }
-                    const uint32_t lo = prmt(__float_as_uint(dd[0]), __float_as_uint(dd[1]), 0xFBu);
-                    const uint32_t hi = prmt(__float_as_uint(dd[2]), __float_as_uint(dd[3]), 0xFBu);
-                    outw[qq] = ~prmt(lo, hi, 0x5410u);
-                }
-            }
-            if (amb && active) { // rare: a value inside the fp32 margin -> fp64 for those pixels
-                const int nr = min(y + p.r_hi, p.h - 1) - max(y - p.r_lo, 0) + 1;
-                for (int t = 0; t < L; ++t) {
-                    const int xg = xg0 + t;
-                    if (xg >= p.w)
-                        break;
-                    const int nc = min(xg + p.r_hi, p.w - 1) - max(xg - p.r_lo, 0) + 1;
-                    const uint32_t n = (uint32_t)(nr * nc);
-                    uint32_t S1 = base1, S2 = base2;
-#pragma unroll
-                    for (int u = 0; u < L; ++u) // register arrays: select, never index dynamically
-                        if (u == t) {
-                            S1 += d1[u];
-                            S2 += d2[u];
-                        }
-                    const uint32_t f = byte_dyn(fw[t >> 2], t & 3);
-                    const unsigned long long V = (unsigned long long)n * S2 - (unsigned long long)S1 * S1;
-                    const float sq = sqrt_approx(v_to_float(V));
-                    const float d = (n == p.nW)
-                                        ? filter_int<RULE>(__uint2float_rn(f), __uint2float_rn(S1), sq, p)
-                                        : filter_n<RULE>(__uint2float_rn(f), __uint2float_rn(S1), sq,
-                                                         rcp_approx(__uint2float_rn(n)), p);
-                    if (fabsf(d) < p.E) {
-                        const uint32_t r = decide_fp64<RULE>(f, n, S1, S2, p);
-                        ++nfb;
-                        nties += (r >> 9) & 1u;
-                        const int sh = 8 * (t & 3);
-                        outw[t >> 2] = (outw[t >> 2] & ~(0xffu << sh)) | ((r & 0xffu) << sh);
-                    }
-                }
-            }
-            if (active && xg0 < p.w) {
-                if (!p.packed) {
-                    uint8_t *drow = p.dst + (size_t)y * p.dst_pitch + xg0;
-                    if (p.vec_ok && xg0 + L <= p.w) {
-                        *reinterpret_cast<uint4 *>(drow) = make_uint4(outw[0], outw[1], outw[2], outw[3]);
-                    } else {
-                        for (int t = 0; t < L && xg0 + t < p.w; ++t)
-                            drow[t] = (uint8_t)byte_dyn(outw[t >> 2], t & 3);
-                    }
-                } else {
-                    uint32_t bits = 0; // bit t <-> pixel xg0 + t: the msb of each byte
-#pragma unroll
-                    for (int qq = 0; qq < 4; ++qq)
-                        bits |= ((((outw[qq] >> 7) & 0x01010101u) * 0x01020408u) >> 24) << (4 * qq);
-                    const int valid = p.w - xg0;
-                    if (valid < L)
-                        bits &= (1u << valid) - 1u;
-                    uint8_t *drow = p.dst + (size_t)y * p.dst_pitch + (xg0 >> 3);
-                    drow[0] = (uint8_t)(bits & 0xffu);
-                    if (valid > 8)
-                        drow[1] = (uint8_t)(bits >> 8);
-                }
-            }
-        }
-        if (k + 2 < sg.nk)
-            bar_arrive(BAR_EMPTY + b, NT);
-    }
-}
 
 template <int CIN, int RULE, int WM8>
 __global__ void __launch_bounds__(NT, 1)
@@ -534,58 +47,25 @@ __global__ void __launch_bounds__(NT, 1)
 {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ int s_abort;
-    const int tid = threadIdx.x;
-    const bool producer = tid < NTP;
-    const int nbar = CIN == 1 ? p.NS : p.NSS;
-    if (tid == 0) {
-        uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
-        for (int i = 0; i < nbar; ++i)
-            mbar_init(&bars[i], 1);
-        fence_mbar_init();
-        fence_proxy_async_smem();
+    if (threadIdx.x == 0) {
+        init_barriers(smem, CIN == 1 ? p.NS : p.NSS);
         prefetch_tmap(&tmap);
         s_abort = 0;
     }
     __syncthreads();
-
     uint64_t phase = 0; // producers: bit i = parity to wait for next on barrier i
     uint32_t nfb = 0, nties = 0;
     const long long T = (long long)p.tiles_x * p.h;
     const long long L0 = T * blockIdx.x / gridDim.x, L1 = T * (blockIdx.x + 1) / gridDim.x;
     for (long long cur = L0; cur < L1;) {
-        Segment sg;
-        const int tx = (int)(cur / p.h);
-        sg.y0 = (int)(cur - (long long)tx * p.h);
-        sg.th_eff = (int)min((long long)(p.h - sg.y0), L1 - cur);
+        const Segment sg = make_segment(p, cur, L1);
         cur += sg.th_eff;
-        sg.x0 = tx * p.TW;
-        sg.xs = sg.x0 - p.r_lo - p.o; // span start column (multiple of 16, may be < 0)
-        sg.ys = sg.y0 - p.r_lo;       // first input row (may be < 0: zero-filled)
-        sg.nchk = (sg.th_eff + p.W - 1 + CH - 1) / CH;
-        sg.nk = (sg.th_eff + CH - 1) / CH;
-        if (producer)
-            produce<CIN>(&tmap, p, sg, smem, phase, &s_abort);
-        else
-            consume<CIN, RULE, WM8>(p, sg, smem, nfb, nties, &s_abort);
+        run_segment<CIN, RULE, WM8>(&tmap, p, sg, smem, phase, nfb, nties, &s_abort);
         __syncthreads(); // the next segment reuses the ring from slot 0
         if (s_abort)
             break;
     }
-
-#pragma unroll
-    for (int off = 16; off; off >>= 1) {
-        nfb += __shfl_xor_sync(0xffffffffu, nfb, off);
-        nties += __shfl_xor_sync(0xffffffffu, nties, off);
-    }
-    if ((tid & 31) == 0 && p.stats && (nfb | nties)) {
-        atomicAdd(&p.stats[BNZ_STATS_FALLBACKS], (unsigned long long)nfb);
-        atomicAdd(&p.stats[BNZ_STATS_TIES], (unsigned long long)nties);
-    }
-    if (s_abort && tid == 0) {
-        if (p.stats)
-            atomicAdd(&p.stats[BNZ_STATS_TIMEOUTS], 1ull);
-        atomicAdd(p.err_flag, 1u);
-    }
+    report(p.stats, p.err_flag, nfb, nties, s_abort != 0);
 }
 
 template <int CIN, int RULE>
@@ -636,9 +116,9 @@ bool layout(int ch, int W, int tw, int PWP, int CH, int NSS, FusedPlan *pl)
     pl->NSS = ch == 3 ? NSS : 0;
     pl->ring_rows = pl->NS * CH;
     const int nbar = std::max(pl->NS, pl->NSS);
-    if (nbar > 64)
+    if (nbar > kMaxBarriers)
         return false;
-    size_t off = round128((size_t)nbar * 8);
+    size_t off = round128((size_t)kMaxBarriers * 8); // same barrier area for every page of a batch
     pl->off_ring = (uint32_t)off;
     off = round128(off + (size_t)pl->NPAN * pl->ring_rows * PWP);
     pl->off_stage = (uint32_t)off;
@@ -705,18 +185,10 @@ void fill_decision_params(FusedParams *p, int h, int w, int W, int rule, double 
     p->E = decision_margin(rule, k, R);
 }
 
-int plan_fused(int h, int w, int ch, int W, const bnz_tile *tile, FusedPlan *pl)
+int plan_shape(int h, int w, int ch, int W, int want_tw, FusedPlan *pl)
 {
-    int sms = 0;
-    int rc = device_sm_count(&sms);
-    if (rc != BNZ_OK)
-        return rc;
-    const int want_tw = tile ? tile->tile_w : 0;
-    const int want_ch = tile && tile->chunk ? tile->chunk : 8;
-    if (want_ch != 8)
-        return fail(BNZ_EINVAL, "bnz_tile.chunk must be 0 or 8 (got %d)", want_ch);
     if (want_tw && want_tw != TW && want_tw != TW / 2 && want_tw != TW / 4)
-        return fail(BNZ_EINVAL, "bnz_tile.tile_w must be 0, 128, 256 or 512 (got %d)", want_tw);
+        return fail(BNZ_EINVAL, "tile width must be 0, 128, 256 or 512 (got %d)", want_tw);
     // widest strip first (least halo work), then narrower panels, then narrower strips
     const int pw[2] = {ch == 1 ? 128 : 80, ch == 1 ? 64 : 80};
     bool found = false;
@@ -725,11 +197,27 @@ int plan_fused(int h, int w, int ch, int W, const bnz_tile *tile, FusedPlan *pl)
             continue;
         for (int pi = 0; pi < 2 && !found; ++pi)
             for (int nss = 3; nss >= 2 && !found; --nss)
-                found = layout(ch, W, tw, pw[pi], want_ch, nss, pl);
+                found = layout(ch, W, tw, pw[pi], CH, nss, pl);
     }
     if (!found)
-        return fail(BNZ_EINVAL, "no tile shape fits shared memory for W=%d", W);
+        return fail(BNZ_EINVAL, "no tile shape fits shared memory for W=%d%s", W,
+                    want_tw ? " with the requested tile width" : "");
     pl->tiles_x = (w + pl->TW - 1) / pl->TW;
+    (void)h;
+    return BNZ_OK;
+}
+
+int plan_fused(int h, int w, int ch, int W, const bnz_tile *tile, FusedPlan *pl)
+{
+    int sms = 0;
+    int rc = device_sm_count(&sms);
+    if (rc != BNZ_OK)
+        return rc;
+    if (tile && tile->chunk && tile->chunk != CH)
+        return fail(BNZ_EINVAL, "bnz_tile.chunk must be 0 or %d (got %d)", CH, tile->chunk);
+    rc = plan_shape(h, w, ch, W, tile ? tile->tile_w : 0, pl);
+    if (rc != BNZ_OK)
+        return rc;
     int occ = 1;
     const void *fn = kernel_for(ch, BNZ_SAUVOLA, W);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl->smem);
@@ -751,6 +239,33 @@ int plan_fused(int h, int w, int ch, int W, const bnz_tile *tile, FusedPlan *pl)
     return BNZ_OK;
 }
 
+void fill_fused_params(FusedParams *p, const FusedPlan &pl, int h, int w, int W, int rule, double k, double R,
+                       uint8_t *d_dst, size_t dst_pitch, int packed, unsigned long long *d_stats, unsigned int *d_err)
+{
+    fill_decision_params(p, h, w, W, rule, k, R);
+    p->dst = d_dst;
+    p->dst_pitch = (long long)dst_pitch;
+    p->stats = d_stats;
+    p->err_flag = d_err;
+    p->o = pl.o;
+    p->TW = pl.TW;
+    p->CH = pl.CH;
+    p->NS = pl.NS;
+    p->NSS = pl.NSS;
+    p->NPAN = pl.NPAN;
+    p->SWP = pl.SWP;
+    p->RSW = pl.RSW;
+    p->ring_rows = pl.ring_rows;
+    p->tiles_x = pl.tiles_x;
+    p->off_ring = pl.off_ring;
+    p->off_stage = pl.off_stage;
+    p->off_cb = pl.off_cb;
+    p->PWP = pl.PWP;
+    p->packed = packed ? 1 : 0;
+    p->vec_ok = ((reinterpret_cast<uintptr_t>(d_dst) | dst_pitch) & 15u) == 0 ? 1 : 0;
+    p->timeout_cycles = 4000000000ll; // ~2 s at 2 GHz
+}
+
 int launch_fused(const uint8_t *d_src, size_t src_pitch, int h, int w, int ch, int W, int rule, double k, double R,
                  uint8_t *d_dst, size_t dst_pitch, int packed, const bnz_tile *tile, cudaStream_t stream,
                  unsigned long long *d_stats, unsigned int *d_err)
@@ -766,29 +281,7 @@ int launch_fused(const uint8_t *d_src, size_t src_pitch, int h, int w, int ch, i
     if (rc != BNZ_OK)
         return rc;
     FusedParams p;
-    fill_decision_params(&p, h, w, W, rule, k, R);
-    p.dst = d_dst;
-    p.dst_pitch = (long long)dst_pitch;
-    p.stats = d_stats;
-    p.err_flag = d_err;
-    p.o = pl.o;
-    p.TW = pl.TW;
-    p.CH = pl.CH;
-    p.NS = pl.NS;
-    p.NSS = pl.NSS;
-    p.NPAN = pl.NPAN;
-    p.SWP = pl.SWP;
-    p.RSW = pl.RSW;
-    p.ring_rows = pl.ring_rows;
-    p.tiles_x = pl.tiles_x;
-    p.off_ring = pl.off_ring;
-    p.off_stage = pl.off_stage;
-    p.off_cb = pl.off_cb;
-    p.PWP = pl.PWP;
-    p.packed = packed ? 1 : 0;
-    p.vec_ok = ((reinterpret_cast<uintptr_t>(d_dst) | dst_pitch) & 15u) == 0 ? 1 : 0;
-    p.s1_magic = 0;
-    p.timeout_cycles = 4000000000ll; // ~2 s at 2 GHz
+    fill_fused_params(&p, pl, h, w, W, rule, k, R, d_dst, dst_pitch, packed, d_stats, d_err);
     const void *fn = kernel_for(ch, rule, W);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
     if (e != cudaSuccess)

@@ -66,7 +66,14 @@ struct FusedParams {
     long long timeout_cycles;
 };
 
+// Shape of the fused kernel for one page (strip width, ring, shared-memory
+// offsets); want_tw = 0 picks the widest strip that fits.
+int plan_shape(int h, int w, int ch, int W, int want_tw, FusedPlan *plan);
 int plan_fused(int h, int w, int ch, int W, const bnz_tile *tile, FusedPlan *plan);
+void fill_fused_params(FusedParams *p, const FusedPlan &pl, int h, int w, int W, int rule, double k, double R,
+                       uint8_t *d_dst, size_t dst_pitch, int packed, unsigned long long *d_stats,
+                       unsigned int *d_err);
+constexpr int kMaxBarriers = 64; // mbarriers reserved at the start of shared memory
 int launch_fused(const uint8_t *d_src, size_t src_pitch, int h, int w, int ch, int W, int rule, double k,
                  double R, uint8_t *d_dst, size_t dst_pitch, int packed, const bnz_tile *tile,
                  cudaStream_t stream, unsigned long long *d_stats, unsigned int *d_err);
