@@ -53,7 +53,7 @@ def measured_peak():
 
 def fused_source_hash():
     h = hashlib.sha256()
-    for f in ("fused.cu", "ptx.cuh", "internal.h"):
+    for f in ("fused.cu", "segment.cuh", "decide.cuh", "ptx.cuh", "internal.h"):
         h.update(open(os.path.join(ROOT, "paper_1210_3165_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -370,6 +370,104 @@ def run_batch(args):
     return 0
 
 
+SERVE_WORKLOAD = "Poisson stream of uint8 RGB pages, width U[600,4960] x height U[800,7016], W odd U{15..101}, " \
+                 "Sauvola k=0.5 R=128 / Niblack k=-0.2 50/50, 16 GB device budget, pages from pinned host memory, " \
+                 "byte masks back to pinned host memory"
+SERVE_CANVAS = (7016, 4960)
+
+
+def serve_requests(n, seed, canvases):
+    """The trace's requests as crops of pinned host canvases (row pitch = the canvas's)."""
+    import numpy as np
+    import synth
+    trace = synth.serve_trace(n, seed=seed, rate_per_s=1.0)
+    rng = np.random.default_rng(seed + 1)
+    out = []
+    for i, tr in enumerate(trace):
+        cv = canvases[i % len(canvases)]
+        y0 = int(rng.integers(0, SERVE_CANVAS[0] - tr["h"] + 1))
+        x0 = int(rng.integers(0, SERVE_CANVAS[1] - tr["w"] + 1)) // 16 * 16   # 16-byte aligned device crops
+        out.append((tr, cv[y0:y0 + tr["h"], x0:x0 + tr["w"]]))
+    return out
+
+
+def serve_once(executor, reqs, rate, max_batch):
+    """Replay `reqs` (rate None: all at once, closed loop); returns pages/s and latency stats."""
+    from paper_1210_3165_gb300.serve import Request, Server
+    srv = Server(executor, max_batch=max_batch).start()
+    done_t = []
+    t0 = time.perf_counter() + 0.01
+    for tr, img in reqs:
+        due = t0 + (tr["t"] / rate if rate else 0.0)
+        now = time.perf_counter()
+        if due > now:
+            time.sleep(due - now)
+        r = Request(image=img, W=tr["W"], rule=tr["rule"], k=tr["k"], R=tr["R"], arrival=due)
+        r.future.add_done_callback(lambda f: done_t.append(time.perf_counter()))
+        srv.submit(r)
+    srv.stop(drain=True)
+    st = srv.stats()
+    st.update(pool=executor.pool.stats())
+    span = max(done_t) - t0
+    st.update(pages_per_s=len(reqs) / span, seconds=span, offered_pages_per_s=rate,
+              mpix_per_s=sum(tr["h"] * tr["w"] for tr, _ in reqs) / span / 1e6)
+    return st
+
+
+def run_serve(args):
+    """Continuous-batching server vs per-image launches on a Poisson stream of RGB pages."""
+    import torch
+    import synth
+    import paper_1210_3165_gb300 as bnz
+    from paper_1210_3165_gb300.serve import TorchExecutor
+    torch.cuda.set_device(0)
+    bnz.load()
+    ch, cw = SERVE_CANVAS
+    canvases = []
+    for j, prof in enumerate((synth.STAINS, synth.DOC, synth.VIGNETTE, synth.STAINS)):
+        canvases.append(torch.from_numpy(synth.page(ch, cw, 50 + j, prof, 3, random_dir=True)).pin_memory())
+    n = args.serve_requests
+    budget = 16 << 30
+    loads = [float(x) for x in args.serve_loads.split(",")]
+    exs = {"batched": TorchExecutor(batched=True, compute_streams=2, budget_bytes=budget),
+           "per_image": TorchExecutor(batched=False, budget_bytes=budget)}
+    modes = {}
+    # "host": pages in pinned host memory, H2D + kernel + D2H per request;
+    # "resident": pages already in device memory (crops of device canvases), kernel + D2H
+    dev_canvases = [c.to("cuda") for c in canvases]
+    for mode, cvs in (("host", canvases), ("resident", dev_canvases)):
+        reqs = serve_requests(n, 5, cvs)
+        res = {}
+        for name, ex in exs.items():
+            serve_once(ex, reqs[:64], None, args.max_batch)        # warm-up: tensor maps, pinned pool, clocks
+            res[name] = {"capacity": serve_once(ex, reqs[:min(n, args.serve_capacity)], None, args.max_batch),
+                         "loads": []}
+        cap_b = res["batched"]["capacity"]["pages_per_s"]
+        for name, ex in exs.items():
+            for ld in loads:
+                st = serve_once(ex, reqs, ld * cap_b, args.max_batch)
+                st["load"] = ld
+                res[name]["loads"].append(st)
+        modes[mode] = res
+    res = modes["host"]
+    top = res["batched"]["loads"][-1]
+    px = sum(tr["h"] * tr["w"] for tr, _ in reqs)
+    print(json.dumps({
+        "metric": METRIC, "value": round(top["pages_per_s"], 2), "unit": "pages/s", "n_gpus": 1,
+        "steps": n, "warmup": 16, "ms_per_step": 1e3 / top["pages_per_s"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": SERVE_WORKLOAD, "requests": n, "mean_mpix_per_page": round(px / n / 1e6, 3),
+                   "budget_bytes": budget, "max_batch": args.max_batch, "loads_of_batched_capacity": loads,
+                   "l2": "pages of 1.4-104 MB stream through; working set >> 129 MB L2"},
+        "p50_ms": round(top["p50_ms"], 3), "p99_ms": round(top["p99_ms"], 3),
+        "e2e": {"value": round(top["pages_per_s"], 2), "unit": "pages/s",
+                "h2d_bytes_per_step": px * 3 // n, "d2h_bytes_per_step": px // n},
+        "serve": modes, "gpu_launches": res["batched"]["loads"][-1]["steps"],
+        "device_memory_reserved_max": torch.cuda.max_memory_reserved(),
+    }))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -378,14 +476,21 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="page", choices=["page", "batch"],
-                    help="page: the 4096x4096 RGB page (default); batch: 256 uneven gray pages")
+    ap.add_argument("--workload", default="page", choices=["page", "batch", "serve"],
+                    help="page: the 4096x4096 RGB page (default); batch: 256 uneven gray pages; "
+                         "serve: Poisson stream of RGB pages through the serving loop")
+    ap.add_argument("--serve-requests", type=int, default=10000)
+    ap.add_argument("--serve-capacity", type=int, default=2000, help="requests of the closed-loop capacity run")
+    ap.add_argument("--serve-loads", default="0.5,0.8,0.95", help="offered loads, fractions of batched capacity")
+    ap.add_argument("--max-batch", type=int, default=16)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_ours(args)
 
 

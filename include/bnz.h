@@ -150,6 +150,15 @@ typedef struct bnz_batch bnz_batch; /* opaque */
  * nullable device counters as for bnz_binarize_dev.  On error *out is NULL. */
 BNZ_API int bnz_batch_create(const bnz_page *pages, int n, int use_graph, unsigned long long *d_stats,
                              bnz_batch **out);
+/* Bytes of device memory bnz_batch_create_async needs for n page descriptors. */
+BNZ_API size_t bnz_batch_desc_bytes(int n);
+/* Like bnz_batch_create without a graph and without allocating: the page
+ * descriptors go to caller-provided device memory d_desc (128-byte aligned,
+ * bnz_batch_desc_bytes(n) bytes) by a copy ordered on `stream`; run the batch
+ * on the same stream (or after it).  The batch keeps the host copy until it
+ * is destroyed; d_desc must outlive the batch's runs. */
+BNZ_API int bnz_batch_create_async(const bnz_page *pages, int n, void *d_desc, size_t desc_bytes, void *stream,
+                                   unsigned long long *d_stats, bnz_batch **out);
 /* Enqueue the whole batch on `stream` (one graph launch, or one kernel per channel count). */
 BNZ_API int bnz_batch_run(bnz_batch *b, void *stream);
 /* Pages, kernel launches per run, grid size, shared memory per CTA and total strip-rows. */
@@ -157,6 +166,34 @@ BNZ_API int bnz_batch_info(const bnz_batch *b, int *pages, int *launches, int *g
                            long long *strip_rows);
 /* Free the batch (after its last run has completed). */
 BNZ_API int bnz_batch_destroy(bnz_batch *b);
+
+/* ---- device-memory pool for the serving loop -----------------------------
+ * Host-side bookkeeping (first fit, neighbours coalesced on free) over one
+ * device range the caller allocated once, e.g. the serving loop's whole
+ * memory budget.  Requests of mixed page sizes get their input and output
+ * buffers from it without cudaMalloc/cudaFree, which would stall the device.
+ * The pool never reads or writes the range, so it also works over a range no
+ * device backs (tests).  Thread-safe.  No counterpart in the paper. */
+typedef struct bnz_pool bnz_pool; /* opaque */
+
+/* Manage [base, base+bytes); base must be 256-byte aligned.  The range stays
+ * owned by the caller and must outlive the pool. */
+BNZ_API int bnz_pool_create(void *base, size_t bytes, bnz_pool **out);
+/* 256-byte-aligned block of at least `bytes` bytes.  BNZ_ENOMEM (not an
+ * error to report: the caller waits for frees) when no free range fits. */
+BNZ_API int bnz_pool_alloc(bnz_pool *p, size_t bytes, void **out);
+/* Return a block.  The caller guarantees that no queued device work still
+ * uses it (the pool cannot see streams).  BNZ_EINVAL for a pointer that is
+ * not a live block of this pool. */
+BNZ_API int bnz_pool_free(bnz_pool *p, void *ptr);
+/* Bytes in live blocks, their high-water mark, the largest free range, and
+ * the number of live blocks; any pointer may be NULL. */
+BNZ_API int bnz_pool_stats(const bnz_pool *p, size_t *used, size_t *high_water, size_t *largest_free, int *live);
+/* Fault injection: the next n calls of bnz_pool_alloc fail with BNZ_ENOMEM
+ * (n=0 clears it).  Host-side only; nothing on the device is affected. */
+BNZ_API int bnz_pool_fail_next(bnz_pool *p, int n);
+/* Free the bookkeeping (live blocks are forgotten, the range is not freed). */
+BNZ_API int bnz_pool_destroy(bnz_pool *p);
 
 /* ---- integral-image comparison variant ------------------------------------
  * The O(N^2) method with summed-area tables that Sec. 1 cites (Shafait et
@@ -205,6 +242,16 @@ BNZ_API int bnz_binarize_integral_static_dev(const uint8_t *d_src, size_t src_pi
 
 /* Message for the calling thread's most recent failure ("" if none). */
 BNZ_API const char *bnz_last_error(void);
+
+/* Stream-ordered 2-D copy of `height` rows of `width_bytes` bytes between
+ * any two of host (pinned or pageable) and device memory (unified
+ * addressing decides the direction).  A copy-engine transfer, no kernel; the
+ * serving loop uses it to move pages between a caller's dense host buffers
+ * and the 16-byte-pitched device buffers the kernels read.  It has no
+ * counterpart in the paper.  Returns BNZ_EINVAL for a null pointer with a
+ * non-empty extent or a pitch below width_bytes. */
+BNZ_API int bnz_copy2d_async(void *dst, size_t dst_pitch, const void *src, size_t src_pitch, size_t width_bytes,
+                             size_t height, void *stream);
 
 /* Library ABI version (major*10000 + minor*100 + patch). */
 BNZ_API int bnz_version(void);

@@ -81,9 +81,19 @@ def _optional_symbols(lib):
     table = {
         "bnz_batch_create": ([P, i, i, P, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
         "bnz_batch_run": ([P, P], ctypes.c_int),
+        "bnz_batch_desc_bytes": ([i], ctypes.c_size_t),
+        "bnz_batch_create_async": ([P, i, P, sz, P, P, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
         "bnz_batch_info": ([P, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(sz),
                             ctypes.POINTER(ctypes.c_longlong)], ctypes.c_int),
         "bnz_batch_destroy": ([P], ctypes.c_int),
+        "bnz_copy2d_async": ([P, sz, P, sz, sz, sz, P], ctypes.c_int),
+        "bnz_pool_create": ([P, sz, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+        "bnz_pool_alloc": ([P, sz, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+        "bnz_pool_free": ([P, P], ctypes.c_int),
+        "bnz_pool_stats": ([P, ctypes.POINTER(sz), ctypes.POINTER(sz), ctypes.POINTER(sz), ctypes.POINTER(i)],
+                           ctypes.c_int),
+        "bnz_pool_fail_next": ([P, i], ctypes.c_int),
+        "bnz_pool_destroy": ([P], ctypes.c_int),
         "bnz_selftest_sqrt_approx": ([ctypes.c_float, ctypes.c_float, ctypes.POINTER(ctypes.c_double)],
                                      ctypes.c_int),
         "bnz_selftest_rcp_approx": ([ctypes.c_uint, ctypes.c_uint, ctypes.POINTER(ctypes.c_double)],
@@ -219,6 +229,12 @@ def bnz_niblack_dev(d_src, W: int, k: float, d_dst, packed: bool = False, stream
                                   d_stats.data_ptr() if d_stats is not None else None))
 
 
+def bnz_copy2d_async(dst: int, dst_pitch: int, src: int, src_pitch: int, width_bytes: int, height: int,
+                     stream=None) -> None:
+    """Stream-ordered 2-D copy between host and device pointers (a copy-engine transfer)."""
+    _check(load().bnz_copy2d_async(dst, dst_pitch, src, src_pitch, width_bytes, height, _stream_ptr(stream)))
+
+
 def bnz_integral_scratch_bytes(h: int, w: int) -> int:
     return load().bnz_integral_scratch_bytes(int(h), int(w))
 
@@ -272,7 +288,7 @@ class Batch:
     the same inputs and writes the same outputs every time.
     """
 
-    def __init__(self, pages, use_graph: bool = True, d_stats=None):
+    def __init__(self, pages, use_graph: bool = True, d_stats=None, desc_buffer=None, stream=None):
         arr = (bnz_page * len(pages))()
         self._keep = []
         for i, pg in enumerate(pages):
@@ -289,9 +305,21 @@ class Batch:
             self._keep += [pg["src"], dst]
         self._stats = d_stats
         h = ctypes.c_void_p(None)
-        _check(load().bnz_batch_create(ctypes.cast(arr, ctypes.c_void_p), len(pages), 1 if use_graph else 0,
-                                       d_stats.data_ptr() if d_stats is not None else None, ctypes.byref(h)))
+        stats_ptr = d_stats.data_ptr() if d_stats is not None else None
+        if desc_buffer is not None:  # no allocation: descriptors into the caller's buffer, ordered on `stream`
+            self._keep.append(desc_buffer)
+            _check(load().bnz_batch_create_async(ctypes.cast(arr, ctypes.c_void_p), len(pages),
+                                                 desc_buffer.data_ptr(),
+                                                 desc_buffer.numel() * desc_buffer.element_size(),
+                                                 _stream_ptr(stream), stats_ptr, ctypes.byref(h)))
+        else:
+            _check(load().bnz_batch_create(ctypes.cast(arr, ctypes.c_void_p), len(pages), 1 if use_graph else 0,
+                                           stats_ptr, ctypes.byref(h)))
         self._h = h
+
+    @staticmethod
+    def desc_bytes(n: int) -> int:
+        return load().bnz_batch_desc_bytes(int(n))
 
     def run(self, stream=None) -> None:
         _check(load().bnz_batch_run(self._h, _stream_ptr(stream)))
@@ -306,6 +334,53 @@ class Batch:
     def close(self) -> None:
         if self._h:
             load().bnz_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Pool:
+    """First-fit bookkeeping over one caller-owned device range (``bnz_pool_*``).
+
+    ``base`` is an address (int) or a CUDA tensor whose memory the pool carves up; the tensor is kept
+    alive.  ``alloc`` returns an address, or None when no free range fits (BNZ_ENOMEM)."""
+
+    def __init__(self, base, nbytes: int | None = None):
+        self._owner = None
+        if not isinstance(base, int):
+            self._owner = base
+            nbytes = base.numel() * base.element_size() if nbytes is None else nbytes
+            base = base.data_ptr()
+        h = ctypes.c_void_p(None)
+        _check(load().bnz_pool_create(ctypes.c_void_p(base), int(nbytes), ctypes.byref(h)))
+        self._h, self.base, self.nbytes = h, base, int(nbytes)
+
+    def alloc(self, nbytes: int):
+        out = ctypes.c_void_p(None)
+        rc = load().bnz_pool_alloc(self._h, int(nbytes), ctypes.byref(out))
+        if rc == BNZ_ENOMEM:
+            return None
+        _check(rc)
+        return out.value
+
+    def free(self, ptr: int) -> None:
+        _check(load().bnz_pool_free(self._h, ctypes.c_void_p(ptr)))
+
+    def stats(self) -> dict:
+        u, hw, lf, n = ctypes.c_size_t(0), ctypes.c_size_t(0), ctypes.c_size_t(0), ctypes.c_int(0)
+        _check(load().bnz_pool_stats(self._h, ctypes.byref(u), ctypes.byref(hw), ctypes.byref(lf), ctypes.byref(n)))
+        return dict(used=u.value, high_water=hw.value, largest_free=lf.value, live=n.value)
+
+    def fail_next(self, n: int) -> None:
+        _check(load().bnz_pool_fail_next(self._h, int(n)))
+
+    def close(self) -> None:
+        if self._h:
+            load().bnz_pool_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -330,6 +330,22 @@ int bnz_integral_images_dev(const uint8_t *d_src, size_t src_pitch, int height, 
 
 const char *bnz_last_error(void) { return t_err.c_str(); }
 
+int bnz_copy2d_async(void *dst, size_t dst_pitch, const void *src, size_t src_pitch, size_t width_bytes,
+                     size_t height, void *stream)
+{
+    if (width_bytes == 0 || height == 0)
+        return BNZ_OK;
+    if (!dst || !src || dst_pitch < width_bytes || src_pitch < width_bytes)
+        return fail(BNZ_EINVAL, "bnz_copy2d_async: null pointer or pitch below the row width");
+    int dev = 0;
+    int rc = current_device(&dev);
+    if (rc != BNZ_OK)
+        return rc;
+    cudaError_t e = cudaMemcpy2DAsync(dst, dst_pitch, src, src_pitch, width_bytes, height, cudaMemcpyDefault,
+                                      static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? BNZ_OK : cuda_fail(e, "cudaMemcpy2DAsync");
+}
+
 int bnz_version(void) { return 100; }
 
 int bnz_fused_plan(int height, int width, int channels, int W, const bnz_tile *tile, size_t *smem_bytes,

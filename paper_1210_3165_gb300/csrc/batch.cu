@@ -20,8 +20,8 @@
 namespace bnz {
 namespace {
 
-struct alignas(64) PageDesc {
-    CUtensorMap map;  // 128 bytes, 64-byte aligned: TMA reads it from global memory
+struct alignas(128) PageDesc {
+    CUtensorMap map;  // 128 bytes, 128-byte aligned (as cuda.h declares it): TMA reads it from global memory
     FusedParams p;
     long long t0;     // first strip-row of this page in the batch's index range
     int sel;          // rule * 8 + (W mod 8)
@@ -96,6 +96,7 @@ struct Group {
     int ch = 0;
     std::vector<PageDesc> host;
     PageDesc *dev = nullptr;
+    bool owned = false; // dev allocated by the batch (freed with it)
     long long total = 0;
     size_t smem = 0;
     int grid = 0;
@@ -112,6 +113,7 @@ struct bnz_batch {
     unsigned long long *stats = nullptr;
     unsigned int *err = nullptr;
     int device = 0;
+    cudaStream_t pending = nullptr; // stream of a stream-ordered descriptor upload
 };
 
 namespace bnz {
@@ -151,8 +153,10 @@ void free_batch(bnz_batch *b)
         cudaGraphExecDestroy(b->exec);
     if (b->graph)
         cudaGraphDestroy(b->graph);
+    if (b->pending) // the host copies may still be the source of a stream-ordered upload
+        cudaStreamSynchronize(b->pending);
     for (Group &g : b->groups)
-        if (g.dev)
+        if (g.dev && g.owned)
             cudaFree(g.dev);
     delete b;
 }
@@ -164,7 +168,7 @@ using namespace bnz;
 
 extern "C" {
 
-int bnz_batch_create(const bnz_page *pages, int n, int use_graph, unsigned long long *d_stats, bnz_batch **out)
+static int plan_batch(const bnz_page *pages, int n, unsigned long long *d_stats, bnz_batch **out)
 {
     if (!out)
         return fail(BNZ_EINVAL, "null output handle");
@@ -231,15 +235,36 @@ int bnz_batch_create(const bnz_page *pages, int n, int use_graph, unsigned long 
         int occ = 1;
         if (e == cudaSuccess)
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, NT, g.smem);
-        if (e == cudaSuccess)
-            e = cudaMalloc(&g.dev, g.host.size() * sizeof(PageDesc));
-        if (e == cudaSuccess)
-            e = cudaMemcpy(g.dev, g.host.data(), g.host.size() * sizeof(PageDesc), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {
             free_batch(b);
             return cuda_fail(e, "batch set-up");
         }
         g.grid = (int)std::max<long long>(1, std::min<long long>((long long)sms * std::max(occ, 1), g.total / 32 + 1));
+    }
+    *out = b;
+    return BNZ_OK;
+}
+
+int bnz_batch_create(const bnz_page *pages, int n, int use_graph, unsigned long long *d_stats, bnz_batch **out)
+{
+    bnz_batch *b = nullptr;
+    int rc = plan_batch(pages, n, d_stats, &b);
+    if (rc != BNZ_OK)
+        return rc;
+    for (Group &g : b->groups) {
+        if (g.host.empty())
+            continue;
+        void *p = nullptr;
+        cudaError_t e = cudaMalloc(&p, g.host.size() * sizeof(PageDesc));
+        if (e == cudaSuccess) {
+            g.dev = static_cast<PageDesc *>(p);
+            g.owned = true;
+            e = cudaMemcpy(g.dev, g.host.data(), g.host.size() * sizeof(PageDesc), cudaMemcpyHostToDevice);
+        }
+        if (e != cudaSuccess) {
+            free_batch(b);
+            return cuda_fail(e, "batch descriptors");
+        }
     }
     if (use_graph) {
         cudaStream_t s = nullptr;
@@ -261,6 +286,35 @@ int bnz_batch_create(const bnz_page *pages, int n, int use_graph, unsigned long 
             return rc != BNZ_OK ? rc : cuda_fail(e, "capture batch graph");
         }
     }
+    *out = b;
+    return BNZ_OK;
+}
+
+size_t bnz_batch_desc_bytes(int n) { return n > 0 ? (size_t)n * sizeof(PageDesc) : 0; }
+
+int bnz_batch_create_async(const bnz_page *pages, int n, void *d_desc, size_t desc_bytes, void *stream,
+                           unsigned long long *d_stats, bnz_batch **out)
+{
+    if (!d_desc || (reinterpret_cast<uintptr_t>(d_desc) & 127u) || desc_bytes < bnz_batch_desc_bytes(n))
+        return fail(BNZ_EINVAL, "d_desc must be 128-byte aligned device memory of bnz_batch_desc_bytes(n) bytes");
+    bnz_batch *b = nullptr;
+    int rc = plan_batch(pages, n, d_stats, &b);
+    if (rc != BNZ_OK)
+        return rc;
+    PageDesc *next = static_cast<PageDesc *>(d_desc);
+    for (Group &g : b->groups) {
+        if (g.host.empty())
+            continue;
+        g.dev = next;
+        next += g.host.size();
+        cudaError_t e = cudaMemcpyAsync(g.dev, g.host.data(), g.host.size() * sizeof(PageDesc),
+                                        cudaMemcpyHostToDevice, static_cast<cudaStream_t>(stream));
+        if (e != cudaSuccess) {
+            free_batch(b);
+            return cuda_fail(e, "batch descriptors");
+        }
+    }
+    b->pending = static_cast<cudaStream_t>(stream);
     *out = b;
     return BNZ_OK;
 }

@@ -1,0 +1,368 @@
+"""Serving loop: continuous batching of binarization requests on one GPU.
+
+Requests (uint8 gray or RGB pages with their own W, rule, k, R) arrive at any
+time through ``Server.submit``.  A scheduler thread
+
+* admits waiting requests in arrival order while their device memory (input +
+  output) fits the budget; a request that does not fit waits (it is never
+  dropped) until finished requests release memory;
+* copies each admitted page to the device on a copy stream;
+* every step, launches one batched kernel (``bnz_batch_create_async``: one
+  persistent launch over all pages of the step, no allocation) over all
+  admitted pages whose input has arrived, on one of several compute streams,
+  so that consecutive steps -- and copies -- overlap on the device;
+* copies finished masks back and completes the requests' futures, recording
+  the latency from arrival to result.
+
+With ``batched=False`` the same loop launches the plain single-page kernel
+once per page on one compute stream: the per-image baseline.
+
+The GPU operations live behind a small executor interface (``TorchExecutor``)
+so the scheduling logic can be tested without a GPU.
+"""
+from __future__ import annotations
+
+import collections
+import threading
+import time
+from concurrent.futures import Future
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class Request:
+    image: object            # uint8 HxW or HxWx3: host array/tensor (pinned for overlap), or a CUDA
+                             # tensor with a 16-byte row pitch already resident in device memory
+    W: int
+    rule: str = "sauvola"
+    k: float | None = None
+    R: float = 128.0
+    packed: bool = False
+    timeout_s: float | None = None   # give up (TimeoutError) if not admitted within this time
+    arrival: float = 0.0     # time.perf_counter() of arrival (submit stamps it when left 0)
+    future: Future = field(default_factory=Future)
+    # scheduler bookkeeping
+    nbytes: int = 0
+    slot: object = None
+    stage: str = "waiting"
+    done_at: float = 0.0
+
+    @property
+    def shape(self):
+        return tuple(self.image.shape)
+
+
+class Rejected(RuntimeError):
+    """The request can never fit the device-memory budget."""
+
+
+def request_bytes(h: int, w: int, ch: int, packed: bool = False, with_input: bool = True) -> int:
+    """Device bytes a request holds: pitched input (unless already on the device) plus output."""
+    pitch = (w * ch + 15) // 16 * 16 if with_input else 0
+    out_pitch = (((w + 7) // 8 if packed else w) + 15) // 16 * 16
+    return h * (pitch + out_pitch)
+
+
+def on_device(img) -> bool:
+    return bool(getattr(img, "is_cuda", False))
+
+
+class Server:
+    def __init__(self, executor, budget_bytes: int | None = None, max_batch: int = 64, poll_s: float = 50e-6):
+        self.ex = executor
+        if budget_bytes is None:
+            budget_bytes = getattr(executor, "budget_bytes", 16 << 30)
+        self.budget = int(budget_bytes)
+        self.max_batch = max_batch
+        self.poll_s = poll_s
+        self.reserved = 0
+        self.high_water = 0
+        self.latencies: list[float] = []
+        self.completed = 0
+        self._waiting: collections.deque[Request] = collections.deque()
+        self._lock = threading.Lock()
+        self._admitted: list[Request] = []   # input copy in flight
+        self._ready: list[Request] = []      # on the device, not launched
+        self._steps: list[tuple[object, list[Request], object]] = []  # (event, requests, keep-alive)
+        self._back: list[tuple[object, Request, object]] = []          # (event, request, host result)
+        self._stop = threading.Event()
+        self._thread: threading.Thread | None = None
+        self.steps_launched = 0
+        self._outstanding = 0                # submitted and not yet completed
+        self.alloc_waits = 0                 # admissions deferred because the pool had no fitting range
+        self.timed_out = 0
+        self.cancelled = 0
+
+    # ---- client side --------------------------------------------------------
+    def submit(self, req: Request) -> Future:
+        h, w = req.shape[:2]
+        ch = 1 if len(req.shape) == 2 else 3
+        req.nbytes = request_bytes(h, w, ch, req.packed, with_input=not on_device(req.image))
+        if not req.arrival:        # a caller replaying a trace may stamp the scheduled arrival itself
+            req.arrival = time.perf_counter()
+        if req.nbytes > self.budget:
+            req.future.set_exception(Rejected(f"a {h}x{w}x{ch} page needs {req.nbytes} bytes, "
+                                              f"more than the {self.budget}-byte budget"))
+            return req.future
+        with self._lock:
+            self._waiting.append(req)
+            self._outstanding += 1
+        return req.future
+
+    def start(self):
+        self._thread = threading.Thread(target=self._loop, name="bnz-serve", daemon=True)
+        self._thread.start()
+        return self
+
+    def stop(self, drain: bool = True, timeout: float | None = None):
+        if drain:
+            t0 = time.perf_counter()
+            while self.pending() and (timeout is None or time.perf_counter() - t0 < timeout):
+                time.sleep(1e-3)
+        self._stop.set()
+        if self._thread:
+            self._thread.join()
+
+    def pending(self) -> int:
+        """Requests submitted and not yet completed (safe to call from any thread)."""
+        with self._lock:
+            return self._outstanding
+
+    def stats(self) -> dict:
+        lat = np.array(self.latencies) if self.latencies else np.zeros(1)
+        return dict(completed=self.completed, steps=self.steps_launched, alloc_waits=self.alloc_waits,
+                    timed_out=self.timed_out, cancelled=self.cancelled,
+                    p50_ms=float(np.percentile(lat, 50) * 1e3), p99_ms=float(np.percentile(lat, 99) * 1e3),
+                    max_ms=float(lat.max() * 1e3), high_water_bytes=self.high_water)
+
+    # ---- scheduler ----------------------------------------------------------
+    def step(self) -> bool:
+        """One scheduler iteration; returns True if anything moved."""
+        moved = False
+        # 1. admission, in arrival order, while the budget and the pool allow
+        now = time.perf_counter()
+        while True:
+            with self._lock:
+                if not self._waiting:
+                    break
+                req = self._waiting[0]
+                if req.timeout_s is not None and now - req.arrival > req.timeout_s:
+                    self._waiting.popleft()
+                    self._outstanding -= 1
+                    self.timed_out += 1
+                    req.future.set_exception(TimeoutError(f"not admitted within {req.timeout_s} s"))
+                    continue
+                if req.future.cancelled():
+                    self._waiting.popleft()
+                    self._outstanding -= 1
+                    self.cancelled += 1
+                    continue
+                if self.reserved + req.nbytes > self.budget:
+                    break
+            slot = self.ex.alloc(req)
+            if slot is None:             # no free range fits (fragmentation, injected failure): wait
+                self.alloc_waits += 1
+                break
+            with self._lock:
+                self._waiting.popleft()
+            if not req.future.set_running_or_notify_cancel():   # cancelled just now
+                self.ex.release(slot)
+                with self._lock:
+                    self._outstanding -= 1
+                self.cancelled += 1
+                continue
+            self.reserved += req.nbytes
+            self.high_water = max(self.high_water, self.reserved)
+            req.slot = slot
+            req.h2d_event = self.ex.h2d(req.slot, req)
+            req.stage = "h2d"
+            self._admitted.append(req)
+            moved = True
+        # 2. inputs that have landed become launchable (copies complete in
+        #    issue order: stop at the first one still in flight)
+        n = 0
+        for req in self._admitted:
+            if not self.ex.done(req.h2d_event):
+                break
+            req.stage = "ready"
+            self._ready.append(req)
+            n += 1
+        if n:
+            del self._admitted[:n]
+            moved = True
+        # 3. launch one step over the ready pages
+        if self._ready and self.ex.can_launch():
+            batch, self._ready = self._ready[:self.max_batch], self._ready[self.max_batch:]
+            event, keep = self.ex.launch([r.slot for r in batch])
+            for r in batch:
+                r.stage = "running"
+            self._steps.append((event, batch, keep))
+            self.steps_launched += 1
+            moved = True
+        # 4. finished steps: results back to the host
+        still_steps = []
+        for event, batch, keep in self._steps:
+            if self.ex.done(event):
+                for r in batch:
+                    ev, host = self.ex.d2h(r.slot)
+                    r.stage = "d2h"
+                    self._back.append((ev, r, host))
+                moved = True
+            else:
+                still_steps.append((event, batch, keep))
+        self._steps = still_steps
+        # 5. delivered results (in issue order): complete, release memory
+        n = 0
+        for ev, r, host in self._back:
+            if not self.ex.done(ev):
+                break
+            r.done_at = time.perf_counter()
+            self.latencies.append(r.done_at - r.arrival)
+            self.ex.release(r.slot)
+            r.slot = None
+            self.reserved -= r.nbytes
+            self.completed += 1
+            with self._lock:
+                self._outstanding -= 1
+            r.stage = "done"
+            r.future.set_result(host)
+            n += 1
+        if n:
+            del self._back[:n]
+            moved = True
+        return moved
+
+    def _loop(self):
+        while not self._stop.is_set():
+            if not self.step():
+                time.sleep(self.poll_s)
+
+
+class TorchExecutor:
+    """GPU side of the server: torch memory and streams, the bnz kernels."""
+
+    def __init__(self, batched: bool = True, compute_streams: int = 2, tile_table=None, device="cuda",
+                 budget_bytes: int = 16 << 30):
+        import torch
+        from . import BNZ_NIBLACK, BNZ_SAUVOLA, Batch, Pool, bnz_binarize_dev, bnz_copy2d_async, load
+        from .tune import tile_for
+        load()
+        self.torch = torch
+        self.dev = torch.device(device)
+        # the whole budget is reserved once; requests get their buffers from the pool over it
+        self.budget_bytes = int(budget_bytes)
+        self.arena = torch.empty((self.budget_bytes,), dtype=torch.uint8, device=self.dev)
+        self.pool = Pool(self.arena)
+        self.batched = batched
+        self.copy_in = torch.cuda.Stream(self.dev)
+        self.copy_out = torch.cuda.Stream(self.dev)
+        self.compute = [torch.cuda.Stream(self.dev) for _ in range(max(1, compute_streams if batched else 1))]
+        self._rr = 0
+        self._inflight = [None] * len(self.compute)
+        self._Batch = Batch
+        self._single = bnz_binarize_dev
+        self._copy2d = bnz_copy2d_async
+        self._rules = {"sauvola": BNZ_SAUVOLA, "niblack": BNZ_NIBLACK}
+        self._table = tile_table
+        self._tile_for = tile_for
+
+    def alloc(self, req):
+        """Input (unless resident) and output buffers, 16-byte row pitch, in one pool block; None if none fits."""
+        h, w = req.shape[:2]
+        ch = 1 if len(req.shape) == 2 else 3
+        resident = on_device(req.image)
+        pin = 0 if resident else (w * ch + 15) // 16 * 16
+        ow = (w + 7) // 8 if req.packed else w
+        pout = (ow + 15) // 16 * 16
+        off_out = (h * pin + 255) // 256 * 256
+        ptr = self.pool.alloc(off_out + h * pout)
+        if ptr is None:
+            return None
+        off = ptr - self.pool.base
+        st = self.torch.as_strided
+        if resident:
+            src = req.image
+        elif ch == 1:
+            src = st(self.arena, (h, w), (pin, 1), off)
+        else:
+            src = st(self.arena, (h, w, 3), (pin, 3, 1), off)
+        dst = st(self.arena, (h, ow), (pout, 1), off + off_out)
+        return dict(req=req, src=src, dst=dst, ch=ch, ptr=ptr)
+
+    def h2d(self, slot, req):
+        torch = self.torch
+        if on_device(req.image):
+            # already in device memory: order after the work queued so far on the producer's stream
+            ev = torch.cuda.Event()
+            ev.record(torch.cuda.current_stream(self.dev))
+            return ev
+        img = req.image if isinstance(req.image, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(req.image))
+        h, w = img.shape[:2]
+        ch = slot["ch"]
+        # any row pitch on the host (a crop of a larger pinned canvas, say); rows themselves dense
+        if (w > 1 and img.stride(1) != ch) or (ch == 3 and img.stride(2) != 1):
+            img = img.contiguous()
+        row = w * ch
+        src = slot["src"]
+        self._copy2d(src.data_ptr(), src.stride(0), img.data_ptr(), img.stride(0) if h > 1 else row, row, h,
+                     self.copy_in)
+        ev = torch.cuda.Event()
+        ev.record(self.copy_in)
+        slot["host_in"] = img      # kept alive until the copy has completed
+        return ev
+
+    def done(self, ev) -> bool:
+        return ev.query()
+
+    def can_launch(self) -> bool:
+        # at most one step in flight per compute stream
+        s = self._inflight[self._rr]
+        return s is None or s.query()
+
+    def launch(self, slots):
+        torch = self.torch
+        stream = self.compute[self._rr]
+        self._rr = (self._rr + 1) % len(self.compute)
+        keep = []
+        with torch.cuda.stream(stream):
+            if self.batched:
+                pages = []
+                for sl in slots:
+                    r = sl["req"]
+                    k = r.k if r.k is not None else (0.5 if r.rule == "sauvola" else -0.2)
+                    tw = self._tile_for(self._table, sl["ch"], r.W) if self._table else 0
+                    pages.append(dict(src=sl["src"], dst=sl["dst"], W=r.W, rule=r.rule, k=k, R=r.R,
+                                      packed=r.packed, tile_w=tw))
+                # descriptors in stream-ordered torch memory: no cudaMalloc once the cache is warm
+                desc = torch.empty(((self._Batch.desc_bytes(len(pages)) + 7) // 8,), dtype=torch.int64,
+                                   device=self.dev)
+                b = self._Batch(pages, desc_buffer=desc, stream=stream)
+                b.run(stream)
+                keep += [b, desc]
+            else:
+                for sl in slots:
+                    r = sl["req"]
+                    k = r.k if r.k is not None else (0.5 if r.rule == "sauvola" else -0.2)
+                    self._single(sl["src"], r.W, self._rules[r.rule], k, r.R, sl["dst"], packed=r.packed,
+                                 stream=stream)
+            ev = torch.cuda.Event()
+            ev.record(stream)
+        self._inflight[(self._rr - 1) % len(self.compute)] = ev
+        return ev, keep
+
+    def d2h(self, slot):
+        torch = self.torch
+        dst = slot["dst"]
+        h, wb = dst.shape
+        host = torch.empty((h, wb), dtype=torch.uint8, pin_memory=True)
+        self._copy2d(host.data_ptr(), wb, dst.data_ptr(), dst.stride(0) if h > 1 else wb, wb, h, self.copy_out)
+        ev = torch.cuda.Event()
+        ev.record(self.copy_out)
+        slot["host_out"] = host
+        return ev, host
+
+    def release(self, slot):
+        self.pool.free(slot["ptr"])
+        slot.clear()

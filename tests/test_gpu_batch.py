@@ -61,6 +61,40 @@ def test_batch_matches_single_page_and_oracle(bnz, use_graph):
     b.close()
 
 
+def test_async_batch_in_caller_memory_on_a_stream(bnz):
+    """bnz_batch_create_async: descriptors uploaded into caller memory on the stream the batch then runs on."""
+    pages, hosts = make_pages(bnz, SPECS)
+    stream = torch.cuda.Stream()
+    desc = bnz.alloc_scratch(bnz.Batch.desc_bytes(len(pages)))
+    assert desc.data_ptr() % 128 == 0
+    with pytest.raises(bnz.BnzError) as e:  # too small a descriptor buffer
+        bnz.Batch(pages, desc_buffer=desc[:1], stream=stream)
+    assert e.value.status == bnz.BNZ_EINVAL
+    torch.cuda.synchronize()
+    b = bnz.Batch(pages, desc_buffer=desc, stream=stream)
+    assert b.info()["launches"] == 2
+    b.run(stream)
+    stream.synchronize()
+    for pg, img, (h, w, ch, W, rule, packed, _) in zip(pages, hosts, SPECS):
+        rid = oracle.SAUVOLA if rule == "sauvola" else oracle.NIBLACK
+        ref, _ = oracle.binarize(img, W, rid, pg["k"], 128.0, threads=NTHREADS, packed=packed)
+        np.testing.assert_array_equal(pg["dst"].cpu().numpy(), ref)
+    b.close()
+
+
+def test_copy2d_round_trip(bnz):
+    host = torch.from_numpy(np.arange(37 * 53, dtype=np.int64).astype(np.uint8).reshape(37, 53)).pin_memory()
+    dev = bnz.alloc_pitched(37, 53)
+    s = torch.cuda.Stream()
+    bnz.bnz_copy2d_async(dev.data_ptr(), dev.stride(0), host.data_ptr(), 53, 53, 37, s)
+    back = torch.empty((37, 53), dtype=torch.uint8, pin_memory=True)
+    bnz.bnz_copy2d_async(back.data_ptr(), 53, dev.data_ptr(), dev.stride(0), 53, 37, s)
+    s.synchronize()
+    assert torch.equal(back, host) and torch.equal(dev.cpu(), host)
+    with pytest.raises(bnz.BnzError):
+        bnz.bnz_copy2d_async(dev.data_ptr(), 16, host.data_ptr(), 53, 53, 37, s)
+
+
 def test_batch_rejects_a_bad_page(bnz):
     pages, _ = make_pages(bnz, SPECS[:3])
     pages[1]["W"] = 0

@@ -1,0 +1,65 @@
+"""Serving loop on the GPU: every request's mask, served in a mix of uneven
+pages with other windows and rules, equals the same page binarized alone and
+the oracle's mask."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+NTHREADS = os.cpu_count() or 4
+
+
+@pytest.fixture(scope="module")
+def bnz():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1210_3165_gb300 as b
+    b.load()
+    return b
+
+
+def mix(n, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        h, w = int(rng.integers(1, 700)), int(rng.integers(1, 900))
+        ch = 3 if i % 3 == 0 else 1
+        W = int(rng.choice([3, 15, 31, 61, 101]))
+        rule = "sauvola" if i % 2 == 0 else "niblack"
+        packed = i % 5 == 4
+        img = synth.page(h, w, 900 + i, synth.STAINS if ch == 3 else synth.DOC, ch, random_dir=True)
+        out.append((img, W, rule, packed))
+    return out
+
+
+@pytest.mark.parametrize("batched", [True, False])
+def test_served_masks_equal_alone_and_oracle(bnz, batched):
+    from paper_1210_3165_gb300.serve import Request, Server, TorchExecutor
+    items = mix(30, 7)
+    # a budget that holds only a few pages at a time, so admission has to wait
+    ex = TorchExecutor(batched=batched, compute_streams=2, budget_bytes=4 << 20)
+    srv = Server(ex, max_batch=8).start()
+    futs = []
+    for i, (img, W, rule, packed) in enumerate(items):
+        # most pages come from pinned host memory, every fourth is already resident on the device
+        src = bnz.to_device_pitched(img) if i % 4 == 3 else torch.from_numpy(img).pin_memory()
+        futs.append(srv.submit(Request(image=src, W=W, rule=rule, packed=packed)))
+    srv.stop(drain=True, timeout=120)
+    assert srv.reserved == 0 and srv.high_water <= 4 << 20
+    st = ex.pool.stats()
+    assert st["used"] == 0 and st["high_water"] <= 4 << 20
+    for (img, W, rule, packed), f in zip(items, futs):
+        got = f.result(timeout=0).numpy()
+        k = 0.5 if rule == "sauvola" else -0.2
+        alone = bnz.binarize(bnz.to_device_pitched(img), W, rule, k, packed=packed).cpu().numpy()
+        np.testing.assert_array_equal(got, alone)
+        rid = oracle.SAUVOLA if rule == "sauvola" else oracle.NIBLACK
+        ref, _ = oracle.binarize(img, W, rid, k, 128.0, threads=NTHREADS, packed=packed)
+        np.testing.assert_array_equal(got, ref)
+    if batched:
+        assert srv.steps_launched < len(items)   # pages shared launches
