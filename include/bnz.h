@@ -103,6 +103,9 @@ BNZ_API int bnz_niblack(const uint8_t *src, int height, int width, int channels,
 /* ---- asynchronous device-pointer API -------------------------------------
  * d_src: device pointer, 16-byte aligned, rows src_pitch bytes apart,
  *   src_pitch a multiple of 16 and >= width*channels (TMA requirement).
+ *   The buffer spans height * src_pitch bytes: the kernels read rows in
+ *   8-byte units, so up to 7 padding bytes after a row's last pixel may be
+ *   read (never used, never written).
  * d_dst: device pointer, rows dst_pitch bytes apart (>= width, or
  *   >= (width+7)/8 when packed).
  * stream: a cudaStream_t (NULL = legacy default stream).
@@ -131,7 +134,7 @@ BNZ_API int bnz_binarize_dev(const uint8_t *d_src, size_t src_pitch, int height,
  * buffers (refill the inputs between runs).  With use_graph != 0 the
  * launches are captured once into a CUDA graph and bnz_batch_run replays it. */
 typedef struct {
-    const uint8_t *d_src; /* device, 16-byte aligned, src_pitch % 16 == 0 */
+    const uint8_t *d_src; /* device, 16-byte aligned, src_pitch % 16 == 0, height*src_pitch bytes */
     size_t src_pitch;
     int height, width, channels; /* channels 1 or 3 */
     int W, rule, packed;         /* as bnz_binarize_dev */

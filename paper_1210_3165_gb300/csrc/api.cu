@@ -43,8 +43,8 @@ static const int kMaxDev = 64;
 static int g_sms[kMaxDev];
 static unsigned int *g_err[kMaxDev];
 
-int encode_u8_map(CUtensorMap *map, const void *base, uint64_t inner_bytes, uint64_t rows, uint64_t pitch,
-                  uint32_t box_inner, uint32_t box_rows)
+int encode_span_map(CUtensorMap *map, const void *base, uint64_t row_bytes, uint64_t rows, uint64_t pitch,
+                    uint32_t box_bytes, uint32_t box_rows)
 {
     {
         std::lock_guard<std::mutex> lk(g_mu);
@@ -58,16 +58,18 @@ int encode_u8_map(CUtensorMap *map, const void *base, uint64_t inner_bytes, uint
             g_encode = reinterpret_cast<EncodeTiledFn>(fn);
         }
     }
-    cuuint64_t dims[2] = {(cuuint64_t)inner_bytes, (cuuint64_t)rows};
+    if ((box_bytes & 15u) || box_bytes / 8 > 256 || box_rows < 1 || box_rows > 256)
+        return fail(BNZ_EINVAL, "span box %ux%u out of range", box_bytes, box_rows);
+    cuuint64_t dims[2] = {(cuuint64_t)((row_bytes + 7) / 8), (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)pitch};
-    cuuint32_t box[2] = {box_inner, box_rows};
+    cuuint32_t box[2] = {box_bytes / 8, box_rows};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void *>(base), dims, strides, box, estr,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<void *>(base), dims, strides, box,
+                          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS)
-        return fail(BNZ_EINVAL, "cuTensorMapEncodeTiled failed (%d): base=%p inner=%llu rows=%llu pitch=%llu",
-                    (int)r, base, (unsigned long long)inner_bytes, (unsigned long long)rows,
+        return fail(BNZ_EINVAL, "cuTensorMapEncodeTiled failed (%d): base=%p row=%llu rows=%llu pitch=%llu",
+                    (int)r, base, (unsigned long long)row_bytes, (unsigned long long)rows,
                     (unsigned long long)pitch);
     return BNZ_OK;
 }

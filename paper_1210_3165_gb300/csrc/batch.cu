@@ -30,12 +30,13 @@ struct alignas(128) PageDesc {
 
 template <int CIN>
 __device__ __forceinline__ void dispatch(int sel, const CUtensorMap *map, const FusedParams &p, const Segment &sg,
-                                         uint8_t *smem, uint64_t &phase, uint32_t &nfb, uint32_t &nties,
+                                         uint8_t *smem, uint64_t &phase, uint64_t &ephase, uint64_t &eused,
+                                         uint32_t &nfb, uint32_t &nties,
                                          volatile int *s_abort)
 {
 #define BNZ_CASE(R, M)                                                                                             \
     case (R) * 8 + (M):                                                                                            \
-        run_segment<CIN, R, M>(map, p, sg, smem, phase, nfb, nties, s_abort);                                      \
+        run_segment<CIN, R, M>(map, p, sg, smem, phase, ephase, eused, nfb, nties, s_abort);                      \
         break;
     switch (sel) {
         BNZ_CASE(0, 0) BNZ_CASE(0, 1) BNZ_CASE(0, 2) BNZ_CASE(0, 3)
@@ -57,11 +58,11 @@ __global__ void __launch_bounds__(NT, 1)
     __shared__ int s_abort;
     __shared__ FusedParams s_p;
     if (threadIdx.x == 0) {
-        init_barriers(smem, kMaxBarriers);
+        init_barriers(smem, kEmpty);
         s_abort = 0;
     }
     __syncthreads();
-    uint64_t phase = 0;
+    uint64_t phase = 0, ephase = 0, eused = 0;
     uint32_t nfb = 0, nties = 0;
     const long long L0 = total * blockIdx.x / gridDim.x, L1 = total * (blockIdx.x + 1) / gridDim.x;
     int pi = 0;
@@ -84,7 +85,7 @@ __global__ void __launch_bounds__(NT, 1)
         __syncthreads();
         const Segment sg = make_segment(s_p, cur - pd.t0, min(L1, page_end) - pd.t0);
         cur += sg.th_eff;
-        dispatch<CIN>(pd.sel, &pd.map, s_p, sg, smem, phase, nfb, nties, &s_abort);
+        dispatch<CIN>(pd.sel, &pd.map, s_p, sg, smem, phase, ephase, eused, nfb, nties, &s_abort);
         __syncthreads(); // the next segment reuses the ring and s_p
         if (s_abort)
             break;
@@ -211,8 +212,8 @@ static int plan_batch(const bnz_page *pages, int n, unsigned long long *d_stats,
         Group &g = b->groups[pg.channels == 1 ? 0 : 1];
         PageDesc d;
         memset(&d, 0, sizeof d);
-        rc = encode_u8_map(&d.map, pg.d_src, (uint64_t)pg.width * pg.channels, (uint64_t)pg.height,
-                           (uint64_t)pg.src_pitch, (uint32_t)(pl.PWP * pg.channels), (uint32_t)CH);
+        rc = encode_span_map(&d.map, pg.d_src, (uint64_t)pg.width * pg.channels, (uint64_t)pg.height,
+                             (uint64_t)pg.src_pitch, (uint32_t)(pl.SWP * pg.channels), (uint32_t)CH);
         if (rc != BNZ_OK) {
             free_batch(b);
             return rc;

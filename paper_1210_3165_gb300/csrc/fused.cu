@@ -53,14 +53,15 @@ __global__ void __launch_bounds__(NT, 1)
         s_abort = 0;
     }
     __syncthreads();
-    uint64_t phase = 0; // producers: bit i = parity to wait for next on barrier i
+    uint64_t phase = 0;             // bit i: parity of the next completion of full barrier i
+    uint64_t ephase = 0, eused = 0; // TMA issuer: free-signal parity, slots ever loaded
     uint32_t nfb = 0, nties = 0;
     const long long T = (long long)p.tiles_x * p.h;
     const long long L0 = T * blockIdx.x / gridDim.x, L1 = T * (blockIdx.x + 1) / gridDim.x;
     for (long long cur = L0; cur < L1;) {
         const Segment sg = make_segment(p, cur, L1);
         cur += sg.th_eff;
-        run_segment<CIN, RULE, WM8>(&tmap, p, sg, smem, phase, nfb, nties, &s_abort);
+        run_segment<CIN, RULE, WM8>(&tmap, p, sg, smem, phase, ephase, eused, nfb, nties, &s_abort);
         __syncthreads(); // the next segment reuses the ring from slot 0
         if (s_abort)
             break;
@@ -93,20 +94,19 @@ const void *kernel_for(int ch, int rule, int W)
 
 size_t round128(size_t v) { return (v + 127) & ~size_t(127); }
 
-// Shared-memory layout for one (strip width, chunk, staging) choice.
-bool layout(int ch, int W, int tw, int PWP, int CH, int NSS, FusedPlan *pl)
+// Shared-memory layout for one (strip width, staging) choice.  The span of a
+// strip (its outputs plus the window halo, 16-aligned on the left, plus the
+// 128-bit over-read of the consumers' streams) is one TMA box per chunk of
+// rows: at most 256 elements of 8 bytes.
+bool layout(int ch, int W, int tw, int NSS, FusedPlan *pl)
 {
     const int r_lo = W / 2;
-    const int PWB = PWP * ch;
     pl->TW = tw;
     pl->CH = CH;
     pl->o = (16 - (r_lo % 16)) % 16;
-    pl->PWP = PWP;
-    // window columns of every output plus the 128-bit over-read of the streams
     const int need = pl->o + tw + W + 4;
-    pl->NPAN = (need + PWP - 1) / PWP;
-    pl->SWP = pl->NPAN * PWP;
-    if (pl->SWP / 4 > NTP)
+    pl->SWP = (need + 15) / 16 * 16;
+    if (pl->SWP * ch > 256 * 8 || pl->SWP / 4 > NTPW)
         return false;
     pl->RSW = ((pl->SWP + 4) / 16 + 1) * 20;
     const int D = (CH + W - 1) / CH;
@@ -116,13 +116,13 @@ bool layout(int ch, int W, int tw, int PWP, int CH, int NSS, FusedPlan *pl)
     pl->NSS = ch == 3 ? NSS : 0;
     pl->ring_rows = pl->NS * CH;
     const int nbar = std::max(pl->NS, pl->NSS);
-    if (nbar > kMaxBarriers)
+    if (2 * nbar > kMaxBarriers)
         return false;
     size_t off = round128((size_t)kMaxBarriers * 8); // same barrier area for every page of a batch
     pl->off_ring = (uint32_t)off;
-    off = round128(off + (size_t)pl->NPAN * pl->ring_rows * PWP);
+    off = round128(off + (size_t)pl->ring_rows * pl->SWP);
     pl->off_stage = (uint32_t)off;
-    off = round128(off + (size_t)pl->NSS * pl->NPAN * CH * PWB);
+    off = round128(off + (size_t)pl->NSS * CH * pl->SWP * ch);
     pl->off_cb = (uint32_t)off;
     off += (size_t)4 * CH * pl->RSW * 4; // 2 buffers x {c1, c2}
     pl->smem = off;
@@ -189,15 +189,13 @@ int plan_shape(int h, int w, int ch, int W, int want_tw, FusedPlan *pl)
 {
     if (want_tw && want_tw != TW && want_tw != TW / 2 && want_tw != TW / 4)
         return fail(BNZ_EINVAL, "tile width must be 0, 128, 256 or 512 (got %d)", want_tw);
-    // widest strip first (least halo work), then narrower panels, then narrower strips
-    const int pw[2] = {ch == 1 ? 128 : 80, ch == 1 ? 64 : 80};
+    // widest strip first (least halo work), then fewer staging slots, then narrower strips
     bool found = false;
     for (int tw = TW; tw >= TW / 4 && !found; tw /= 2) {
         if (want_tw && tw != want_tw)
             continue;
-        for (int pi = 0; pi < 2 && !found; ++pi)
-            for (int nss = 3; nss >= 2 && !found; --nss)
-                found = layout(ch, W, tw, pw[pi], CH, nss, pl);
+        for (int nss = 3; nss >= 2 && !found; --nss)
+            found = layout(ch, W, tw, nss, pl);
     }
     if (!found)
         return fail(BNZ_EINVAL, "no tile shape fits shared memory for W=%d%s", W,
@@ -252,7 +250,6 @@ void fill_fused_params(FusedParams *p, const FusedPlan &pl, int h, int w, int W,
     p->CH = pl.CH;
     p->NS = pl.NS;
     p->NSS = pl.NSS;
-    p->NPAN = pl.NPAN;
     p->SWP = pl.SWP;
     p->RSW = pl.RSW;
     p->ring_rows = pl.ring_rows;
@@ -260,7 +257,6 @@ void fill_fused_params(FusedParams *p, const FusedPlan &pl, int h, int w, int W,
     p->off_ring = pl.off_ring;
     p->off_stage = pl.off_stage;
     p->off_cb = pl.off_cb;
-    p->PWP = pl.PWP;
     p->packed = packed ? 1 : 0;
     p->vec_ok = ((reinterpret_cast<uintptr_t>(d_dst) | dst_pitch) & 15u) == 0 ? 1 : 0;
     p->timeout_cycles = 4000000000ll; // ~2 s at 2 GHz
@@ -275,9 +271,8 @@ int launch_fused(const uint8_t *d_src, size_t src_pitch, int h, int w, int ch, i
     if (rc != BNZ_OK)
         return rc;
     CUtensorMap map;
-    const int PWB = pl.PWP * ch;
-    rc = encode_u8_map(&map, d_src, (uint64_t)w * ch, (uint64_t)h, (uint64_t)src_pitch, (uint32_t)PWB,
-                       (uint32_t)pl.CH);
+    rc = encode_span_map(&map, d_src, (uint64_t)w * ch, (uint64_t)h, (uint64_t)src_pitch,
+                         (uint32_t)(pl.SWP * ch), (uint32_t)pl.CH);
     if (rc != BNZ_OK)
         return rc;
     FusedParams p;

@@ -15,9 +15,11 @@ int fail(int rc, const char *fmt, ...);
 // Maps a CUDA runtime error to BNZ_ECUDA with a message naming `what`.
 int cuda_fail(cudaError_t e, const char *what);
 
-// Encodes a 2-D uint8 tensor map through the driver entry point.
-int encode_u8_map(CUtensorMap *map, const void *base, uint64_t inner_bytes, uint64_t rows, uint64_t pitch,
-                  uint32_t box_inner, uint32_t box_rows);
+// Encodes a 2-D tensor map over rows of `row_bytes` bytes, `pitch` apart, in
+// 8-byte elements (ceil(row_bytes/8) per row, so the last element of a row
+// may take up to 7 padding bytes), with boxes of box_bytes x box_rows.
+int encode_span_map(CUtensorMap *map, const void *base, uint64_t row_bytes, uint64_t rows, uint64_t pitch,
+                    uint32_t box_bytes, uint32_t box_rows);
 
 int device_sm_count(int *sms);
 
@@ -30,10 +32,9 @@ int check_common(const void *src, size_t src_pitch, int height, int width, int c
 // Shape of one launch of the fused kernel (host-side plan).
 struct FusedPlan {
     int TW, CH;     // strip width (32 lanes x 16 outputs), rows per TMA chunk
-    int NS;         // ring slots (chunks) of gray rows in shared memory (D + 3)
+    int NS;         // ring slots (chunks) of gray rows in shared memory
     int NSS;        // staging slots for RGB chunks (0 for gray)
-    int PWP;        // panel width in pixels (one TMA box per panel per chunk)
-    int NPAN, SWP;  // panels per span, span width in pixels
+    int SWP;        // span width in pixels: one TMA box of SWP*channels bytes per chunk
     int RSW;        // row stride (32-bit words) of each column-sum array
     int ring_rows;  // NS * CH
     int o;          // span start offset: (x0 - r_lo) - floor16(x0 - r_lo)
@@ -50,7 +51,7 @@ struct FusedParams {
     unsigned long long *stats;
     unsigned int *err_flag; // library-owned device word, counts CTAs that gave up
     int h, w, W, r_lo, r_hi, o;
-    int TW, CH, NS, NSS, PWP, NPAN, SWP, RSW, ring_rows, tiles_x;
+    int TW, CH, NS, NSS, SWP, RSW, ring_rows, tiles_x;
     uint32_t off_ring, off_stage, off_cb;
     int packed;     // 1: one bit per pixel
     int vec_ok;     // dst and dst_pitch 16-byte aligned
@@ -73,7 +74,7 @@ int plan_fused(int h, int w, int ch, int W, const bnz_tile *tile, FusedPlan *pla
 void fill_fused_params(FusedParams *p, const FusedPlan &pl, int h, int w, int W, int rule, double k, double R,
                        uint8_t *d_dst, size_t dst_pitch, int packed, unsigned long long *d_stats,
                        unsigned int *d_err);
-constexpr int kMaxBarriers = 64; // mbarriers reserved at the start of shared memory
+constexpr int kMaxBarriers = 96; // mbarriers reserved at the start of shared memory: full + empty per slot
 int launch_fused(const uint8_t *d_src, size_t src_pitch, int h, int w, int ch, int W, int rule, double k,
                  double R, uint8_t *d_dst, size_t dst_pitch, int packed, const bnz_tile *tile,
                  cudaStream_t stream, unsigned long long *d_stats, unsigned int *d_err);

@@ -11,20 +11,23 @@
 namespace bnz {
 
 constexpr int NTP = 256;            // producer threads (warps 0-7)
+constexpr int NTPW = NTP - 32;      // column-sum producers (warps 0-6); warp 7 issues the TMA loads
 constexpr int NTQ = 256;            // consumer threads (warps 8-15), one row each
 constexpr int NT = NTP + NTQ;
+constexpr int NTX = NTPW + NTQ;     // threads of the producer/consumer hand-over barriers
+constexpr int kEmpty = 48;          // mbarriers [0, 48): slot full; [48, 96): slot free again
 constexpr int L = 16;               // outputs per consumer lane per row
 constexpr int TW = 32 * L;          // widest strip; 256 is used when the ring would not fit
 constexpr int BAR_FULL = 1;         // named barriers 1,2: column-sum buffer b is ready
 constexpr int BAR_EMPTY = 3;        // named barriers 3,4: column-sum buffer b may be refilled
 constexpr int BAR_PROD = 5;         // producers only
-constexpr int kL2 = 6;              // chunks of L2 prefetch lead beyond the shared-memory loads
 constexpr int CH = 8;               // rows per chunk (TMA box height, one consumer warp per row)
 constexpr int kLeadGray = 3;        // gray: chunks loaded ahead of the ones in use
 constexpr int MAX_DYN_SMEM = 232448 - 1024; // 227 KB opt-in limit, minus slack
 
-// Panel widths in pixels (one TMA box per panel and chunk): gray 128 (or 64
-// when shared memory is tight), RGB 80 (240-byte boxes, whole r,g,b triples).
+// Shared memory holds rows row-major: the gray ring (ring_rows x SWP bytes)
+// and, for RGB, the staging slots (CH x 3*SWP bytes each), each chunk of rows
+// one TMA box of 8-byte elements.
 
 __device__ __forceinline__ void bar_sync(int id, int n)
 {
@@ -103,97 +106,124 @@ __device__ __forceinline__ Segment make_segment(const FusedParams &p, long long 
 // One segment with the 16 warps split into producers and consumers.
 template <int CIN, int RULE, int WM8>
 __device__ __forceinline__ void run_segment(const CUtensorMap *tmap, const FusedParams &p, const Segment &sg,
-                                            uint8_t *smem, uint64_t &phase, uint32_t &nfb, uint32_t &nties,
-                                            volatile int *s_abort);
+                                            uint8_t *smem, uint64_t &phase, uint64_t &ephase, uint64_t &eused,
+                                            uint32_t &nfb, uint32_t &nties, volatile int *s_abort);
 
 // ---------------------------------------------------------------------------
 // producers: TMA ring, RGB->gray, column sums (a1-a3)
 // ---------------------------------------------------------------------------
 template <int CIN>
 __device__ __forceinline__ void produce(const CUtensorMap *tmap, const FusedParams &p, const Segment &sg,
-                                        uint8_t *smem, uint64_t &phase, volatile int *s_abort)
+                                        uint8_t *smem, uint64_t &phase, uint64_t &ephase, uint64_t &eused,
+                                        volatile int *s_abort)
 {
-    const int PWP = p.PWP;
-    const int PWB = PWP * CIN;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
+    const int SWP = p.SWP;
+    const int SWB = SWP * CIN;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);
+    uint64_t *empty = full + kEmpty;
     uint8_t *ring = smem + p.off_ring;
     uint8_t *stage = smem + p.off_stage;
     uint32_t *cb = reinterpret_cast<uint32_t *>(smem + p.off_cb);
     const int tid = threadIdx.x; // 0..NTP-1
     const int W = p.W;
     const int D = (CH + W - 1) / CH;
-    const int nbar = CIN == 1 ? p.NS : p.NSS;
-    const uint32_t chunk_bytes = (uint32_t)(p.NPAN * CH * PWB);
-    const bool owner = tid < (p.SWP >> 2);
-    const int gcol = tid * 4;
-    const int gpn = gcol / PWP, gip = gcol - gpn * PWP;
-    const int gpos = cpos(gcol);
-    uint8_t *gbase = ring + (size_t)gpn * p.ring_rows * PWP + gip; // this thread's 4 columns, ring row 0
-    const uint8_t *sbase = stage + (size_t)gpn * CH * PWB + 3 * gip;  // the same columns in staging slot 0
-    const int ring_bytes = p.ring_rows * PWP;                     // one panel of the ring
+    const int nbar = CIN == 1 ? p.NS : p.NSS; // TMA targets: gray ring slots or RGB staging slots
+    const uint32_t chunk_bytes = (uint32_t)(CH * SWB);
 
-    int issued = 0, waited = 0;
-    bool good = !*s_abort;
-    // L2 prefetch of the chunk kL2 ahead of each shared-memory load, so the
-    // loads find their rows in L2 (the ring has room for only a few chunks)
-    auto prefetch = [&](int j) {
-        if (j < sg.nchk)
-            for (int pn = 0; pn < p.NPAN; ++pn)
-                tma_prefetch_l2_2d(tmap, (sg.xs + pn * PWP) * CIN, sg.ys + j * CH);
-    };
-    auto issue = [&](int j) { // thread 0 only
-        const int slot = j % nbar;
-        uint64_t *bar = &bars[slot];
-        mbar_arrive_expect_tx(bar, chunk_bytes);
-        for (int pn = 0; pn < p.NPAN; ++pn) {
-            uint8_t *dst = (CIN == 1) ? ring + (size_t)pn * p.ring_rows * PWP + (size_t)slot * CH * PWP
-                                      : stage + ((size_t)slot * p.NPAN + pn) * CH * PWB;
-            tma_load_2d(dst, tmap, (sg.xs + pn * PWP) * CIN, sg.ys + j * CH, bar);
+    // ---- warp 7: the TMA issuer (lane 0).  It runs ahead of the column-sum
+    // producers, limited only by free slots: a slot is refilled once the
+    // producers signal (empty barrier) that its previous chunk is consumed.
+    // Its own state, kept across segments: `phase` bit s = parity of the next
+    // completion of full[s], `ephase` bit s = parity of the next free signal
+    // of slot s, `eused` bit s = slot s was ever loaded.
+    if (tid >= NTPW) {
+        if (tid != NTPW)
+            return;
+        const int x = sg.xs * CIN / 8; // element coordinate, 16-byte aligned (xs is a multiple of 16)
+        int j = 0;
+        for (; j < sg.nchk && !*s_abort; ++j) {
+            const int slot = j % nbar;
+            if ((eused >> slot) & 1ull) {
+                if (!mbar_wait_bounded(&empty[slot], (uint32_t)((ephase >> slot) & 1ull), p.timeout_cycles)) {
+                    *s_abort = 1;
+                    break;
+                }
+                ephase ^= 1ull << slot;
+            }
+            eused |= 1ull << slot;
+            uint8_t *dst = (CIN == 1 ? ring : stage) + (size_t)slot * chunk_bytes;
+            mbar_arrive_expect_tx(&full[slot], chunk_bytes);
+            tma_load_2d(dst, tmap, x, sg.ys + j * CH, &full[slot]);
+            phase ^= 1ull << slot;
         }
-        prefetch(j + kL2);
-    };
+        // no copy may be in flight when the segment ends: wait (bounded) for
+        // the last load of each slot (earlier ones completed before its reuse)
+        for (int q = max(0, j - nbar); q < j; ++q) {
+            const int slot = q % nbar;
+            (void)mbar_wait_bounded(&full[slot], (uint32_t)(((phase >> slot) & 1ull) ^ 1ull), p.timeout_cycles);
+        }
+        return;
+    }
+
+    // ---- warps 0-6: RGB->gray (a2) and column sums (a3), 4 columns per thread
+    const bool owner = tid < (SWP >> 2);
+    const int gcol = tid * 4;
+    const int gpos = cpos(gcol);
+    uint8_t *gbase = ring + gcol;              // this thread's 4 columns, ring row 0
+    const uint8_t *sbase = stage + 3 * gcol;   // the same columns in staging slot 0
+    const int ring_bytes = p.ring_rows * SWP;
+    // columns at or right of the image edge must read as zero; the last 8-byte
+    // element of a row may carry up to 7 padding bytes past the edge
+    const int xg = sg.xs + gcol;
+    uint32_t keep = 0xffffffffu;
+    if (xg + 4 > p.w)
+        keep = xg >= p.w ? 0u : (0xffffffffu >> (8 * (4 - (p.w - xg))));
+    const bool fix = owner && keep != 0xffffffffu && xg < ((p.w * CIN + 7) / 8 * 8 + CIN - 1) / CIN;
+
+    int waited = 0, freed = 0;
+    bool good = !*s_abort;
     // every producer waits for itself; a wait that gives up flags the CTA
     // (the barrier protocol goes on, so no thread is left waiting)
     auto wait_one = [&]() {
         const int slot = waited % nbar;
-        if (!mbar_wait_bounded(&bars[slot], (uint32_t)((phase >> slot) & 1ull), p.timeout_cycles)) {
+        if (!mbar_wait_bounded(&full[slot], (uint32_t)((phase >> slot) & 1ull), p.timeout_cycles)) {
             good = false;
             *s_abort = 1;
         }
         phase ^= 1ull << slot;
+        if (CIN == 1 && fix && good) { // gray: clear the padding bytes in this thread's columns
+            uint8_t *r0 = gbase + (size_t)slot * CH * SWP;
+            for (int r = 0; r < CH; ++r)
+                *reinterpret_cast<uint32_t *>(r0 + r * SWP) &= keep;
+            fence_proxy_async_smem(); // these writes precede the slot's next TMA load
+        }
         ++waited;
+    };
+    // one producer frees the slots whose chunks no producer or consumer reads again
+    auto release_to = [&](int upto) {
+        for (; freed < upto; ++freed)
+            if (tid == 0)
+                mbar_arrive(&empty[freed % nbar]);
     };
     // RGB: this thread's 4 columns of chunk j, staging slot -> gray ring slot (Eq. 1)
     auto convert = [&](int j) {
         if (!owner)
             return;
-        const uint8_t *src = sbase + (size_t)(j % p.NSS) * p.NPAN * CH * PWB;
-        uint8_t *dst = gbase + (size_t)(j % p.NS) * CH * PWP;
+        const uint8_t *src = sbase + (size_t)(j % p.NSS) * CH * SWB;
+        uint8_t *dst = gbase + (size_t)(j % p.NS) * CH * SWP;
         uint32_t wv[CH][3];
 #pragma unroll
         for (int r = 0; r < CH; ++r) {
-            const uint32_t *s32 = reinterpret_cast<const uint32_t *>(src + r * PWB);
+            const uint32_t *s32 = reinterpret_cast<const uint32_t *>(src + r * SWB);
             wv[r][0] = s32[0];
             wv[r][1] = s32[1];
             wv[r][2] = s32[2];
         }
 #pragma unroll
         for (int r = 0; r < CH; ++r)
-            *reinterpret_cast<uint32_t *>(dst + r * PWP) = gray4(wv[r][0], wv[r][1], wv[r][2]);
+            *reinterpret_cast<uint32_t *>(dst + r * SWP) = gray4(wv[r][0], wv[r][1], wv[r][2]) & keep;
     };
 
-    // prologue: gray loads chunks 0..D+lead-1 straight into the ring; RGB fills its staging slots
-    const int lead = p.NS - D - 2; // gray: chunks in flight beyond the ones in use
-    if (good) {
-        const int pre = CIN == 1 ? min(sg.nchk, D + lead) : min(sg.nchk, p.NSS);
-        if (tid == 0) {
-            for (int j = pre; j < pre + kL2; ++j)
-                prefetch(j);
-            for (int j = 0; j < pre; ++j)
-                issue(j);
-        }
-        issued = pre;
-    }
     // warm-up: chunks 0..D-1 hold rows 0..W-1, the window of the segment's first output row
     for (int j = 0; j < D; ++j) {
         if (good)
@@ -201,12 +231,8 @@ __device__ __forceinline__ void produce(const CUtensorMap *tmap, const FusedPara
         if (CIN == 3) {
             if (good)
                 convert(j);
-            bar_sync(BAR_PROD, NTP); // staging slot j is free
-            if (good && issued < sg.nchk) {
-                if (tid == 0)
-                    issue(issued);
-                ++issued;
-            }
+            bar_sync(BAR_PROD, NTPW); // staging slot j is free
+            release_to(j + 1);
         }
     }
     uint32_t c1[4] = {0u, 0u, 0u, 0u}, c2[4] = {0u, 0u, 0u, 0u};
@@ -222,34 +248,27 @@ __device__ __forceinline__ void produce(const CUtensorMap *tmap, const FusedPara
             c2[1] += byte_at<1>(v) * byte_at<1>(v);
             c2[2] += byte_at<2>(v) * byte_at<2>(v);
             c2[3] += byte_at<3>(v) * byte_at<3>(v);
-            off += PWP;
+            off += SWP;
             if (off == ring_bytes)
                 off = 0;
         }
     }
-    int off_in = (W % p.ring_rows) * PWP; // ring offset of row i + W (entering for output row i + 1)
+    int off_in = (W % p.ring_rows) * SWP; // ring offset of row i + W (entering for output row i + 1)
     int off_out = 0;                      // ring offset of row i (leaving), chunk-aligned
 
     for (int k = 0; k < sg.nk; ++k) {
         const int b = k & 1;
-        if (k >= 2)
-            bar_sync(BAR_EMPTY + b, NT); // consumers are done with chunk k-2
+        if (k >= 2) {
+            bar_sync(BAR_EMPTY + b, NTX); // consumers are done with chunk k-2
+            if (CIN == 1)
+                release_to(k - 1);        // gray: chunk k-2 was last read as leaving / centre rows
+        }
         const int need = min(k + D, sg.nchk - 1);
-        if (CIN == 1) {
-            if (good && issued < sg.nchk) { // keep `lead` chunks in flight
-                if (tid == 0)
-                    issue(issued);
-                ++issued;
-            }
-            while (good && waited <= need)
-                wait_one();
-        } else {
-            while (good && waited <= need) {
-                const int j = waited;
-                wait_one();
-                if (good)
-                    convert(j); // own columns only: no barrier before the column sums
-            }
+        while (good && waited <= need) {
+            const int j = waited;
+            wait_one();
+            if (CIN == 3 && good)
+                convert(j); // own columns only: no barrier before the column sums
         }
         const int rows_k = min(CH, sg.th_eff - k * CH);
         if (good && owner) {
@@ -259,11 +278,11 @@ __device__ __forceinline__ void produce(const CUtensorMap *tmap, const FusedPara
             uint32_t vi[CH], vo[CH];
 #pragma unroll
             for (int r = 0; r < CH; ++r) { // load first, then add: no smem latency per row
-                int oi = off_in + r * PWP;
+                int oi = off_in + r * SWP;
                 if (oi >= ring_bytes)
                     oi -= ring_bytes;
                 vi[r] = *reinterpret_cast<const uint32_t *>(gbase + oi);
-                vo[r] = *reinterpret_cast<const uint32_t *>(gbase + off_out + r * PWP);
+                vo[r] = *reinterpret_cast<const uint32_t *>(gbase + off_out + r * SWP);
             }
 #pragma unroll
             for (int r = 0; r < CH; ++r) {
@@ -284,29 +303,22 @@ __device__ __forceinline__ void produce(const CUtensorMap *tmap, const FusedPara
                 }
             }
         }
-        off_in += CH * PWP;
+        off_in += CH * SWP;
         if (off_in >= ring_bytes)
             off_in -= ring_bytes;
-        off_out += CH * PWP;
+        off_out += CH * SWP;
         if (off_out >= ring_bytes)
             off_out -= ring_bytes;
-        bar_arrive(BAR_FULL + b, NT); // always, so consumers never wait forever
+        bar_arrive(BAR_FULL + b, NTX); // always, so consumers never wait forever
         if (CIN == 3) {
-            bar_sync(BAR_PROD, NTP); // every producer is past the conversions of this step
-            while (good && issued < min(sg.nchk, waited + p.NSS)) {
-                if (tid == 0)
-                    issue(issued);
-                ++issued;
-            }
+            bar_sync(BAR_PROD, NTPW); // every producer is past the conversions of this step
+            release_to(waited);       // their staging slots may be refilled
         }
     }
-    // drain this segment's copies (bounded) before the ring is reused
-    while (waited < issued) {
-        const int slot = waited % nbar;
-        mbar_wait_bounded(&bars[slot], (uint32_t)((phase >> slot) & 1ull), p.timeout_cycles);
-        phase ^= 1ull << slot;
-        ++waited;
-    }
+    // every chunk of the segment is consumed: free the remaining slots so the
+    // issuer's count of free signals per slot matches its count of loads
+    if (good)
+        release_to(sg.nchk);
 }
 
 // ---------------------------------------------------------------------------
@@ -316,7 +328,7 @@ template <int CIN, int RULE, int WM8>
 __device__ __forceinline__ void consume(const FusedParams &p, const Segment &sg, uint8_t *smem, uint32_t &nfb,
                                         uint32_t &nties, volatile int *s_abort)
 {
-    const int PWP = p.PWP;
+    const int SWP = p.SWP;
     // o = (-r_lo) mod 16 and r_lo = W/2: the misalignments of the leaving
     // (span column o + x) and entering (o + W + x) streams depend on W mod 8
     constexpr int KO = (4 - ((WM8 >> 1) & 3)) & 3;
@@ -329,15 +341,14 @@ __device__ __forceinline__ void consume(const FusedParams &p, const Segment &sg,
     const bool active = lane * L < p.TW; // 256-wide strips leave lanes 16..31 idle
     // centre pixels of this lane's 16 outputs start at span column lane*16 + o + r_lo (a multiple of 16)
     const int fcol = active ? lane * L + p.o + p.r_lo : 0;
-    const int fpn = fcol / PWP;
-    const uint8_t *fbase = ring + (size_t)fpn * p.ring_rows * PWP + (fcol - fpn * PWP);
+    const uint8_t *fbase = ring + fcol;
     const int xg0 = sg.x0 + lane * L;
     const bool xclip = xg0 < p.r_lo || xg0 + L - 1 + p.r_hi > p.w - 1; // some window of the lane leaves the image
 
     int rc = (ii + p.r_lo) % p.ring_rows; // ring row of this warp's centre row in chunk k
     for (int k = 0; k < sg.nk; ++k, rc = (rc + CH < p.ring_rows) ? rc + CH : rc + CH - p.ring_rows) {
         const int b = k & 1;
-        bar_sync(BAR_FULL + b, NT);
+        bar_sync(BAR_FULL + b, NTX);
         const int rows_k = min(CH, sg.th_eff - k * CH);
         if (ii < rows_k && !*s_abort) {
             const int i = k * CH + ii;
@@ -405,7 +416,7 @@ __device__ __forceinline__ void consume(const FusedParams &p, const Segment &sg,
             }
             const uint32_t base1 = s1 + x1 - a1, base2 = s2 + x2 - a2;
 
-            const uint4 fv = *reinterpret_cast<const uint4 *>(fbase + (size_t)rc * PWP);
+            const uint4 fv = *reinterpret_cast<const uint4 *>(fbase + (size_t)rc * SWP);
             const uint32_t fw[4] = {fv.x, fv.y, fv.z, fv.w};
             const bool yclip = (y < p.r_lo) || (y + p.r_hi > p.h - 1);
             const bool lane_clip = active && xg0 < p.w && (yclip || xclip);
@@ -513,28 +524,30 @@ __device__ __forceinline__ void consume(const FusedParams &p, const Segment &sg,
             }
         }
         if (k + 2 < sg.nk)
-            bar_arrive(BAR_EMPTY + b, NT);
+            bar_arrive(BAR_EMPTY + b, NTX);
     }
 }
 
 
 template <int CIN, int RULE, int WM8>
 __device__ __forceinline__ void run_segment(const CUtensorMap *tmap, const FusedParams &p, const Segment &sg,
-                                            uint8_t *smem, uint64_t &phase, uint32_t &nfb, uint32_t &nties,
-                                            volatile int *s_abort)
+                                            uint8_t *smem, uint64_t &phase, uint64_t &ephase, uint64_t &eused,
+                                            uint32_t &nfb, uint32_t &nties, volatile int *s_abort)
 {
     if (threadIdx.x < NTP)
-        produce<CIN>(tmap, p, sg, smem, phase, s_abort);
+        produce<CIN>(tmap, p, sg, smem, phase, ephase, eused, s_abort);
     else
         consume<CIN, RULE, WM8>(p, sg, smem, nfb, nties, s_abort);
 }
 
-// Kernel prologue: barriers for up to `nbar` ring/staging slots.
+// Kernel prologue: full and empty barriers for up to `nbar` ring/staging slots.
 __device__ __forceinline__ void init_barriers(uint8_t *smem, int nbar)
 {
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
-    for (int i = 0; i < nbar; ++i)
+    for (int i = 0; i < nbar; ++i) {
         mbar_init(&bars[i], 1);
+        mbar_init(&bars[kEmpty + i], 1);
+    }
     fence_mbar_init();
     fence_proxy_async_smem();
 }
