@@ -108,7 +108,7 @@ bool layout(int ch, int W, int tw, int NSS, FusedPlan *pl)
     pl->SWP = (need + 15) / 16 * 16;
     if (pl->SWP * ch > 256 * 8 || pl->SWP / 4 > NTPW)
         return false;
-    pl->RSW = ((pl->SWP + 4) / 16 + 1) * 20;
+    pl->RSW = (pl->SWP + 4 + 31) / 32 * 32; // words per column-sum row (swizzled, unpadded)
     const int D = (CH + W - 1) / CH;
     // ring: chunks in use (D + 1), one more because producers run a chunk ahead
     // of the consumers' centre rows, and for gray the chunks loaded ahead

@@ -35,7 +35,7 @@ struct FusedPlan {
     int NS;         // ring slots (chunks) of gray rows in shared memory
     int NSS;        // staging slots for RGB chunks (0 for gray)
     int SWP;        // span width in pixels: one TMA box of SWP*channels bytes per chunk
-    int RSW;        // row stride (32-bit words) of each column-sum array
+    int RSW;        // row stride (32-bit words) of each column-sum array, a multiple of 32
     int ring_rows;  // NS * CH
     int o;          // span start offset: (x0 - r_lo) - floor16(x0 - r_lo)
     int tiles_x;    // strips across the image

@@ -51,16 +51,25 @@ __device__ __forceinline__ uint32_t byte_dyn(uint32_t w, int j)
     return (w >> (8 * j)) & 0xffu;
 }
 
-// Position of span column c in a column-sum row: 4 words of padding after
-// every 16 columns keep the lanes' 128-bit loads free of bank conflicts.
+// Word offset of 4-column group g in a column-sum row.  The groups are
+// XOR-swizzled within aligned blocks of four, g ^ ((g >> 3) & 3), so that
+// both access patterns hit eight distinct 16-byte bank groups per phase: the
+// producers' 128-bit stores (consecutive groups, one per thread) and the
+// consumers' 128-bit loads (groups four apart, one per lane, any offset).
+__device__ __forceinline__ int gpos(int g)
+{
+    return 4 * (g ^ ((g >> 3) & 3));
+}
+
+// Word offset of span column c.
 __device__ __forceinline__ int cpos(int c)
 {
-    return c + ((c >> 4) << 2);
+    return gpos(c >> 2) + (c & 3);
 }
 
 __device__ __forceinline__ uint4 ld_group(const uint32_t *C, int a) // columns 4a..4a+3
 {
-    return *reinterpret_cast<const uint4 *>(C + 4 * a + ((a >> 2) << 2));
+    return *reinterpret_cast<const uint4 *>(C + gpos(a));
 }
 
 // Eq. 1 for one pixel whose r, g, b are bytes 0..2 of px (byte 3 ignored):
@@ -168,7 +177,7 @@ __device__ __forceinline__ void produce(const CUtensorMap *tmap, const FusedPara
     // ---- warps 0-6: RGB->gray (a2) and column sums (a3), 4 columns per thread
     const bool owner = tid < (SWP >> 2);
     const int gcol = tid * 4;
-    const int gpos = cpos(gcol);
+    const int gofs = cpos(gcol);
     uint8_t *gbase = ring + gcol;              // this thread's 4 columns, ring row 0
     const uint8_t *sbase = stage + 3 * gcol;   // the same columns in staging slot 0
     const int ring_bytes = p.ring_rows * SWP;
@@ -273,7 +282,7 @@ __device__ __forceinline__ void produce(const CUtensorMap *tmap, const FusedPara
         const int rows_k = min(CH, sg.th_eff - k * CH);
         if (good && owner) {
             const bool last = (k + 1 == sg.nk);
-            uint32_t *C1 = cb + (size_t)(2 * b) * CH * p.RSW + gpos;
+            uint32_t *C1 = cb + (size_t)(2 * b) * CH * p.RSW + gofs;
             uint32_t *C2 = C1 + (size_t)CH * p.RSW;
             uint32_t vi[CH], vo[CH];
 #pragma unroll
@@ -421,11 +430,9 @@ __device__ __forceinline__ void consume(const FusedParams &p, const Segment &sg,
             const bool yclip = (y < p.r_lo) || (y + p.r_hi > p.h - 1);
             const bool lane_clip = active && xg0 < p.w && (yclip || xclip);
             uint32_t outw[4];
-            bool amb = false;
+            float mn = INFINITY; // smallest |d| of the lane's pixels inside the image
             if (!__any_sync(0xffffffffu, lane_clip)) {
                 // every window of the warp is W x W: shared constants
-                // n*S2 = n*base2 + n*d2 (mod 2^64, d2 taken as a signed offset)
-                const unsigned long long nb2 = (unsigned long long)p.nW * base2;
 #pragma unroll
                 for (int qq = 0; qq < 4; ++qq) {
                     float dd[4];
@@ -433,11 +440,12 @@ __device__ __forceinline__ void consume(const FusedParams &p, const Segment &sg,
                     for (int e = 0; e < 4; ++e) {
                         const int t = 4 * qq + e;
                         const uint32_t S1 = base1 + d1[t];
-                        const unsigned long long V = nb2 + (unsigned long long)((long long)p.nW * (int)d2[t]) -
-                                                     (unsigned long long)S1 * S1;
+                        const uint32_t S2 = base2 + d2[t]; // exact: S2 < 2^32
+                        const unsigned long long V =
+                            (unsigned long long)p.nW * S2 - (unsigned long long)S1 * S1;
                         const float ff = __uint2float_rn(byte_dyn(fw[qq], e));
                         dd[e] = filter_int<RULE>(ff, __uint2float_rn(S1), sqrt_approx(v_to_float(V)), p);
-                        amb = amb || (fabsf(dd[e]) < p.E);
+                        mn = fminf(mn, fabsf(dd[e]));
                     }
                     // byte = 0xFF where d >= +0, 0x00 where d < 0 (sign bit replicated)
                     const uint32_t lo = prmt(__float_as_uint(dd[0]), __float_as_uint(dd[1]), 0xFBu);
@@ -461,14 +469,14 @@ __device__ __forceinline__ void consume(const FusedParams &p, const Segment &sg,
                         const float ff = __uint2float_rn(byte_dyn(fw[qq], e));
                         const float invn = rcp_approx(__uint2float_rn(n));
                         dd[e] = filter_n<RULE>(ff, __uint2float_rn(S1), sqrt_approx(v_to_float(V)), invn, p);
-                        amb = amb || (xg < p.w && fabsf(dd[e]) < p.E);
+                        mn = fminf(mn, xg < p.w ? fabsf(dd[e]) : INFINITY);
                     }
                     const uint32_t lo = prmt(__float_as_uint(dd[0]), __float_as_uint(dd[1]), 0xFBu);
                     const uint32_t hi = prmt(__float_as_uint(dd[2]), __float_as_uint(dd[3]), 0xFBu);
                     outw[qq] = ~prmt(lo, hi, 0x5410u);
                 }
             }
-            if (amb && active) { // rare: a value inside the fp32 margin -> fp64 for those pixels
+            if (mn < p.E && active) { // rare: a value inside the fp32 margin -> fp64 for those pixels
                 const int nr = min(y + p.r_hi, p.h - 1) - max(y - p.r_lo, 0) + 1;
                 for (int t = 0; t < L; ++t) {
                     const int xg = xg0 + t;
