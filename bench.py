@@ -194,11 +194,16 @@ def run_ours(args):
     stream = torch.cuda.Stream(device=dev)
     rule_id = {"sauvola": bnz.BNZ_SAUVOLA, "niblack": bnz.BNZ_NIBLACK}
 
+    rot = [0]
+
     def step(evs=None):
+        # every launch reads the next of the NCOPY input copies, so none finds its input in L2
         for j, (W, rule, k, R) in enumerate(RUNS):
             if evs is not None:
                 evs[j].record(stream)
-            bnz.bnz_binarize_dev(srcs[j], W, rule_id[rule], k, R, outs[j], stream=stream)
+            c = rot[0] % NCOPY
+            rot[0] += 1
+            bnz.bnz_binarize_dev(srcs[c], W, rule_id[rule], k, R, outs[c], stream=stream)
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -479,6 +484,9 @@ def main():
     ap.add_argument("--workload", default="page", choices=["page", "batch", "serve"],
                     help="page: the 4096x4096 RGB page (default); batch: 256 uneven gray pages; "
                          "serve: Poisson stream of RGB pages through the serving loop")
+    ap.add_argument("--case", default=None,
+                    help="page workload restricted to one configuration CH,W,RULE (e.g. 3,15,sauvola): "
+                         "one launch per step, for profiler captures")
     ap.add_argument("--serve-requests", type=int, default=10000)
     ap.add_argument("--serve-capacity", type=int, default=2000, help="requests of the closed-loop capacity run")
     ap.add_argument("--serve-loads", default="0.5,0.8,0.95", help="offered loads, fractions of batched capacity")
@@ -491,6 +499,15 @@ def main():
         return run_batch(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.case:
+        global CH, RUNS, NCOPY, BYTES_PER_PX, WORKLOAD
+        ch, W, rule = args.case.split(",")
+        CH = int(ch)
+        k = 0.5 if rule == "sauvola" else -0.2
+        RUNS = [(int(W), rule, k, 128.0)]
+        NCOPY = 8
+        BYTES_PER_PX = CH + 1
+        WORKLOAD = f"page 4096x4096 {'RGB' if CH == 3 else 'gray'}, {rule} k={k} W={W}, byte mask (one case)"
     return run_ours(args)
 
 

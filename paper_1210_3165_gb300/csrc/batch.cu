@@ -221,15 +221,24 @@ static int plan_batch(const bnz_page *pages, int n, unsigned long long *d_stats,
         const double R = pg.rule == BNZ_NIBLACK ? 1.0 : pg.R;
         fill_fused_params(&d.p, pl, pg.height, pg.width, pg.W, pg.rule, pg.k, R, pg.d_dst, pg.dst_pitch, pg.packed,
                           d_stats, err);
-        d.t0 = g.total;
+        d.t0 = (long long)pl.tiles_x * pg.height; // strip rows of this page; turned into offsets below
         d.sel = pg.rule * 8 + (pg.W & 7);
-        g.total += (long long)pl.tiles_x * pg.height;
         g.smem = std::max(g.smem, pl.smem);
         g.host.push_back(d);
     }
     for (Group &g : b->groups) {
         if (g.host.empty())
             continue;
+        // pages of the same kernel instance (rule, W mod 8) next to each other: the
+        // persistent CTAs walk contiguous ranges, so most of them then run the same
+        // code at any time instead of thrashing the instruction caches
+        std::stable_sort(g.host.begin(), g.host.end(),
+                         [](const PageDesc &a, const PageDesc &c) { return a.sel < c.sel; });
+        for (PageDesc &d : g.host) {
+            const long long rows = d.t0;
+            d.t0 = g.total;
+            g.total += rows;
+        }
         const void *fn = g.ch == 1 ? reinterpret_cast<const void *>(&batch_kernel<1>)
                                    : reinterpret_cast<const void *>(&batch_kernel<3>);
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);

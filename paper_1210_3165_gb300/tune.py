@@ -2,7 +2,10 @@
 
 For each (channels, W) it times the fused kernel with every strip width that
 fits shared memory (512, 256, 128 output columns) on a synthetic page and
-keeps the fastest.  Results are cached as JSON keyed by GPU name, so tuning is
+keeps the fastest.  The page is tall (4096 rows by default) so that, as in a
+batch or a stream of pages, the W rows of warm-up at the top of each strip
+segment are amortized; on short pages narrower strips win only because they
+give each CTA more rows per segment.  Results are cached as JSON keyed by GPU name, so tuning is
 done once per machine; batches take their per-page ``tile_w`` from the table.
 """
 from __future__ import annotations
@@ -41,7 +44,7 @@ def _time_one(src, out, W, tile, reps):
     return times[len(times) // 2]
 
 
-def tune(windows=DEFAULT_WINDOWS, channels=(1, 3), shape=(2048, 2048), reps: int = 7, seed: int = 4,
+def tune(windows=DEFAULT_WINDOWS, channels=(1, 3), shape=(4096, 4096), reps: int = 7, seed: int = 4,
          save: bool = True) -> dict:
     """Return {"1": {"15": 512, ...}, "3": {...}} and cache it unless save=False."""
     import torch
