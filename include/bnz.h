@@ -274,6 +274,15 @@ BNZ_API int bnz_selftest_sqrt_approx(float lo, float hi, double *max_rel_err);
  * n_lo <= n < n_hi (the clipped window counts; assumed <= 2^-22). */
 BNZ_API int bnz_selftest_rcp_approx(unsigned int n_lo, unsigned int n_hi, double *max_rel_err);
 
+/* Device self-test of the bounded wait every kernel uses on its mbarriers:
+ * one thread waits for a barrier phase with a limit of `limit_cycles` SM
+ * cycles; with arrive = 0 nothing ever completes the phase, so the wait must
+ * give up (*timed_out = 1) after about the limit and return, leaving the
+ * context usable; with arrive = 1 the phase is complete and *timed_out = 0.
+ * *waited_cycles (nullable) receives the cycles spent.  Synchronous. */
+BNZ_API int bnz_selftest_wait_timeout(long long limit_cycles, int arrive, int *timed_out,
+                                      long long *waited_cycles);
+
 #ifdef __cplusplus
 }
 #endif

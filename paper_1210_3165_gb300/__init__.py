@@ -98,6 +98,8 @@ def _optional_symbols(lib):
                                      ctypes.c_int),
         "bnz_selftest_rcp_approx": ([ctypes.c_uint, ctypes.c_uint, ctypes.POINTER(ctypes.c_double)],
                                     ctypes.c_int),
+        "bnz_selftest_wait_timeout": ([ctypes.c_longlong, i, ctypes.POINTER(i), ctypes.POINTER(ctypes.c_longlong)],
+                                      ctypes.c_int),
         "bnz_integral_scratch_bytes": ([i, i], ctypes.c_size_t),
         "bnz_binarize_integral_dev": ([P, sz, i, i, i, i, i, d, d, P, sz, i, P, sz, P, P], ctypes.c_int),
         "bnz_binarize_integral_static_dev": ([P, sz, i, i, i, i, i, d, d, P, sz, i, P, P], ctypes.c_int),

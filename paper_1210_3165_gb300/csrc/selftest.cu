@@ -4,6 +4,7 @@
 #include <cstring>
 
 #include "internal.h"
+#include "ptx.cuh"
 
 namespace bnz {
 namespace {
@@ -42,8 +43,53 @@ __global__ void rcp_approx_err_kernel(uint32_t n_lo, uint32_t n_hi, unsigned int
         atomicMax(max_err_bits, __float_as_uint(worst));
 }
 
+// One thread waits, with the kernels' bounded wait, for the first phase of an
+// mbarrier that expects one arrival; when `arrive` is 0 nothing ever arrives.
+// out[0] = 1 if the wait gave up, out[1] = cycles spent waiting.
+__global__ void wait_timeout_kernel(long long limit, int arrive, long long *out)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+        if (arrive)
+            mbar_arrive(&bar);
+        const long long t0 = clock64();
+        const bool ok = mbar_wait_bounded(&bar, 0u, limit);
+        out[1] = clock64() - t0;
+        out[0] = ok ? 0 : 1;
+    }
+}
+
 } // namespace
 } // namespace bnz
+
+extern "C" BNZ_API int bnz_selftest_wait_timeout(long long limit_cycles, int arrive, int *timed_out,
+                                                 long long *waited_cycles)
+{
+    using namespace bnz;
+    if (!timed_out || limit_cycles < 0 || limit_cycles > 4000000000ll)
+        return fail(BNZ_EINVAL, "need 0 <= limit_cycles <= 4e9 and a result pointer");
+    long long *d = nullptr;
+    cudaError_t e = cudaMalloc(&d, 2 * sizeof(long long));
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaMalloc(selftest)");
+    long long h[2] = {-1, -1};
+    do {
+        wait_timeout_kernel<<<1, 32>>>(limit_cycles, arrive ? 1 : 0, d);
+        if ((e = cudaGetLastError()) != cudaSuccess)
+            break;
+        if ((e = cudaMemcpy(h, d, sizeof h, cudaMemcpyDeviceToHost)) != cudaSuccess)
+            break;
+    } while (0);
+    cudaFree(d);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "wait self-test");
+    *timed_out = (int)h[0];
+    if (waited_cycles)
+        *waited_cycles = h[1];
+    return BNZ_OK;
+}
 
 extern "C" BNZ_API int bnz_selftest_rcp_approx(unsigned int n_lo, unsigned int n_hi, double *max_rel_err)
 {

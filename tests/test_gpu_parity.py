@@ -173,3 +173,21 @@ def test_rcp_approx_error_within_margin_assumption(bnz):
     rc = bnz.load().bnz_selftest_rcp_approx(1, 65026, ctypes.byref(err))
     assert rc == 0, bnz.bnz_last_error()
     assert 0.0 < err.value <= 2.0 ** -22, err.value
+
+
+def test_bounded_wait_gives_up_and_context_stays_usable(bnz):
+    """A wait on a barrier phase that nothing completes gives up after its limit and reports it; the
+    context then still runs the fused kernel correctly.  (The failure is made by never arriving: no
+    trap, no bad address, no endless loop.)"""
+    import ctypes
+    lib = bnz.load()
+    limit = 2_000_000  # SM cycles, about 1 ms
+    to, cyc = ctypes.c_int(-1), ctypes.c_longlong(-1)
+    rc = lib.bnz_selftest_wait_timeout(limit, 0, ctypes.byref(to), ctypes.byref(cyc))
+    assert rc == 0, bnz.bnz_last_error()
+    assert to.value == 1
+    assert limit < cyc.value < limit + 1_000_000  # gives up soon after the limit (suspends <= 20 us per try)
+    rc = lib.bnz_selftest_wait_timeout(limit, 1, ctypes.byref(to), ctypes.byref(cyc))
+    assert rc == 0 and to.value == 0 and 0 <= cyc.value < limit
+    img = synth.page(300, 257, 21, synth.DOC, 1)
+    check(bnz, img, 15, "sauvola", 0.5)
