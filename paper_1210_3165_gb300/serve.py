@@ -69,6 +69,28 @@ def on_device(img) -> bool:
     return bool(getattr(img, "is_cuda", False))
 
 
+MAX_W = 255
+
+
+def validate(req: Request) -> str | None:
+    """Why a request cannot be served, or None."""
+    shape = tuple(getattr(req.image, "shape", ()))
+    if len(shape) not in (2, 3) or (len(shape) == 3 and shape[2] != 3):
+        return f"image must be HxW (gray) or HxWx3 (RGB), got shape {shape}"
+    if shape[0] < 1 or shape[1] < 1:
+        return f"empty image {shape}"
+    dt = getattr(req.image, "dtype", None)
+    if str(dt) not in ("uint8", "torch.uint8"):
+        return f"image must be uint8, got {dt}"
+    if not (isinstance(req.W, int) and 1 <= req.W <= MAX_W):
+        return f"W must be an integer in [1, {MAX_W}], got {req.W!r}"
+    if req.rule not in ("sauvola", "niblack"):
+        return f"rule must be 'sauvola' or 'niblack', got {req.rule!r}"
+    if req.rule == "sauvola" and not (req.R > 0):
+        return f"R must be > 0 for Sauvola, got {req.R!r}"
+    return None
+
+
 class Server:
     def __init__(self, executor, budget_bytes: int | None = None, max_batch: int = 64, poll_s: float = 50e-6):
         self.ex = executor
@@ -97,6 +119,11 @@ class Server:
 
     # ---- client side --------------------------------------------------------
     def submit(self, req: Request) -> Future:
+        """Queue a request; malformed or over-budget requests fail their future at once (never the loop)."""
+        problem = validate(req)
+        if problem:
+            req.future.set_exception(ValueError(problem))
+            return req.future
         h, w = req.shape[:2]
         ch = 1 if len(req.shape) == 2 else 3
         req.nbytes = request_bytes(h, w, ch, req.packed, with_input=not on_device(req.image))

@@ -221,3 +221,21 @@ def test_cancelled_and_timed_out_requests_do_not_run():
     with pytest.raises(TimeoutError):
         fc.result(timeout=0)
     assert ex.order == [0] and srv.cancelled == 1 and srv.timed_out == 1 and srv.pending() == 0
+
+
+@pytest.mark.parametrize("bad", [
+    dict(image=np.zeros((0, 5), np.uint8)), dict(image=np.zeros((4, 0, 3), np.uint8)),
+    dict(image=np.zeros((4, 5, 2), np.uint8)), dict(image=np.zeros((4, 5), np.float32)),
+    dict(W=0), dict(W=256), dict(W=15.0), dict(rule="otsu"), dict(R=0.0)])
+def test_malformed_requests_fail_their_future_not_the_loop(bad):
+    ex = FakeExecutor()
+    srv = Server(ex, budget_bytes=1 << 20)
+    kw = dict(image=np.zeros((4, 5), np.uint8), W=3)
+    kw.update(bad)
+    f = srv.submit(Request(**kw))
+    with pytest.raises(ValueError):
+        f.result(timeout=0)
+    good = req(1, 4, 5)
+    g = srv.submit(good)
+    drive(srv)
+    assert g.result() is not None and ex.order == [1]
