@@ -149,9 +149,8 @@ __device__ __forceinline__ void produce(const CUtensorMap *tmap, const FusedPara
         if (tid != NTPW)
             return;
         const int x = sg.xs * CIN / 8; // element coordinate, 16-byte aligned (xs is a multiple of 16)
-        int j = 0;
-        for (; j < sg.nchk && !*s_abort; ++j) {
-            const int slot = j % nbar;
+        int j = 0, slot = 0; // slot = j mod nbar, kept by increment (no division)
+        for (; j < sg.nchk && !*s_abort; ++j, slot = (slot + 1 == nbar) ? 0 : slot + 1) {
             if ((eused >> slot) & 1ull) {
                 if (!mbar_wait_bounded(&empty[slot], (uint32_t)((ephase >> slot) & 1ull), p.timeout_cycles)) {
                     *s_abort = 1;
@@ -167,10 +166,9 @@ __device__ __forceinline__ void produce(const CUtensorMap *tmap, const FusedPara
         }
         // no copy may be in flight when the segment ends: wait (bounded) for
         // the last load of each slot (earlier ones completed before its reuse)
-        for (int q = max(0, j - nbar); q < j; ++q) {
-            const int slot = q % nbar;
-            (void)mbar_wait_bounded(&full[slot], (uint32_t)(((phase >> slot) & 1ull) ^ 1ull), p.timeout_cycles);
-        }
+        const int q0 = max(0, j - nbar);
+        for (int q = q0, qs = q0 % nbar; q < j; ++q, qs = (qs + 1 == nbar) ? 0 : qs + 1)
+            (void)mbar_wait_bounded(&full[qs], (uint32_t)(((phase >> qs) & 1ull) ^ 1ull), p.timeout_cycles);
         return;
     }
 
@@ -189,12 +187,18 @@ __device__ __forceinline__ void produce(const CUtensorMap *tmap, const FusedPara
         keep = xg >= p.w ? 0u : (0xffffffffu >> (8 * (4 - (p.w - xg))));
     const bool fix = owner && keep != 0xffffffffu && xg < ((p.w * CIN + 7) / 8 * 8 + CIN - 1) / CIN;
 
+    // chunk counters and their slots, kept by increment (a run-time modulo costs
+    // about twenty instructions and every producer thread would pay it per chunk)
     int waited = 0, freed = 0;
+    int wslot = 0, fslot = 0, last = 0; // slots (mod nbar) of chunk `waited`, of chunk `freed`, of the last wait
+    int gslot = 0;                      // RGB: gray ring slot (mod NS) of the next chunk converted
     bool good = !*s_abort;
     // every producer waits for itself; a wait that gives up flags the CTA
     // (the barrier protocol goes on, so no thread is left waiting)
     auto wait_one = [&]() {
-        const int slot = waited % nbar;
+        const int slot = wslot;
+        last = slot;
+        wslot = (wslot + 1 == nbar) ? 0 : wslot + 1;
         if (!mbar_wait_bounded(&full[slot], (uint32_t)((phase >> slot) & 1ull), p.timeout_cycles)) {
             good = false;
             *s_abort = 1;
@@ -210,16 +214,21 @@ __device__ __forceinline__ void produce(const CUtensorMap *tmap, const FusedPara
     };
     // one producer frees the slots whose chunks no producer or consumer reads again
     auto release_to = [&](int upto) {
-        for (; freed < upto; ++freed)
+        for (; freed < upto; ++freed) {
             if (tid == 0)
-                mbar_arrive(&empty[freed % nbar]);
+                mbar_arrive(&empty[fslot]);
+            fslot = (fslot + 1 == nbar) ? 0 : fslot + 1;
+        }
     };
-    // RGB: this thread's 4 columns of chunk j, staging slot -> gray ring slot (Eq. 1)
-    auto convert = [&](int j) {
+    // RGB: this thread's 4 columns of the chunk just waited for (staging slot
+    // `last`), into the next gray ring slot (Eq. 1); chunks are converted in order
+    auto convert = [&]() {
+        const int gs = gslot;
+        gslot = (gslot + 1 == p.NS) ? 0 : gslot + 1;
         if (!owner)
             return;
-        const uint8_t *src = sbase + (size_t)(j % p.NSS) * CH * SWB;
-        uint8_t *dst = gbase + (size_t)(j % p.NS) * CH * SWP;
+        const uint8_t *src = sbase + (size_t)last * CH * SWB;
+        uint8_t *dst = gbase + (size_t)gs * CH * SWP;
         uint32_t wv[CH][3];
 #pragma unroll
         for (int r = 0; r < CH; ++r) {
@@ -239,7 +248,7 @@ __device__ __forceinline__ void produce(const CUtensorMap *tmap, const FusedPara
             wait_one();
         if (CIN == 3) {
             if (good)
-                convert(j);
+                convert();
             bar_sync(BAR_PROD, NTPW); // staging slot j is free
             release_to(j + 1);
         }
@@ -274,10 +283,9 @@ __device__ __forceinline__ void produce(const CUtensorMap *tmap, const FusedPara
         }
         const int need = min(k + D, sg.nchk - 1);
         while (good && waited <= need) {
-            const int j = waited;
             wait_one();
             if (CIN == 3 && good)
-                convert(j); // own columns only: no barrier before the column sums
+                convert(); // own columns only: no barrier before the column sums
         }
         const int rows_k = min(CH, sg.th_eff - k * CH);
         if (good && owner) {
