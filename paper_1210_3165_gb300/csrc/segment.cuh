@@ -338,6 +338,46 @@ __device__ __forceinline__ void produce(const CUtensorMap *tmap, const FusedPara
         release_to(sg.nchk);
 }
 
+// A lane's 16 outputs: running offsets d[t] = S(x0 + t) - S(x0) of the window
+// sums (leaving stream from column group ao, entering from ai, realigned at
+// compile time by KO / KI), and their total a = S(x0 + 16) - S(x0).
+template <int KO, int KI>
+__device__ __forceinline__ void lane_deltas(const uint32_t *C1, const uint32_t *C2, int ao, int ai, uint32_t (&d1)[L],
+                                            uint32_t (&d2)[L], uint32_t &a1, uint32_t &a2)
+{
+    a1 = 0;
+    a2 = 0;
+    uint4 o1 = ld_group(C1, ao), o2 = ld_group(C2, ao);
+    uint4 i1 = ld_group(C1, ai), i2 = ld_group(C2, ai);
+#pragma unroll
+    for (int j = 0; j < L / 4; ++j) {
+        uint4 o1n = make_uint4(0, 0, 0, 0), o2n = o1n, i1n = o1n, i2n = o1n;
+        if (KO != 0 || j + 1 < L / 4) {
+            o1n = ld_group(C1, ao + j + 1);
+            o2n = ld_group(C2, ao + j + 1);
+        }
+        if (KI != 0 || j + 1 < L / 4) {
+            i1n = ld_group(C1, ai + j + 1);
+            i2n = ld_group(C2, ai + j + 1);
+        }
+        const uint32_t vo1[8] = {o1.x, o1.y, o1.z, o1.w, o1n.x, o1n.y, o1n.z, o1n.w};
+        const uint32_t vo2[8] = {o2.x, o2.y, o2.z, o2.w, o2n.x, o2n.y, o2n.z, o2n.w};
+        const uint32_t vi1[8] = {i1.x, i1.y, i1.z, i1.w, i1n.x, i1n.y, i1n.z, i1n.w};
+        const uint32_t vi2[8] = {i2.x, i2.y, i2.z, i2.w, i2n.x, i2n.y, i2n.z, i2n.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            d1[4 * j + e] = a1;
+            d2[4 * j + e] = a2;
+            a1 = a1 + vi1[e + KI] - vo1[e + KO];
+            a2 = a2 + vi2[e + KI] - vo2[e + KO];
+        }
+        o1 = o1n;
+        o2 = o2n;
+        i1 = i1n;
+        i2 = i2n;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // consumers: horizontal sums, threshold, output (a4-a7)
 // ---------------------------------------------------------------------------
@@ -378,35 +418,7 @@ __device__ __forceinline__ void consume(const FusedParams &p, const Segment &sg,
             uint32_t d1[L], d2[L];
             uint32_t a1 = 0, a2 = 0;
             if (active) {
-                uint4 o1 = ld_group(C1, ao), o2 = ld_group(C2, ao);
-                uint4 i1 = ld_group(C1, ai), i2 = ld_group(C2, ai);
-#pragma unroll
-                for (int j = 0; j < L / 4; ++j) {
-                    uint4 o1n = make_uint4(0, 0, 0, 0), o2n = o1n, i1n = o1n, i2n = o1n;
-                    if (KO != 0 || j + 1 < L / 4) {
-                        o1n = ld_group(C1, ao + j + 1);
-                        o2n = ld_group(C2, ao + j + 1);
-                    }
-                    if (KI != 0 || j + 1 < L / 4) {
-                        i1n = ld_group(C1, ai + j + 1);
-                        i2n = ld_group(C2, ai + j + 1);
-                    }
-                    const uint32_t vo1[8] = {o1.x, o1.y, o1.z, o1.w, o1n.x, o1n.y, o1n.z, o1n.w};
-                    const uint32_t vo2[8] = {o2.x, o2.y, o2.z, o2.w, o2n.x, o2n.y, o2n.z, o2n.w};
-                    const uint32_t vi1[8] = {i1.x, i1.y, i1.z, i1.w, i1n.x, i1n.y, i1n.z, i1n.w};
-                    const uint32_t vi2[8] = {i2.x, i2.y, i2.z, i2.w, i2n.x, i2n.y, i2n.z, i2n.w};
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        d1[4 * j + e] = a1;
-                        d2[4 * j + e] = a2;
-                        a1 = a1 + vi1[e + KI] - vo1[e + KO];
-                        a2 = a2 + vi2[e + KI] - vo2[e + KO];
-                    }
-                    o1 = o1n;
-                    o2 = o2n;
-                    i1 = i1n;
-                    i2 = i2n;
-                }
+                lane_deltas<KO, KI>(C1, C2, ao, ai, d1, d2, a1, a2);
             } else {
 #pragma unroll
                 for (int t = 0; t < L; ++t)
@@ -485,34 +497,59 @@ __device__ __forceinline__ void consume(const FusedParams &p, const Segment &sg,
                 }
             }
             if (mn < p.E && active) { // rare: a value inside the fp32 margin -> fp64 for those pixels
+                // (1) which pixels: the 16 filters again, unrolled and independent (with
+                // each pixel's own n, as the border path), into a bit mask;
+                // (2) the fp64 sequence for the set bits only, typically one.  Register
+                // arrays are indexed with compile-time constants only, so nothing of the
+                // fast path moves to local memory.
                 const int nr = min(y + p.r_hi, p.h - 1) - max(y - p.r_lo, 0) + 1;
+                // the sums again from the column-sum buffer (still valid: it is released
+                // after this row), so the fast path's offsets need not live until here
+                uint32_t e1[L], e2[L], t1, t2;
+                lane_deltas<KO, KI>(C1, C2, ao, ai, e1, e2, t1, t2);
+                uint32_t amask = 0;
+#pragma unroll
                 for (int t = 0; t < L; ++t) {
                     const int xg = xg0 + t;
-                    if (xg >= p.w)
-                        break;
                     const int nc = min(xg + p.r_hi, p.w - 1) - max(xg - p.r_lo, 0) + 1;
                     const uint32_t n = (uint32_t)(nr * nc);
-                    uint32_t S1 = base1, S2 = base2;
-#pragma unroll
-                    for (int u = 0; u < L; ++u) // register arrays: select, never index dynamically
-                        if (u == t) {
-                            S1 += d1[u];
-                            S2 += d2[u];
-                        }
-                    const uint32_t f = byte_dyn(fw[t >> 2], t & 3);
+                    const uint32_t S1 = base1 + e1[t], S2 = base2 + e2[t];
                     const unsigned long long V = (unsigned long long)n * S2 - (unsigned long long)S1 * S1;
+                    const float ff = __uint2float_rn(byte_dyn(fw[t >> 2], t & 3));
                     const float sq = sqrt_approx(v_to_float(V));
-                    const float d = (n == p.nW)
-                                        ? filter_int<RULE>(__uint2float_rn(f), __uint2float_rn(S1), sq, p)
-                                        : filter_n<RULE>(__uint2float_rn(f), __uint2float_rn(S1), sq,
-                                                         rcp_approx(__uint2float_rn(n)), p);
-                    if (fabsf(d) < p.E) {
-                        const uint32_t r = decide_fp64<RULE>(f, n, S1, S2, p);
-                        ++nfb;
-                        nties += (r >> 9) & 1u;
-                        const int sh = 8 * (t & 3);
-                        outw[t >> 2] = (outw[t >> 2] & ~(0xffu << sh)) | ((r & 0xffu) << sh);
-                    }
+                    const float d = (n == p.nW) ? filter_int<RULE>(ff, __uint2float_rn(S1), sq, p)
+                                                : filter_n<RULE>(ff, __uint2float_rn(S1), sq,
+                                                                 rcp_approx(__uint2float_rn(n)), p);
+                    if (xg < p.w && fabsf(d) < p.E)
+                        amask |= 1u << t;
+                }
+                uint32_t white = 0; // bit t: the fp64 decision of pixel t is 255
+                for (uint32_t m = amask; m; m &= m - 1) {
+                    const int t = __ffs(m) - 1;
+                    uint32_t S1 = base1, S2 = base2, word = fw[0];
+#pragma unroll
+                    for (int u = 0; u < L; ++u)
+                        if (u == t) {
+                            S1 += e1[u];
+                            S2 += e2[u];
+                        }
+#pragma unroll
+                    for (int qq = 1; qq < 4; ++qq)
+                        if ((t >> 2) == qq)
+                            word = fw[qq];
+                    const uint32_t f = (word >> (8 * (t & 3))) & 0xffu;
+                    const int xg = xg0 + t;
+                    const int nc = min(xg + p.r_hi, p.w - 1) - max(xg - p.r_lo, 0) + 1;
+                    const uint32_t r = decide_fp64<RULE>(f, (uint32_t)(nr * nc), S1, S2, p);
+                    ++nfb;
+                    nties += (r >> 9) & 1u;
+                    white |= (r & 1u) << t;
+                }
+#pragma unroll
+                for (int qq = 0; qq < 4; ++qq) { // bits 4qq..4qq+3 -> bytes 0..3 of word qq
+                    const uint32_t mm = ((((amask >> (4 * qq)) & 15u) * 0x00204081u) & 0x01010101u) * 0xffu;
+                    const uint32_t vv = ((((white >> (4 * qq)) & 15u) * 0x00204081u) & 0x01010101u) * 0xffu;
+                    outw[qq] = (outw[qq] & ~mm) | (vv & mm);
                 }
             }
             if (active && xg0 < p.w) {
