@@ -76,12 +76,99 @@ __device__ __noinline__ uint32_t decide_fp64(uint32_t f, uint32_t n, uint32_t S1
     return (fd < td ? 0u : 255u) | tie;
 }
 
+// ---- double-float (two fp32 words, value = hi + lo) helpers ------------------
+// Explicit round-to-nearest intrinsics throughout: contraction into fma would
+// change the error terms.  u = 2^-24.
+
+struct df {
+    float hi, lo;
+};
+
+__device__ __forceinline__ df two_sum(float a, float b) // exact: a + b = s + e
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+__device__ __forceinline__ df fast_two_sum(float a, float b) // exact when |a| >= |b| or a == 0
+{
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ df df_add(df a, df b) // relative error <= 4u^2 (no cancellation assumed)
+{
+    const df s = two_sum(a.hi, b.hi);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+
+__device__ __forceinline__ df df_mul(df a, df b) // relative error <= 6u^2
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p); // exact product error
+    e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+    return fast_two_sum(p, e);
+}
+
+// x / n for exact fp32 x and integer n < 2^24: q = RN(x/n), the remainder
+// x - q n is exact (fma), the correction is rounded once (relative u^2 error)
+__device__ __forceinline__ df df_div_int(df x, float nf)
+{
+    const float q = __fdiv_rn(x.hi, nf);
+    const float r = __fmaf_rn(-q, nf, x.hi);
+    return fast_two_sum(q, __fdiv_rn(__fadd_rn(r, x.lo), nf));
+}
+
+// sqrt(V) for 0 <= V < 2^48 (V = hi 2^32 + lo): V in double-float from three
+// exact pieces, then one Newton correction of the rounded root
+__device__ __forceinline__ df df_sqrt_v(unsigned long long V)
+{
+    const uint32_t h = (uint32_t)(V >> 32), lo = (uint32_t)V;
+    const df a = two_sum(__fmul_rn(__uint2float_rn(h), 4294967296.0f), __uint2float_rn(lo >> 16) * 65536.0f);
+    const df v = fast_two_sum(a.hi, __fadd_rn(a.lo, __uint2float_rn(lo & 0xffffu)));
+    if (v.hi == 0.0f)
+        return {0.0f, 0.0f};
+    const float sh = __fsqrt_rn(v.hi);
+    const float p = __fmul_rn(sh, sh);
+    const float pe = __fmaf_rn(sh, sh, -p);
+    const float r = __fadd_rn(__fsub_rn(__fsub_rn(v.hi, p), pe), v.lo); // V - sh^2, to rounding
+    return fast_two_sum(sh, __fdiv_rn(r, __fmul_rn(2.0f, sh)));
+}
+
+// Eq. 3 for a pixel the fp32 filter could not decide.  f - t in double-float
+// (Niblack t = m + k s; Sauvola t = m (1-k) + m s (k/R), m = S1/n, s = sqrt(V)/n),
+// absolute error < 1e-10 for every f, m <= 255, s <= 128, |k| <= 16.  When it
+// is farther than 1e-9 + 1e-10 + 1e-12 from zero, neither the exact value nor
+// the fp64 definition (within 1e-12 of it) is a tie and the sign decides;
+// otherwise the fp64 sequence of the definition decides (and counts the tie).
+template <int RULE>
+__device__ uint32_t decide_exact(uint32_t f, uint32_t n, uint32_t S1, uint32_t S2, const FusedParams &p)
+{
+    const unsigned long long V = (unsigned long long)n * S2 - (unsigned long long)S1 * S1;
+    const float nf = __uint2float_rn(n);
+    const df m = df_div_int({__uint2float_rn(S1), 0.0f}, nf);
+    const df sv = df_sqrt_v(V);
+    const df sd = df_div_int(sv, nf);
+    df t;
+    if (RULE == BNZ_SAUVOLA)
+        t = df_add(df_mul(m, {p.c1h, p.c1l}), df_mul(df_mul(m, sd), {p.c2h, p.c2l}));
+    else
+        t = df_add(m, df_mul({p.kh, p.kl}, sd));
+    const df d = df_add({__uint2float_rn(f), 0.0f}, {-t.hi, -t.lo});
+    const float dv = __fadd_rn(d.hi, d.lo);
+    if (fabsf(dv) > 1.2e-9f)
+        return dv < 0.0f ? 0u : 255u;
+    return decide_fp64<RULE>(f, n, S1, S2, p);
+}
+
 } // namespace bnz
 
 namespace bnz {
 
-// Eq. 3 for one pixel with exact window sums: fp32 filter, fp64 when inside
-// the margin.  Counts fp64 evaluations and ties.
+// Eq. 3 for one pixel with exact window sums: fp32 filter, double-float and
+// then fp64 when inside the margin.  Counts re-evaluated pixels and ties.
 template <int RULE>
 __device__ __forceinline__ uint32_t decide_pixel(uint32_t f, uint32_t n, uint32_t S1, uint32_t S2,
                                                  const FusedParams &p, uint32_t &nfb, uint32_t &nties)
@@ -93,7 +180,7 @@ __device__ __forceinline__ uint32_t decide_pixel(uint32_t f, uint32_t n, uint32_
                                 : filter_n<RULE>(ff, S1f, sq, rcp_approx(__uint2float_rn(n)), p);
     if (fabsf(d) >= p.E)
         return d < 0.0f ? 0u : 255u;
-    const uint32_t r = decide_fp64<RULE>(f, n, S1, S2, p);
+    const uint32_t r = decide_exact<RULE>(f, n, S1, S2, p);
     ++nfb;
     nties += (r >> 9) & 1u;
     return r & 0xffu;

@@ -183,6 +183,13 @@ void fill_decision_params(FusedParams *p, int h, int w, int W, int rule, double 
     p->omk = (float)(1.0 - k);
     p->kR = (float)(k / R);
     p->E = decision_margin(rule, k, R);
+    auto split = [](double x, float *hi, float *lo) {
+        *hi = (float)x;
+        *lo = (float)(x - (double)*hi);
+    };
+    split(k, &p->kh, &p->kl);
+    split(1.0 - k, &p->c1h, &p->c1l);
+    split(k / R, &p->c2h, &p->c2l);
 }
 
 int plan_shape(int h, int w, int ch, int W, int want_tw, FusedPlan *pl)

@@ -64,6 +64,8 @@ struct FusedParams {
     float omkn, kRn2, invn, kn;
     float kf, omk, kR; // k, 1-k, k/R for windows with a per-pixel n
     float E;           // proven bound on |d32 - (f - t)|, with safety factor
+    // double-float constants of the second stage: k, 1-k, k/R as hi + lo
+    float kh, kl, c1h, c1l, c2h, c2l;
     long long timeout_cycles;
 };
 

@@ -540,7 +540,7 @@ __device__ __forceinline__ void consume(const FusedParams &p, const Segment &sg,
                     const uint32_t f = (word >> (8 * (t & 3))) & 0xffu;
                     const int xg = xg0 + t;
                     const int nc = min(xg + p.r_hi, p.w - 1) - max(xg - p.r_lo, 0) + 1;
-                    const uint32_t r = decide_fp64<RULE>(f, (uint32_t)(nr * nc), S1, S2, p);
+                    const uint32_t r = decide_exact<RULE>(f, (uint32_t)(nr * nc), S1, S2, p);
                     ++nfb;
                     nties += (r >> 9) & 1u;
                     white |= (r & 1u) << t;
