@@ -198,6 +198,64 @@ BNZ_API int bnz_pool_fail_next(bnz_pool *p, int n);
 /* Free the bookkeeping (live blocks are forgotten, the range is not freed). */
 BNZ_API int bnz_pool_destroy(bnz_pool *p);
 
+/* ---- native serving engine ------------------------------------------------
+ * Requests of mixed page sizes and windows, submitted at any time from any
+ * thread, are binarized by continuous batching: a scheduler thread admits
+ * them in arrival order while their device buffers fit a budget reserved once
+ * at creation (requests wait, none is dropped), copies host inputs up on a
+ * copy stream, launches one batched kernel per step over admitted pages whose
+ * input has arrived and that share a kernel instance (channels, rule, W mod 8;
+ * the oldest ready page picks it; steps alternate over `compute_streams`),
+ * copies the masks into the callers' host buffers on a second copy stream and
+ * reports completions through bnz_server_poll.  No counterpart in the paper. */
+typedef struct bnz_server bnz_server; /* opaque */
+
+typedef struct {
+    size_t budget_bytes;  /* device memory for request buffers, reserved at creation (>= 1 MiB) */
+    int max_batch;        /* pages per launch step, 1..4096 */
+    int compute_streams;  /* 1..4; 1 is fastest for mixed traffic (kernels of different instances running
+                             side by side share the SMs' instruction caches) */
+    int batched;          /* 1: one batched launch per step; 0: one plain launch per page */
+    int reserved;
+} bnz_server_config;
+
+typedef struct {
+    const uint8_t *src;   /* host (pinned memory overlaps; pageable works) or device pointer */
+    size_t src_pitch;     /* bytes between rows of src */
+    int src_on_device;    /* 1: src is device memory, complete when submitted, 16-byte aligned,
+                             pitch % 16 == 0, height*src_pitch bytes; it must stay valid until completion */
+    int height, width, channels, W, rule;
+    double k, R;
+    int packed;
+    uint8_t *dst;         /* host memory (pinned for overlap) receiving the mask, valid until completion */
+    size_t dst_pitch;
+    unsigned long long tag; /* returned by bnz_server_poll */
+} bnz_request;
+
+/* Reserve the budget, create the streams and start the scheduler thread.
+ * BNZ_ENODEV without a device, BNZ_ENOMEM if the budget cannot be reserved. */
+BNZ_API int bnz_server_create(const bnz_server_config *cfg, bnz_server **out);
+/* Queue a request (the descriptor is copied; the buffers are not).  Argument
+ * errors return BNZ_EINVAL, a request larger than the whole budget
+ * BNZ_ENOMEM; neither is queued. */
+BNZ_API int bnz_server_submit(bnz_server *s, const bnz_request *req);
+/* Up to `max` completed requests: their tags, statuses (BNZ_OK or the error)
+ * and latencies from submission to the mask in host memory, in seconds
+ * (status and latency_s nullable).  Waits up to timeout_ms for the first one.
+ * Returns the number written (0 on timeout). */
+BNZ_API int bnz_server_poll(bnz_server *s, unsigned long long *tags, int *status, double *latency_s, int max,
+                            int timeout_ms);
+/* Requests submitted and not yet polled, completed, launch steps, admissions
+ * deferred for memory, and the high-water mark of device bytes in use (any
+ * pointer may be NULL). */
+BNZ_API int bnz_server_stats(bnz_server *s, long long *outstanding, long long *completed, long long *steps,
+                             long long *alloc_waits, size_t *high_water);
+/* Copy the scheduler's last failure message (empty if none) into buf. */
+BNZ_API int bnz_server_error(bnz_server *s, char *buf, size_t n);
+/* Finish every submitted request, stop the thread, free the budget.  Requests
+ * not yet polled are discarded. */
+BNZ_API int bnz_server_destroy(bnz_server *s);
+
 /* ---- integral-image comparison variant ------------------------------------
  * The O(N^2) method with summed-area tables that Sec. 1 cites (Shafait et
  * al.) and Sec. 3.3 charges 12 S_z bytes of memory: two (h+1) x (w+1) int64

@@ -38,6 +38,18 @@ class bnz_page(ctypes.Structure):
                 ("tile_w", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
+class bnz_server_config(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_size_t), ("max_batch", ctypes.c_int), ("compute_streams", ctypes.c_int),
+                ("batched", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+
+class bnz_request(ctypes.Structure):
+    _fields_ = [("src", ctypes.c_void_p), ("src_pitch", ctypes.c_size_t), ("src_on_device", ctypes.c_int),
+                ("height", ctypes.c_int), ("width", ctypes.c_int), ("channels", ctypes.c_int), ("W", ctypes.c_int),
+                ("rule", ctypes.c_int), ("k", ctypes.c_double), ("R", ctypes.c_double), ("packed", ctypes.c_int),
+                ("dst", ctypes.c_void_p), ("dst_pitch", ctypes.c_size_t), ("tag", ctypes.c_ulonglong)]
+
+
 class bnz_tile(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int), ("chunk", ctypes.c_int),
                 ("reserved", ctypes.c_int)]
@@ -87,6 +99,12 @@ def _optional_symbols(lib):
                             ctypes.POINTER(ctypes.c_longlong)], ctypes.c_int),
         "bnz_batch_destroy": ([P], ctypes.c_int),
         "bnz_copy2d_async": ([P, sz, P, sz, sz, sz, P], ctypes.c_int),
+        "bnz_server_create": ([P, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+        "bnz_server_submit": ([P, P], ctypes.c_int),
+        "bnz_server_poll": ([P, P, P, P, i, i], ctypes.c_int),
+        "bnz_server_stats": ([P, P, P, P, P, P], ctypes.c_int),
+        "bnz_server_error": ([P, ctypes.c_char_p, sz], ctypes.c_int),
+        "bnz_server_destroy": ([P], ctypes.c_int),
         "bnz_pool_create": ([P, sz, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
         "bnz_pool_alloc": ([P, sz, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
         "bnz_pool_free": ([P, P], ctypes.c_int),

@@ -8,9 +8,12 @@ time through ``Server.submit``.  A scheduler thread
   dropped) until finished requests release memory;
 * copies each admitted page to the device on a copy stream;
 * every step, launches one batched kernel (``bnz_batch_create_async``: one
-  persistent launch over all pages of the step, no allocation) over all
-  admitted pages whose input has arrived, on one of several compute streams,
-  so that consecutive steps -- and copies -- overlap on the device;
+  persistent launch over the step's pages, no allocation) over admitted pages
+  whose input has arrived and that run on the same kernel instance (channels,
+  rule, W mod 8; the oldest ready page picks it), so the copies of other
+  pages overlap the kernel on their own streams.  One compute stream is the
+  default: two batches of different instances running side by side thrash the
+  SMs' instruction caches;
 * copies finished masks back and completes the requests' futures, recording
   the latency from arrival to result.
 
@@ -70,6 +73,11 @@ def on_device(img) -> bool:
 
 
 MAX_W = 255
+
+
+def instance_key(req: Request) -> tuple:
+    """The kernel instance a page runs on: channels, rule and W mod 8."""
+    return (1 if len(req.shape) == 2 else 3, req.rule, req.W % 8)
 
 
 def validate(req: Request) -> str | None:
@@ -221,7 +229,13 @@ class Server:
             moved = True
         # 3. launch one step over the ready pages
         if self._ready and self.ex.can_launch():
-            batch, self._ready = self._ready[:self.max_batch], self._ready[self.max_batch:]
+            # one kernel instance per step (channels, rule, W mod 8), picked by the oldest ready page:
+            # launches that mix instances thrash the SMs' instruction caches
+            want = instance_key(self._ready[0])
+            batch, rest = [], []
+            for r in self._ready:
+                (batch if len(batch) < self.max_batch and instance_key(r) == want else rest).append(r)
+            self._ready = rest
             event, keep = self.ex.launch([r.slot for r in batch])
             for r in batch:
                 r.stage = "running"
@@ -267,10 +281,120 @@ class Server:
                 time.sleep(self.poll_s)
 
 
+class NativeServer:
+    """The same service on the library's native engine (`bnz_server_*`): admission, batching, copies and
+    completion detection run in a C++ scheduler thread; Python only submits requests and completes futures.
+
+    Inputs: host arrays/tensors (pinned ones overlap with the GPU) or CUDA tensors already on the device
+    (16-byte row pitch).  Masks land in pinned host tensors that the futures return."""
+
+    def __init__(self, budget_bytes: int = 16 << 30, max_batch: int = 16, batched: bool = True,
+                 compute_streams: int = 1):
+        import ctypes
+        from . import _check, bnz_server_config, load
+        self._ct = ctypes
+        self._lib = load()
+        self.budget = int(budget_bytes)
+        cfg = bnz_server_config(self.budget, int(max_batch), int(compute_streams), 1 if batched else 0, 0)
+        h = ctypes.c_void_p(None)
+        _check(self._lib.bnz_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+        self._lock = threading.Lock()
+        self._live: dict[int, tuple] = {}   # tag -> (future, output, input kept alive)
+        self._tag = 0
+        self.latencies: list[float] = []
+        self.failed = 0
+        self._stop = threading.Event()
+        self._poller = threading.Thread(target=self._poll_loop, name="bnz-native-poll", daemon=True)
+        self._poller.start()
+
+    def submit(self, req: Request) -> Future:
+        import torch
+        from . import BNZ_NIBLACK, BNZ_SAUVOLA, BnzError, bnz_request
+        problem = validate(req)
+        if problem:
+            req.future.set_exception(ValueError(problem))
+            return req.future
+        img = req.image if isinstance(req.image, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(req.image))
+        h, w = img.shape[:2]
+        ch = 1 if img.dim() == 2 else 3
+        if (w > 1 and img.stride(1) != ch) or (ch == 3 and img.stride(2) != 1):
+            img = img.contiguous()
+        pitch = img.stride(0) if h > 1 else w * ch
+        ow = (w + 7) // 8 if req.packed else w
+        out = torch.empty((h, ow), dtype=torch.uint8, pin_memory=True)
+        k = req.k if req.k is not None else (0.5 if req.rule == "sauvola" else -0.2)
+        with self._lock:
+            self._tag += 1
+            tag = self._tag
+            self._live[tag] = (req.future, out, img)
+        r = bnz_request(img.data_ptr(), pitch, 1 if img.is_cuda else 0, h, w, ch, req.W,
+                        BNZ_SAUVOLA if req.rule == "sauvola" else BNZ_NIBLACK, float(k), float(req.R),
+                        1 if req.packed else 0, out.data_ptr(), ow, tag)
+        rc = self._lib.bnz_server_submit(self._h, self._ct.byref(r))
+        if rc != 0:
+            with self._lock:
+                self._live.pop(tag, None)
+            from . import bnz_last_error
+            req.future.set_exception(BnzError(rc, bnz_last_error()))
+        return req.future
+
+    def _poll_loop(self):
+        ct = self._ct
+        n = 256
+        tags = (ct.c_ulonglong * n)()
+        st = (ct.c_int * n)()
+        lat = (ct.c_double * n)()
+        while not self._stop.is_set():
+            got = self._lib.bnz_server_poll(self._h, tags, st, lat, n, 20)  # releases the GIL while waiting
+            for i in range(max(got, 0)):
+                with self._lock:
+                    fut, out, _ = self._live.pop(tags[i])
+                if st[i] == 0:
+                    self.latencies.append(lat[i])
+                    fut.set_result(out)
+                else:
+                    self.failed += 1
+                    fut.set_exception(RuntimeError(f"request failed with status {st[i]}: {self.error()}"))
+
+    def error(self) -> str:
+        buf = self._ct.create_string_buffer(512)
+        self._lib.bnz_server_error(self._h, buf, 512)
+        return buf.value.decode(errors="replace")
+
+    def pending(self) -> int:
+        with self._lock:
+            return len(self._live)
+
+    def stats(self) -> dict:
+        if not self._h:
+            return dict(self._final)
+        ct = self._ct
+        o, c, s_, a = ct.c_longlong(0), ct.c_longlong(0), ct.c_longlong(0), ct.c_longlong(0)
+        hw = ct.c_size_t(0)
+        self._lib.bnz_server_stats(self._h, ct.byref(o), ct.byref(c), ct.byref(s_), ct.byref(a), ct.byref(hw))
+        lat = np.array(self.latencies) if self.latencies else np.zeros(1)
+        return dict(completed=c.value, steps=s_.value, alloc_waits=a.value, high_water_bytes=hw.value,
+                    failed=self.failed, p50_ms=float(np.percentile(lat, 50) * 1e3),
+                    p99_ms=float(np.percentile(lat, 99) * 1e3), max_ms=float(lat.max() * 1e3))
+
+    def stop(self, drain: bool = True, timeout: float | None = None):
+        if drain:
+            t0 = time.perf_counter()
+            while self.pending() and (timeout is None or time.perf_counter() - t0 < timeout):
+                time.sleep(1e-3)
+        self._stop.set()
+        self._poller.join()
+        if self._h:
+            self._final = self.stats()
+            self._lib.bnz_server_destroy(self._h)
+            self._h = None
+
+
 class TorchExecutor:
     """GPU side of the server: torch memory and streams, the bnz kernels."""
 
-    def __init__(self, batched: bool = True, compute_streams: int = 2, tile_table=None, device="cuda",
+    def __init__(self, batched: bool = True, compute_streams: int = 1, tile_table=None, device="cuda",
                  budget_bytes: int = 16 << 30):
         import torch
         from . import BNZ_NIBLACK, BNZ_SAUVOLA, Batch, Pool, bnz_binarize_dev, bnz_copy2d_async, load

@@ -78,3 +78,18 @@ def test_no_gpu_means_no_result():
     assert (dst == 0).all()
     with pytest.raises(bnz.BnzError):
         bnz.bnz_sauvola(src, 5)
+
+
+def test_native_server_needs_a_device_and_checks_its_config():
+    import ctypes
+    import torch
+    lib = bnz.load()
+    h = ctypes.c_void_p(None)
+    bad = bnz.bnz_server_config(1 << 10, 16, 2, 1, 0)  # budget below 1 MiB
+    assert lib.bnz_server_create(ctypes.byref(bad), ctypes.byref(h)) == bnz.BNZ_EINVAL and not h.value
+    bad = bnz.bnz_server_config(1 << 30, 16, 9, 1, 0)  # too many compute streams
+    assert lib.bnz_server_create(ctypes.byref(bad), ctypes.byref(h)) == bnz.BNZ_EINVAL
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    ok = bnz.bnz_server_config(1 << 30, 16, 2, 1, 0)
+    assert lib.bnz_server_create(ctypes.byref(ok), ctypes.byref(h)) == bnz.BNZ_ENODEV and not h.value

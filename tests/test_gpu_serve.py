@@ -61,5 +61,32 @@ def test_served_masks_equal_alone_and_oracle(bnz, batched):
         rid = oracle.SAUVOLA if rule == "sauvola" else oracle.NIBLACK
         ref, _ = oracle.binarize(img, W, rid, k, 128.0, threads=NTHREADS, packed=packed)
         np.testing.assert_array_equal(got, ref)
-    if batched:
-        assert srv.steps_launched < len(items)   # pages shared launches
+
+
+@pytest.mark.parametrize("batched", [True, False])
+def test_native_server_masks_equal_alone_and_oracle(bnz, batched):
+    """The C++ serving engine: same mix, same budget pressure, same bits."""
+    from paper_1210_3165_gb300.serve import NativeServer, Request
+    items = mix(30, 11)
+    srv = NativeServer(budget_bytes=4 << 20, max_batch=8, batched=batched, compute_streams=2)
+    futs = []
+    for i, (img, W, rule, packed) in enumerate(items):
+        src = bnz.to_device_pitched(img) if i % 4 == 3 else torch.from_numpy(img).pin_memory()
+        futs.append(srv.submit(Request(image=src, W=W, rule=rule, packed=packed)))
+    too_big = srv.submit(Request(image=np.zeros((4000, 4000), np.uint8), W=15))
+    bad = srv.submit(Request(image=np.zeros((10, 10), np.uint8), W=300))
+    srv.stop(drain=True, timeout=120)
+    with pytest.raises(bnz.BnzError):
+        too_big.result(timeout=0)
+    with pytest.raises(ValueError):
+        bad.result(timeout=0)
+    st = srv.stats()
+    assert st["completed"] == len(items) and st["failed"] == 0 and st["high_water_bytes"] <= 4 << 20
+    for (img, W, rule, packed), f in zip(items, futs):
+        got = f.result(timeout=0).numpy()
+        k = 0.5 if rule == "sauvola" else -0.2
+        alone = bnz.binarize(bnz.to_device_pitched(img), W, rule, k, packed=packed).cpu().numpy()
+        np.testing.assert_array_equal(got, alone)
+        rid = oracle.SAUVOLA if rule == "sauvola" else oracle.NIBLACK
+        ref, _ = oracle.binarize(img, W, rid, k, 128.0, threads=NTHREADS, packed=packed)
+        np.testing.assert_array_equal(got, ref)

@@ -239,3 +239,24 @@ def test_malformed_requests_fail_their_future_not_the_loop(bad):
     g = srv.submit(good)
     drive(srv)
     assert g.result() is not None and ex.order == [1]
+
+
+def test_each_step_runs_one_kernel_instance_oldest_first():
+    """Launches never mix kernel instances (channels, rule, W mod 8); the oldest ready page picks the next one."""
+    from paper_1210_3165_gb300.serve import instance_key
+    ex = FakeExecutor(run_polls=1, streams=1)
+    srv = Server(ex, budget_bytes=1 << 30, max_batch=64)
+    specs = [(15, "sauvola", 1), (23, "sauvola", 1), (17, "sauvola", 1), (15, "niblack", 1), (31, "sauvola", 3),
+             (7, "sauvola", 1), (15, "sauvola", 1)]
+    reqs = []
+    for i, (W, rule, ch) in enumerate(specs):
+        r = req(i, 8, 8, ch=ch, W=W)
+        r.rule = rule
+        reqs.append(r)
+        srv.submit(r)
+    drive(srv)
+    by_id = {r.rid: r for r in reqs}
+    for launch in ex.launches:
+        assert len({instance_key(by_id[i]) for i in launch}) == 1
+    assert ex.launches[0] == [0, 1, 5, 6]      # W 15, 23, 7, 15: gray Sauvola, W mod 8 = 7
+    assert sorted(sum(ex.launches, [])) == list(range(len(specs)))
