@@ -116,6 +116,7 @@ class Server:
         self._admitted: list[Request] = []   # input copy in flight
         self._ready: list[Request] = []      # on the device, not launched
         self._steps: list[tuple[object, list[Request], object]] = []  # (event, requests, keep-alive)
+        self._to_host: list[Request] = []                                # computed, mask copy not yet issued
         self._back: list[tuple[object, Request, object]] = []          # (event, request, host result)
         self._stop = threading.Event()
         self._thread: threading.Thread | None = None
@@ -242,18 +243,28 @@ class Server:
             self._steps.append((event, batch, keep))
             self.steps_launched += 1
             moved = True
-        # 4. finished steps: results back to the host
+        # 4. finished steps: results back to the host (in order; a request that finds no host
+        #    memory for its mask waits in _to_host and is retried after deliveries free some)
         still_steps = []
         for event, batch, keep in self._steps:
             if self.ex.done(event):
-                for r in batch:
-                    ev, host = self.ex.d2h(r.slot)
-                    r.stage = "d2h"
-                    self._back.append((ev, r, host))
+                self._to_host.extend(batch)
                 moved = True
             else:
                 still_steps.append((event, batch, keep))
         self._steps = still_steps
+        n = 0
+        for r in self._to_host:
+            got = self.ex.d2h(r.slot)
+            if got is None:
+                break
+            ev, host = got
+            r.stage = "d2h"
+            self._back.append((ev, r, host))
+            n += 1
+        if n:
+            del self._to_host[:n]
+            moved = True
         # 5. delivered results (in issue order): complete, release memory
         n = 0
         for ev, r, host in self._back:
@@ -281,17 +292,59 @@ class Server:
                 time.sleep(self.poll_s)
 
 
+class _Block:
+    """Owner of one arena block; numpy arrays over it keep it alive, the last one frees it."""
+
+    def __init__(self, pool, ptr: int, h: int, w: int):
+        self._pool, self.ptr = pool, ptr
+        self.__array_interface__ = {"shape": (h, w), "typestr": "|u1", "data": (ptr, False), "version": 3}
+
+    def __del__(self):
+        try:
+            self._pool.free(self.ptr)
+        except Exception:
+            pass
+
+
+class HostArena:
+    """Pinned host memory reserved once and carved by the native pool bookkeeping: mask buffers for the
+    serving loops without a cudaHostAlloc per request.  Blocks are numpy arrays whose base object returns
+    the memory when the last array viewing it goes away."""
+
+    def __init__(self, nbytes: int):
+        import torch
+        from . import Pool
+        self.buf = torch.empty((int(nbytes),), dtype=torch.uint8, pin_memory=True)
+        self.pool = Pool(self.buf)
+
+    def take(self, h: int, w: int, wait_s: float = 60.0) -> np.ndarray | None:
+        """An (h, w) uint8 array in pinned memory.  While the arena is full it waits up to wait_s
+        (wait_s = 0: returns None at once), then raises MemoryError."""
+        t0 = time.perf_counter()
+        while True:
+            ptr = self.pool.alloc(h * w)
+            if ptr is not None:
+                break
+            if wait_s == 0:
+                return None
+            if time.perf_counter() - t0 > wait_s:
+                raise MemoryError(f"host arena full for {wait_s} s")
+            time.sleep(1e-4)
+        return np.asarray(_Block(self.pool, ptr, h, w))
+
+
 class NativeServer:
     """The same service on the library's native engine (`bnz_server_*`): admission, batching, copies and
     completion detection run in a C++ scheduler thread; Python only submits requests and completes futures.
 
     Inputs: host arrays/tensors (pinned ones overlap with the GPU) or CUDA tensors already on the device
-    (16-byte row pitch).  Masks land in pinned host tensors that the futures return."""
+    (16-byte row pitch).  Masks land in a pinned host arena; the futures return numpy arrays over it."""
 
     def __init__(self, budget_bytes: int = 16 << 30, max_batch: int = 16, batched: bool = True,
-                 compute_streams: int = 1):
+                 compute_streams: int = 1, host_bytes: int = 4 << 30):
         import ctypes
         from . import _check, bnz_server_config, load
+        self.host = HostArena(host_bytes)
         self._ct = ctypes
         self._lib = load()
         self.budget = int(budget_bytes)
@@ -322,7 +375,7 @@ class NativeServer:
             img = img.contiguous()
         pitch = img.stride(0) if h > 1 else w * ch
         ow = (w + 7) // 8 if req.packed else w
-        out = torch.empty((h, ow), dtype=torch.uint8, pin_memory=True)
+        out = self.host.take(h, ow)
         k = req.k if req.k is not None else (0.5 if req.rule == "sauvola" else -0.2)
         with self._lock:
             self._tag += 1
@@ -330,7 +383,7 @@ class NativeServer:
             self._live[tag] = (req.future, out, img)
         r = bnz_request(img.data_ptr(), pitch, 1 if img.is_cuda else 0, h, w, ch, req.W,
                         BNZ_SAUVOLA if req.rule == "sauvola" else BNZ_NIBLACK, float(k), float(req.R),
-                        1 if req.packed else 0, out.data_ptr(), ow, tag)
+                        1 if req.packed else 0, out.ctypes.data, ow, tag)
         rc = self._lib.bnz_server_submit(self._h, self._ct.byref(r))
         if rc != 0:
             with self._lock:
@@ -395,7 +448,7 @@ class TorchExecutor:
     """GPU side of the server: torch memory and streams, the bnz kernels."""
 
     def __init__(self, batched: bool = True, compute_streams: int = 1, tile_table=None, device="cuda",
-                 budget_bytes: int = 16 << 30):
+                 budget_bytes: int = 16 << 30, host_bytes: int = 4 << 30):
         import torch
         from . import BNZ_NIBLACK, BNZ_SAUVOLA, Batch, Pool, bnz_binarize_dev, bnz_copy2d_async, load
         from .tune import tile_for
@@ -406,6 +459,7 @@ class TorchExecutor:
         self.budget_bytes = int(budget_bytes)
         self.arena = torch.empty((self.budget_bytes,), dtype=torch.uint8, device=self.dev)
         self.pool = Pool(self.arena)
+        self.host = HostArena(host_bytes)
         self.batched = batched
         self.copy_in = torch.cuda.Stream(self.dev)
         self.copy_out = torch.cuda.Stream(self.dev)
@@ -507,8 +561,10 @@ class TorchExecutor:
         torch = self.torch
         dst = slot["dst"]
         h, wb = dst.shape
-        host = torch.empty((h, wb), dtype=torch.uint8, pin_memory=True)
-        self._copy2d(host.data_ptr(), wb, dst.data_ptr(), dst.stride(0) if h > 1 else wb, wb, h, self.copy_out)
+        host = self.host.take(h, wb, wait_s=0)
+        if host is None:  # host arena full: the scheduler retries once delivered results free some
+            return None
+        self._copy2d(host.ctypes.data, wb, dst.data_ptr(), dst.stride(0) if h > 1 else wb, wb, h, self.copy_out)
         ev = torch.cuda.Event()
         ev.record(self.copy_out)
         slot["host_out"] = host

@@ -260,3 +260,44 @@ def test_each_step_runs_one_kernel_instance_oldest_first():
         assert len({instance_key(by_id[i]) for i in launch}) == 1
     assert ex.launches[0] == [0, 1, 5, 6]      # W 15, 23, 7, 15: gray Sauvola, W mod 8 = 7
     assert sorted(sum(ex.launches, [])) == list(range(len(specs)))
+
+
+def test_host_arena_blocks_live_as_long_as_any_view():
+    """Result arrays are views of one pinned arena; a block returns to the pool only when the last array
+    viewing it is gone (here over plain memory: the bookkeeping never touches the bytes)."""
+    import gc
+    import paper_1210_3165_gb300 as bnz
+    from paper_1210_3165_gb300.serve import _Block
+    buf = np.zeros(1 << 16, np.uint8)
+    base = buf.ctypes.data + ((-buf.ctypes.data) % 256)
+    pool = bnz.Pool(base, (1 << 16) - 512)
+    a = np.asarray(_Block(pool, pool.alloc(100 * 50), 100, 50))
+    a[:] = 7
+    part = a[10:20]
+    del a
+    gc.collect()
+    assert pool.stats()["live"] == 1 and int(part.sum()) == 7 * 10 * 50
+    del part
+    gc.collect()
+    assert pool.stats()["live"] == 0
+
+
+def test_mask_copies_wait_for_host_memory_without_stalling_the_loop():
+    """When the host arena has no room for a mask, the request keeps its place and is retried; the loop
+    goes on delivering (which frees host memory) instead of blocking."""
+    class TightHost(FakeExecutor):
+        def __init__(self):
+            super().__init__()
+            self.refusals = 0
+
+        def d2h(self, slot):
+            if self.refusals < 5:   # the first attempts find the host arena full
+                self.refusals += 1
+                return None
+            return super().d2h(slot)
+
+    ex = TightHost()
+    srv = Server(ex, budget_bytes=1 << 30, max_batch=4)
+    futs = [srv.submit(req(i, 8, 8)) for i in range(12)]
+    drive(srv)
+    assert all(f.result() is not None for f in futs) and ex.refusals == 5
