@@ -90,3 +90,21 @@ def test_native_server_masks_equal_alone_and_oracle(bnz, batched):
         rid = oracle.SAUVOLA if rule == "sauvola" else oracle.NIBLACK
         ref, _ = oracle.binarize(img, W, rid, k, 128.0, threads=NTHREADS, packed=packed)
         np.testing.assert_array_equal(got, ref)
+
+
+@pytest.mark.parametrize("rule,W", [("sauvola", 101), ("niblack", 15)])
+def test_native_server_full_size_page(bnz, rule, W):
+    """The largest page of the serving workload (7016 x 4960 RGB, 104 MB) through the native engine, once from
+    pinned host memory and once resident on the device, equals the oracle bit for bit."""
+    from paper_1210_3165_gb300.serve import NativeServer, Request
+    img = synth.page(7016, 4960, 31, synth.STAINS, 3, random_dir=True)
+    k = 0.5 if rule == "sauvola" else -0.2
+    rid = oracle.SAUVOLA if rule == "sauvola" else oracle.NIBLACK
+    ref, _ = oracle.binarize(img, W, rid, k, 128.0, threads=NTHREADS)
+    srv = NativeServer(budget_bytes=1 << 30, max_batch=4)
+    f_host = srv.submit(Request(image=torch.from_numpy(img).pin_memory(), W=W, rule=rule, k=k))
+    f_dev = srv.submit(Request(image=bnz.to_device_pitched(img), W=W, rule=rule, k=k))
+    got_host, got_dev = np.asarray(f_host.result(timeout=120)), np.asarray(f_dev.result(timeout=120))
+    srv.stop()
+    np.testing.assert_array_equal(got_host, ref)
+    np.testing.assert_array_equal(got_dev, ref)
