@@ -178,6 +178,80 @@ static int binarize_dev(const uint8_t *d_src, size_t src_pitch, int height, int 
 
 // Synchronous host-pointer path: stream-ordered device buffers, copies in and
 // out, one launch, then a check of the device error word.
+// Per-thread, per-device resources of the synchronous host API, made once: a
+// stream, grow-only device buffers for the page and its mask, and statistics
+// counters with a pinned host copy.  Creating a stream, allocating and freeing
+// tens of MB (the default pool returns freed memory at each synchronize), or a
+// blocking read of the error word, per call would cost more than the kernel.
+struct HostCallState {
+    struct PerDevice {
+        cudaStream_t stream = nullptr;
+        unsigned long long *stats = nullptr, *h_stats = nullptr;
+        void *src = nullptr, *dst = nullptr;
+        size_t src_cap = 0, dst_cap = 0;
+    };
+    PerDevice dev[64];
+    ~HostCallState()
+    {
+        for (int d = 0; d < 64; ++d) {
+            PerDevice &v = dev[d];
+            if (!v.stream && !v.stats && !v.src && !v.dst && !v.h_stats)
+                continue;
+            cudaSetDevice(d);
+            if (v.stream)
+                cudaStreamDestroy(v.stream);
+            cudaFree(v.stats);
+            cudaFree(v.src);
+            cudaFree(v.dst);
+            cudaFreeHost(v.h_stats);
+        }
+    }
+};
+
+static int grow(void **buf, size_t *cap, size_t need, const char *what)
+{
+    if (*cap >= need)
+        return BNZ_OK;
+    cudaFree(*buf);
+    *buf = nullptr;
+    *cap = 0;
+    const cudaError_t e = cudaMalloc(buf, need);
+    if (e != cudaSuccess) {
+        *buf = nullptr;
+        return cuda_fail(e, what);
+    }
+    *cap = need;
+    return BNZ_OK;
+}
+
+static int host_call_state(int d, size_t src_bytes, size_t dst_bytes, HostCallState::PerDevice **out)
+{
+    static thread_local HostCallState st;
+    if (d < 0 || d >= 64)
+        return fail(BNZ_ENODEV, "device ordinal %d out of range", d);
+    HostCallState::PerDevice &v = st.dev[d];
+    cudaError_t e = cudaSuccess;
+    if (!v.stream && (e = cudaStreamCreateWithFlags(&v.stream, cudaStreamNonBlocking)) != cudaSuccess) {
+        v.stream = nullptr;
+        return cuda_fail(e, "cudaStreamCreate");
+    }
+    if (!v.stats && (e = cudaMalloc(&v.stats, 4 * sizeof(unsigned long long))) != cudaSuccess) {
+        v.stats = nullptr;
+        return cuda_fail(e, "cudaMalloc(statistics)");
+    }
+    if (!v.h_stats && (e = cudaMallocHost(&v.h_stats, 4 * sizeof(unsigned long long))) != cudaSuccess) {
+        v.h_stats = nullptr;
+        return cuda_fail(e, "cudaMallocHost(statistics)");
+    }
+    int rc = grow(&v.src, &v.src_cap, src_bytes, "cudaMalloc(page)");
+    if (rc == BNZ_OK)
+        rc = grow(&v.dst, &v.dst_cap, dst_bytes, "cudaMalloc(mask)");
+    if (rc != BNZ_OK)
+        return rc;
+    *out = &v;
+    return BNZ_OK;
+}
+
 static int binarize_host(const uint8_t *src, int height, int width, int channels, int W, int rule, double k,
                          double R, uint8_t *dst)
 {
@@ -189,60 +263,50 @@ static int binarize_host(const uint8_t *src, int height, int width, int channels
     rc = current_device(&dev);
     if (rc != BNZ_OK)
         return rc;
-    unsigned int *err = nullptr;
-    rc = device_err_flag(&err);
-    if (rc != BNZ_OK)
-        return rc;
-    cudaStream_t s = nullptr;
-    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
-    if (e != cudaSuccess)
-        return cuda_fail(e, "cudaStreamCreate");
     const size_t sp = ((size_t)width * channels + 15) & ~size_t(15);
     const size_t dp = ((size_t)width + 15) & ~size_t(15);
-    void *d_src = nullptr, *d_dst = nullptr;
-    unsigned int before = 0, after = 0;
-    rc = BNZ_OK;
+    HostCallState::PerDevice *v = nullptr;
+    rc = host_call_state(dev, sp * height, dp * height, &v);
+    if (rc != BNZ_OK)
+        return rc;
+    cudaStream_t s = v->stream;
+    cudaError_t e;
     do {
-        if ((e = cudaMemcpyAsync(&before, err, sizeof before, cudaMemcpyDeviceToHost, s)) != cudaSuccess) {
-            rc = cuda_fail(e, "read error word");
+        if ((e = cudaMemsetAsync(v->stats, 0, 4 * sizeof(unsigned long long), s)) != cudaSuccess) {
+            rc = cuda_fail(e, "clear statistics");
             break;
         }
-        if ((e = cudaMallocAsync(&d_src, sp * height, s)) != cudaSuccess) {
-            rc = cuda_fail(e, "cudaMallocAsync(src)");
-            break;
-        }
-        if ((e = cudaMallocAsync(&d_dst, dp * height, s)) != cudaSuccess) {
-            rc = cuda_fail(e, "cudaMallocAsync(dst)");
-            break;
-        }
-        if ((e = cudaMemcpy2DAsync(d_src, sp, src, (size_t)width * channels, (size_t)width * channels, height,
-                                   cudaMemcpyHostToDevice, s)) != cudaSuccess) {
+        // rows already 16-byte multiples: one contiguous copy (the copy engines run
+        // large linear copies faster than row-by-row 2-D ones)
+        e = sp == (size_t)width * channels
+                ? cudaMemcpyAsync(v->src, src, sp * height, cudaMemcpyHostToDevice, s)
+                : cudaMemcpy2DAsync(v->src, sp, src, (size_t)width * channels, (size_t)width * channels, height,
+                                    cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) {
             rc = cuda_fail(e, "copy input to device");
             break;
         }
-        rc = binarize_dev(static_cast<const uint8_t *>(d_src), sp, height, width, channels, W, rule, k, R,
-                          static_cast<uint8_t *>(d_dst), dp, 0, nullptr, s, nullptr);
+        rc = binarize_dev(static_cast<const uint8_t *>(v->src), sp, height, width, channels, W, rule, k, R,
+                          static_cast<uint8_t *>(v->dst), dp, 0, nullptr, s, v->stats);
         if (rc != BNZ_OK)
             break;
-        if ((e = cudaMemcpy2DAsync(dst, (size_t)width, d_dst, dp, (size_t)width, height, cudaMemcpyDeviceToHost,
-                                   s)) != cudaSuccess) {
+        e = dp == (size_t)width
+                ? cudaMemcpyAsync(dst, v->dst, dp * height, cudaMemcpyDeviceToHost, s)
+                : cudaMemcpy2DAsync(dst, (size_t)width, v->dst, dp, (size_t)width, height, cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) {
             rc = cuda_fail(e, "copy result to host");
             break;
         }
-        if ((e = cudaMemcpyAsync(&after, err, sizeof after, cudaMemcpyDeviceToHost, s)) != cudaSuccess) {
-            rc = cuda_fail(e, "read error word");
+        if ((e = cudaMemcpyAsync(v->h_stats, v->stats, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                 s)) != cudaSuccess) {
+            rc = cuda_fail(e, "read statistics");
             break;
         }
     } while (0);
-    if (d_src)
-        cudaFreeAsync(d_src, s);
-    if (d_dst)
-        cudaFreeAsync(d_dst, s);
     e = cudaStreamSynchronize(s);
     if (rc == BNZ_OK && e != cudaSuccess)
         rc = cuda_fail(e, "cudaStreamSynchronize");
-    cudaStreamDestroy(s);
-    if (rc == BNZ_OK && after != before)
+    if (rc == BNZ_OK && v->h_stats[BNZ_STATS_TIMEOUTS] != 0)
         rc = fail(BNZ_ETIMEOUT, "a device-side wait timed out; output incomplete");
     return rc;
 }

@@ -241,13 +241,11 @@ static int plan_batch(const bnz_page *pages, int n, unsigned long long *d_stats,
         }
         const void *fn = g.ch == 1 ? reinterpret_cast<const void *>(&batch_kernel<1>)
                                    : reinterpret_cast<const void *>(&batch_kernel<3>);
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
-        int occ = 1;
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, NT, g.smem);
-        if (e != cudaSuccess) {
+        const int occ = 1; // 512 threads x up to 128 registers: one CTA per SM
+        rc = ensure_smem_optin(fn);
+        if (rc != BNZ_OK) {
             free_batch(b);
-            return cuda_fail(e, "batch set-up");
+            return rc;
         }
         g.grid = (int)std::max<long long>(1, std::min<long long>((long long)sms * std::max(occ, 1), g.total / 32 + 1));
     }

@@ -35,6 +35,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <mutex>
+#include <set>
+#include <utility>
 
 #include "segment.cuh"
 
@@ -212,6 +215,27 @@ int plan_shape(int h, int w, int ch, int W, int want_tw, FusedPlan *pl)
     return BNZ_OK;
 }
 
+// The opt-in to the largest dynamic shared memory any plan uses, once per
+// device and kernel (a per-launch cudaFuncSetAttribute costs microseconds).
+int ensure_smem_optin(const void *fn)
+{
+    static std::mutex mu;
+    static std::set<std::pair<int, const void *>> done;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    {
+        std::lock_guard<std::mutex> g(mu);
+        if (done.count({dev, fn}))
+            return BNZ_OK;
+    }
+    const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaFuncSetAttribute(dynamic shared memory)");
+    std::lock_guard<std::mutex> g(mu);
+    done.insert({dev, fn});
+    return BNZ_OK;
+}
+
 int plan_fused(int h, int w, int ch, int W, const bnz_tile *tile, FusedPlan *pl)
 {
     int sms = 0;
@@ -223,15 +247,8 @@ int plan_fused(int h, int w, int ch, int W, const bnz_tile *tile, FusedPlan *pl)
     rc = plan_shape(h, w, ch, W, tile ? tile->tile_w : 0, pl);
     if (rc != BNZ_OK)
         return rc;
-    int occ = 1;
-    const void *fn = kernel_for(ch, BNZ_SAUVOLA, W);
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl->smem);
-    if (e != cudaSuccess)
-        return cuda_fail(e, "cudaFuncSetAttribute(fused)");
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, NT, pl->smem);
-    if (e != cudaSuccess)
-        return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-    occ = std::max(occ, 1);
+    // one CTA per SM: 512 threads with up to 128 registers each take the whole register file
+    const int occ = 1;
     // persistent grid: one CTA per resident slot, but at least ~2W rows of work per CTA
     const long long T = (long long)pl->tiles_x * h;
     const long long min_rows = std::max(2 * W, 32);
@@ -285,11 +302,11 @@ int launch_fused(const uint8_t *d_src, size_t src_pitch, int h, int w, int ch, i
     FusedParams p;
     fill_fused_params(&p, pl, h, w, W, rule, k, R, d_dst, dst_pitch, packed, d_stats, d_err);
     const void *fn = kernel_for(ch, rule, W);
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
-    if (e != cudaSuccess)
-        return cuda_fail(e, "cudaFuncSetAttribute(fused)");
+    rc = ensure_smem_optin(fn);
+    if (rc != BNZ_OK)
+        return rc;
     void *args[] = {(void *)&map, (void *)&p};
-    e = cudaLaunchKernel(fn, dim3((unsigned)pl.grid), dim3(NT), args, pl.smem, stream);
+    cudaError_t e = cudaLaunchKernel(fn, dim3((unsigned)pl.grid), dim3(NT), args, pl.smem, stream);
     if (e != cudaSuccess)
         return cuda_fail(e, "launch fused kernel");
     return BNZ_OK;

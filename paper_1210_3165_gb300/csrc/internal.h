@@ -77,6 +77,8 @@ void fill_fused_params(FusedParams *p, const FusedPlan &pl, int h, int w, int W,
                        uint8_t *d_dst, size_t dst_pitch, int packed, unsigned long long *d_stats,
                        unsigned int *d_err);
 constexpr int kMaxBarriers = 96; // mbarriers reserved at the start of shared memory: full + empty per slot
+// Raise the kernel's dynamic shared-memory limit to the largest plan, once per device.
+int ensure_smem_optin(const void *fn);
 int launch_fused(const uint8_t *d_src, size_t src_pitch, int h, int w, int ch, int W, int rule, double k,
                  double R, uint8_t *d_dst, size_t dst_pitch, int packed, const bnz_tile *tile,
                  cudaStream_t stream, unsigned long long *d_stats, unsigned int *d_err);

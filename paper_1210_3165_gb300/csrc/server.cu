@@ -159,8 +159,11 @@ bool admit(bnz_server *s)
         } else {
             q->d_src = base;
             const size_t row = (size_t)q->r.width * q->r.channels;
-            const cudaError_t e = cudaMemcpy2DAsync(base, q->sp, q->r.src, q->r.src_pitch, row, q->r.height,
-                                                    cudaMemcpyHostToDevice, s->cin);
+            const cudaError_t e =
+                (q->sp == row && q->r.src_pitch == row) // one linear copy when both sides are dense
+                    ? cudaMemcpyAsync(base, q->r.src, row * q->r.height, cudaMemcpyHostToDevice, s->cin)
+                    : cudaMemcpy2DAsync(base, q->sp, q->r.src, q->r.src_pitch, row, q->r.height,
+                                        cudaMemcpyHostToDevice, s->cin);
             if (e != cudaSuccess) {
                 set_error(s, std::string("input copy: ") + cudaGetErrorString(e));
                 finish(s, q, BNZ_ECUDA);
@@ -273,8 +276,11 @@ bool collect_steps(bnz_server *s)
                 continue;
             }
             const size_t row = q->r.packed ? ((size_t)q->r.width + 7) / 8 : (size_t)q->r.width;
-            const cudaError_t c = cudaMemcpy2DAsync(q->r.dst, q->r.dst_pitch, q->d_dst, q->dp, row, q->r.height,
-                                                    cudaMemcpyDeviceToHost, s->cout);
+            const cudaError_t c =
+                (q->dp == row && q->r.dst_pitch == row)
+                    ? cudaMemcpyAsync(q->r.dst, q->d_dst, row * q->r.height, cudaMemcpyDeviceToHost, s->cout)
+                    : cudaMemcpy2DAsync(q->r.dst, q->r.dst_pitch, q->d_dst, q->dp, row, q->r.height,
+                                        cudaMemcpyDeviceToHost, s->cout);
             if (c != cudaSuccess) {
                 set_error(s, std::string("mask copy: ") + cudaGetErrorString(c));
                 finish(s, q, BNZ_ECUDA);
