@@ -134,16 +134,18 @@ def host_page():
     return _PAGE["p"]
 
 
-def cpu_oracle_sample(rows: int, threads: int):
-    """Time the oracle's sliding-window path on a rows x 4096 crop of the page, all 8 runs."""
+def cpu_oracle_sample(rows: int, threads: int, method: int | None = None, cols: int | None = None, runs=None):
+    """Time the oracle (sliding-window path by default) on a rows x cols crop of the page over `runs`."""
     import oracle
-    img = host_page()[:rows].copy()
+    cols = cols or W_IMG
+    runs = runs or RUNS
+    img = host_page()[:rows, :cols].copy()
     t0 = time.perf_counter()
-    for W, rule, k, R in RUNS:
+    for W, rule, k, R in runs:
         oracle.binarize(img, W, oracle.SAUVOLA if rule == "sauvola" else oracle.NIBLACK, k, R,
-                        method=oracle.SLIDING, threads=threads)
+                        method=oracle.SLIDING if method is None else method, threads=threads)
     dt = time.perf_counter() - t0
-    return rows * W_IMG * len(RUNS) / dt / 1e6, dt
+    return rows * cols * len(runs) / dt / 1e6, dt
 
 
 def run_reference(args):
@@ -270,10 +272,16 @@ def run_ours(args):
     if rank == 0 and not args.no_e2e:
         result["e2e"] = e2e_host_api(bnz, page, min(args.steps, 3))
     if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle
         threads = os.cpu_count() or 1
-        v, dt = cpu_oracle_sample(1024, threads)
+        v, dt = cpu_oracle_sample(H, threads)
+        v1, dt1 = cpu_oracle_sample(256, 1)
+        vn, dtn = cpu_oracle_sample(512, threads, method=oracle.NAIVE, cols=512, runs=[RUNS[0], RUNS[3]])
         result["cpu_baseline"] = {"value": v, "unit": "Mpixel/s", "cores": threads, "kind": "oracle",
-                                  "sample": f"1024x4096 crop of the page, all 8 runs, {dt:.1f} s wall"}
+                                  "sample": f"the whole page, all 8 runs, sliding-window path, {dt:.1f} s wall",
+                                  "single_thread": {"value": v1, "sample": f"256-row crop, all 8 runs, {dt1:.1f} s"},
+                                  "naive_all_cores": {"value": vn, "sample": f"512x512 crop, Sauvola W=15 and W=101, "
+                                                                             f"O(W^2) per pixel, {dtn:.1f} s"}}
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
