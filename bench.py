@@ -42,6 +42,22 @@ def env_rank():
         int(os.environ.get("LOCAL_RANK", 0))
 
 
+def max_over_ranks(ms, world, device):
+    """The slowest rank's time: every replica processed the same pixels, the job ends with the last one."""
+    if world <= 1:
+        return float(ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, steps, px_step, total_ms):
+    """Whole-job throughput in Mpixel/s: pixels processed by all replicas over the slowest rank's time."""
+    return world * steps * px_step / (total_ms / 1e3) / 1e6
+
+
 def measured_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -235,13 +251,10 @@ def run_ours(args):
         for j in range(len(RUNS)):
             nxt = evs[s][j + 1] if j + 1 < len(RUNS) else (evs[s + 1][0] if s + 1 < args.steps else end)
             per_launch[j].append(evs[s][j].elapsed_time(nxt))
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, world, dev)
 
     px_step = H * W_IMG * len(RUNS)
-    value = world * args.steps * px_step / (total_ms / 1e3) / 1e6
+    value = job_value(world, args.steps, px_step, total_ms)
     peak, peak_kind = measured_peak()
     bytes_launch = H * W_IMG * BYTES_PER_PX
     avg_launch_ms = statistics.mean(sum(v) / len(v) for v in per_launch.values())
