@@ -58,6 +58,14 @@ def job_value(world, steps, px_step, total_ms):
     return world * steps * px_step / (total_ms / 1e3) / 1e6
 
 
+def gpu_uuid(dev):
+    try:
+        import torch
+        return str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        return None
+
+
 def measured_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -86,18 +94,74 @@ def ncu_traffic():
     return None
 
 
+class _Nvml:
+    """Read-only NVML queries through the driver's libnvidia-ml (clocks and clock-event reasons)."""
+    SM = 1  # NVML_CLOCK_SM
+    # nvmlClocksEventReason* bits
+    BITS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40}
+
+    def __init__(self, uuid, index):
+        import ctypes
+        self.c = ctypes
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        self.lib = lib
+        self.h = ctypes.c_void_p()
+        rc = -1
+        if uuid:
+            rc = lib.nvmlDeviceGetHandleByUUID(("GPU-" + uuid).encode(), ctypes.byref(self.h))
+        if rc != 0:
+            rc = lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(self.h))
+        if rc != 0:
+            raise RuntimeError("no NVML handle")
+        self.reasons_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        v = ctypes.c_uint()
+        if lib.nvmlDeviceGetMaxClockInfo(self.h, self.SM, ctypes.byref(v)) != 0:
+            raise RuntimeError("no max clock")
+        self.max_mhz = float(v.value)
+
+    def sample(self):
+        c = self.c
+        v, r = c.c_uint(), c.c_ulonglong()
+        if self.lib.nvmlDeviceGetClockInfo(self.h, self.SM, c.byref(v)) != 0:
+            return None
+        reasons = set()
+        if self.reasons_fn(self.h, c.byref(r)) == 0:
+            reasons = {nm for nm, bit in self.BITS.items() if r.value & bit}
+        return float(v.value), reasons
+
+
 class ClockSampler:
-    """nvidia-smi clocks/throttle reasons sampled every 200 ms while the timed region runs."""
+    """SM clock and throttle reasons while the timed region runs: NVML polled every 5 ms (the region can
+    be tens of milliseconds), else nvidia-smi every 200 ms."""
     Q = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active," \
         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown," \
         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, uuid: str | None = None):
         self.gpu = gpu_index
+        self.uuid = uuid
         self.lines = []
+        self.samples = []
         self.proc = None
+        self.nvml = None
+        self.stop_evt = threading.Event()
 
     def start(self):
+        try:
+            self.nvml = _Nvml(self.uuid, self.gpu)
+        except Exception:
+            self.nvml = None
+        if self.nvml is not None:
+            first = self.nvml.sample()  # one sample before the region starts, so polling is known to work
+            if first is not None:
+                self.samples.append(first)
+                self.t = threading.Thread(target=self._poll, daemon=True)
+                self.t.start()
+                return
+            self.nvml = None
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
@@ -107,11 +171,27 @@ class ClockSampler:
         except Exception:
             self.proc = None
 
+    def _poll(self):
+        while not self.stop_evt.wait(0.005):
+            s = self.nvml.sample()
+            if s is not None:
+                self.samples.append(s)
+
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
     def stop(self):
+        if self.nvml is not None:
+            s = self.nvml.sample()  # and one as the region ends
+            self.stop_evt.set()
+            self.t.join(timeout=5)
+            if s is not None:
+                self.samples.append(s)
+            sm = [x[0] for x in self.samples]
+            reasons = set().union(*(x[1] for x in self.samples))
+            return {"sm_mhz": statistics.median(sm), "sm_max_mhz": self.nvml.max_mhz, "reasons": sorted(reasons),
+                    "samples": len(sm), "source": "nvml, 5 ms"}
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -137,7 +217,7 @@ class ClockSampler:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "source": "nvidia-smi, 200 ms"}
 
 
 _PAGE = {}
@@ -234,7 +314,7 @@ def run_ours(args):
     # timed region: K steps, an event before every launch and one at the end
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(RUNS))] for _ in range(args.steps)]
     end = torch.cuda.Event(enable_timing=True)
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(local, gpu_uuid(dev))
     clocks.start()
     with torch.cuda.stream(stream):
         for s in range(args.steps):
@@ -356,21 +436,26 @@ def run_batch(args):
     batch = bnz.Batch(pages, use_graph=True)
     stream = torch.cuda.Stream()
 
-    def timed(fn, steps, warmup):
+    def timed(fn, steps, warmup, clocks=None):
         with torch.cuda.stream(stream):
             for _ in range(warmup):
                 fn()
         stream.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if clocks is not None:
+            clocks.start()
         with torch.cuda.stream(stream):
             a.record(stream)
             for _ in range(steps):
                 fn()
             b.record(stream)
         stream.synchronize()
+        if clocks is not None:
+            clocks.result = clocks.stop()
         return a.elapsed_time(b) / steps
 
-    ms_batch = timed(lambda: batch.run(stream), args.steps, max(args.warmup, 3))
+    clocks = ClockSampler(torch.cuda.current_device(), gpu_uuid(torch.cuda.current_device()))
+    ms_batch = timed(lambda: batch.run(stream), args.steps, max(args.warmup, 3), clocks)
 
     def per_page():
         for pg in pages:
@@ -390,7 +475,8 @@ def run_batch(args):
         "speedup_vs_per_page": ms_pages / ms_batch,
         "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(gbs / peak, 4), "traffic": None, "peak_kind": peak_kind},
-        "tiles": table.get("1"), "batch_info": batch.info(),
+        "tiles": table.get("1"), "batch_info": batch.info(), "gpu_launches": args.steps,
+        "clocks": getattr(clocks, "result", None),
     }))
     batch.close()
     return 0
