@@ -92,8 +92,12 @@ typedef struct {
 
 /* src: height rows of width*channels bytes, tightly packed, host memory.
  * dst: height*width bytes, {0,255}, host memory.  Blocks until done.
- * k: any finite value; R > 0 (the paper's "dynamic range of standard
- * deviation", Sec. 1 after Eq. 4). */
+ * k: any finite value; R > 0 (the dynamic range of the standard deviation,
+ * Sec. 1 after Eq. 4).
+ * Page-locked host buffers copy fastest.  Pages of a megapixel or more are
+ * processed in up to 4 row bands whose uploads, kernels and downloads overlap
+ * on the calling thread's library streams; the result is the same as in one
+ * piece.  Thread-safe: every calling thread has its own streams and buffers. */
 BNZ_API int bnz_sauvola(const uint8_t *src, int height, int width, int channels, int W, double k, double R,
                 uint8_t *dst);
 

@@ -1,6 +1,7 @@
 // api.cu -- the C ABI declared in include/bnz.h: argument checks, error
 // messages, TMA descriptor encoding, device bookkeeping and the synchronous
 // host-pointer calls.  All pixel work happens in the CUDA kernels.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -159,7 +160,8 @@ int check_common(const void *src, size_t src_pitch, int height, int width, int c
 
 static int binarize_dev(const uint8_t *d_src, size_t src_pitch, int height, int width, int channels, int W,
                         int rule, double k, double R, uint8_t *d_dst, size_t dst_pitch, int packed,
-                        const bnz_tile *tile, void *stream, unsigned long long *d_stats)
+                        const bnz_tile *tile, void *stream, unsigned long long *d_stats, int y_lo = 0,
+                        int y_hi = -1)
 {
     int rc = check_common(d_src, src_pitch, height, width, channels, W, rule, k, R, d_dst, dst_pitch, packed);
     if (rc != BNZ_OK)
@@ -173,19 +175,26 @@ static int binarize_dev(const uint8_t *d_src, size_t src_pitch, int height, int 
     if (rc != BNZ_OK)
         return rc;
     return launch_fused(d_src, src_pitch, height, width, channels, W, rule, k, R, d_dst, dst_pitch, packed ? 1 : 0,
-                        tile, static_cast<cudaStream_t>(stream), d_stats, err);
+                        tile, static_cast<cudaStream_t>(stream), d_stats, err, y_lo, y_hi);
 }
 
 // Synchronous host-pointer path: stream-ordered device buffers, copies in and
-// out, one launch, then a check of the device error word.
+// out overlapped with the launches band by band, then a check of the
+// statistics' timeout count.
 // Per-thread, per-device resources of the synchronous host API, made once: a
 // stream, grow-only device buffers for the page and its mask, and statistics
 // counters with a pinned host copy.  Creating a stream, allocating and freeing
 // tens of MB (the default pool returns freed memory at each synchronize), or a
 // blocking read of the error word, per call would cost more than the kernel.
+// A page is cut into up to kMaxBands row bands, so that the upload of band
+// i + 1, the kernel on band i and the download of band i - 1 overlap (the
+// host link, not the kernel, bounds this path).
+constexpr int kMaxBands = 4;
+
 struct HostCallState {
     struct PerDevice {
-        cudaStream_t stream = nullptr;
+        cudaStream_t stream = nullptr, up = nullptr, down = nullptr;
+        cudaEvent_t ev_up[kMaxBands] = {}, ev_k[kMaxBands] = {};
         unsigned long long *stats = nullptr, *h_stats = nullptr;
         void *src = nullptr, *dst = nullptr;
         size_t src_cap = 0, dst_cap = 0;
@@ -198,6 +207,16 @@ struct HostCallState {
             if (!v.stream && !v.stats && !v.src && !v.dst && !v.h_stats)
                 continue;
             cudaSetDevice(d);
+            for (int i = 0; i < kMaxBands; ++i) {
+                if (v.ev_up[i])
+                    cudaEventDestroy(v.ev_up[i]);
+                if (v.ev_k[i])
+                    cudaEventDestroy(v.ev_k[i]);
+            }
+            if (v.up)
+                cudaStreamDestroy(v.up);
+            if (v.down)
+                cudaStreamDestroy(v.down);
             if (v.stream)
                 cudaStreamDestroy(v.stream);
             cudaFree(v.stats);
@@ -231,10 +250,17 @@ static int host_call_state(int d, size_t src_bytes, size_t dst_bytes, HostCallSt
         return fail(BNZ_ENODEV, "device ordinal %d out of range", d);
     HostCallState::PerDevice &v = st.dev[d];
     cudaError_t e = cudaSuccess;
-    if (!v.stream && (e = cudaStreamCreateWithFlags(&v.stream, cudaStreamNonBlocking)) != cudaSuccess) {
-        v.stream = nullptr;
-        return cuda_fail(e, "cudaStreamCreate");
-    }
+    for (cudaStream_t *ps : {&v.stream, &v.up, &v.down})
+        if (!*ps && (e = cudaStreamCreateWithFlags(ps, cudaStreamNonBlocking)) != cudaSuccess) {
+            *ps = nullptr;
+            return cuda_fail(e, "cudaStreamCreate");
+        }
+    for (int i = 0; i < kMaxBands; ++i)
+        for (cudaEvent_t *pe : {&v.ev_up[i], &v.ev_k[i]})
+            if (!*pe && (e = cudaEventCreateWithFlags(pe, cudaEventDisableTiming)) != cudaSuccess) {
+                *pe = nullptr;
+                return cuda_fail(e, "cudaEventCreate");
+            }
     if (!v.stats && (e = cudaMalloc(&v.stats, 4 * sizeof(unsigned long long))) != cudaSuccess) {
         v.stats = nullptr;
         return cuda_fail(e, "cudaMalloc(statistics)");
@@ -252,6 +278,41 @@ static int host_call_state(int d, size_t src_bytes, size_t dst_bytes, HostCallSt
     return BNZ_OK;
 }
 
+// Row bands for a page of h rows, halving towards the end: band i starts at
+// row h - (h >> i) and the last one holds the final h >> (nb - 1) rows.  The
+// early, large bands' kernels and downloads run under the rest of the upload;
+// after the upload only the small last band's kernel and download remain.  The
+// smallest band has at least max(128, 2W) rows (each band's CTAs first sum
+// the W rows of their window), and pages under a megapixel stay in one piece
+// (a launch and two events per band cost more than such a page's copies).
+static int host_bands(int height, int width, int W)
+{
+    if ((long long)height * width < (1ll << 20))
+        return 1;
+    const int min_rows = std::max(128, 2 * W);
+    int nb = 1;
+    while (nb < kMaxBands && (height >> nb) >= min_rows)
+        ++nb;
+    return nb;
+}
+
+static int band_start(int height, int i) { return height - (height >> i); }
+
+// Copies rows [y0, y1) of a page between host (tightly packed rows of `row`
+// bytes) and device (rows `pitch` apart).
+static cudaError_t copy_rows(void *dst_base, size_t dst_pitch, const void *src_base, size_t src_pitch, size_t row,
+                             int y0, int y1, cudaMemcpyKind kind, cudaStream_t s)
+{
+    char *d = static_cast<char *>(dst_base) + (size_t)y0 * dst_pitch;
+    const char *sp = static_cast<const char *>(src_base) + (size_t)y0 * src_pitch;
+    const size_t n = (size_t)(y1 - y0);
+    // rows already 16-byte multiples: one contiguous copy (the copy engines run
+    // large linear copies faster than row-by-row 2-D ones)
+    if (dst_pitch == row && src_pitch == row)
+        return cudaMemcpyAsync(d, sp, row * n, kind, s);
+    return cudaMemcpy2DAsync(d, dst_pitch, sp, src_pitch, row, n, kind, s);
+}
+
 static int binarize_host(const uint8_t *src, int height, int width, int channels, int W, int rule, double k,
                          double R, uint8_t *dst)
 {
@@ -263,49 +324,88 @@ static int binarize_host(const uint8_t *src, int height, int width, int channels
     rc = current_device(&dev);
     if (rc != BNZ_OK)
         return rc;
-    const size_t sp = ((size_t)width * channels + 15) & ~size_t(15);
+    int sms = 0;
+    rc = device_sm_count(&sms);
+    if (rc != BNZ_OK)
+        return rc;
+    const size_t row_in = (size_t)width * channels;
+    const size_t sp = (row_in + 15) & ~size_t(15);
     const size_t dp = ((size_t)width + 15) & ~size_t(15);
     HostCallState::PerDevice *v = nullptr;
     rc = host_call_state(dev, sp * height, dp * height, &v);
     if (rc != BNZ_OK)
         return rc;
     cudaStream_t s = v->stream;
+    const int nb = host_bands(height, width, W);
+    const int r_hi = W - 1 - W / 2;
+    long long strips = 1;
+    if (nb > 1) {
+        FusedPlan shape;
+        if ((rc = plan_shape(height, width, channels, W, 0, &shape)) != BNZ_OK)
+            return rc;
+        strips = shape.tiles_x;
+    }
     cudaError_t e;
     do {
         if ((e = cudaMemsetAsync(v->stats, 0, 4 * sizeof(unsigned long long), s)) != cudaSuccess) {
             rc = cuda_fail(e, "clear statistics");
             break;
         }
-        // rows already 16-byte multiples: one contiguous copy (the copy engines run
-        // large linear copies faster than row-by-row 2-D ones)
-        e = sp == (size_t)width * channels
-                ? cudaMemcpyAsync(v->src, src, sp * height, cudaMemcpyHostToDevice, s)
-                : cudaMemcpy2DAsync(v->src, sp, src, (size_t)width * channels, (size_t)width * channels, height,
-                                    cudaMemcpyHostToDevice, s);
-        if (e != cudaSuccess) {
-            rc = cuda_fail(e, "copy input to device");
-            break;
+        // the upload runs ahead on its own stream; band i's kernel waits for the
+        // rows its windows reach, its download waits for the kernel
+        int uploaded = 0;
+        for (int i = 0; i < nb && rc == BNZ_OK; ++i) {
+            const int y0 = band_start(height, i), y1 = i + 1 < nb ? band_start(height, i + 1) : height;
+            const int need = std::min(height, y1 + r_hi);
+            if (need > uploaded) {
+                e = copy_rows(v->src, sp, src, row_in, row_in, uploaded, need, cudaMemcpyHostToDevice,
+                              nb > 1 ? v->up : s);
+                if (e != cudaSuccess) {
+                    rc = cuda_fail(e, "copy input to device");
+                    break;
+                }
+                uploaded = need;
+            }
+            if (nb > 1 && ((e = cudaEventRecord(v->ev_up[i], v->up)) != cudaSuccess ||
+                           (e = cudaStreamWaitEvent(s, v->ev_up[i], 0)) != cudaSuccess)) {
+                rc = cuda_fail(e, "order band upload");
+                break;
+            }
+            // every SM on each band: its rows are few, the upload bounds the call
+            bnz_tile tile = {0, 0, 0, 0};
+            if (nb > 1)
+                tile.tile_h = (int)std::max<long long>(8, (strips * (y1 - y0) + sms - 1) / sms);
+            rc = binarize_dev(static_cast<const uint8_t *>(v->src), sp, height, width, channels, W, rule, k, R,
+                              static_cast<uint8_t *>(v->dst), dp, 0, nb > 1 ? &tile : nullptr, s, v->stats, y0, y1);
+            if (rc != BNZ_OK)
+                break;
+            if (nb > 1 && ((e = cudaEventRecord(v->ev_k[i], s)) != cudaSuccess ||
+                           (e = cudaStreamWaitEvent(v->down, v->ev_k[i], 0)) != cudaSuccess)) {
+                rc = cuda_fail(e, "order band download");
+                break;
+            }
+            e = copy_rows(dst, (size_t)width, v->dst, dp, (size_t)width, y0, y1, cudaMemcpyDeviceToHost,
+                          nb > 1 ? v->down : s);
+            if (e != cudaSuccess) {
+                rc = cuda_fail(e, "copy result to host");
+                break;
+            }
         }
-        rc = binarize_dev(static_cast<const uint8_t *>(v->src), sp, height, width, channels, W, rule, k, R,
-                          static_cast<uint8_t *>(v->dst), dp, 0, nullptr, s, v->stats);
         if (rc != BNZ_OK)
             break;
-        e = dp == (size_t)width
-                ? cudaMemcpyAsync(dst, v->dst, dp * height, cudaMemcpyDeviceToHost, s)
-                : cudaMemcpy2DAsync(dst, (size_t)width, v->dst, dp, (size_t)width, height, cudaMemcpyDeviceToHost, s);
-        if (e != cudaSuccess) {
-            rc = cuda_fail(e, "copy result to host");
-            break;
-        }
+        // the download stream has waited for the last kernel
         if ((e = cudaMemcpyAsync(v->h_stats, v->stats, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
-                                 s)) != cudaSuccess) {
+                                 nb > 1 ? v->down : s)) != cudaSuccess) {
             rc = cuda_fail(e, "read statistics");
             break;
         }
     } while (0);
-    e = cudaStreamSynchronize(s);
-    if (rc == BNZ_OK && e != cudaSuccess)
-        rc = cuda_fail(e, "cudaStreamSynchronize");
+    // all three streams, also after an error, so no copy outlives the call
+    for (cudaStream_t q : {v->up, s, v->down}) {
+        e = cudaStreamSynchronize(q);
+        if (rc == BNZ_OK && e != cudaSuccess)
+            rc = cuda_fail(e, "cudaStreamSynchronize");
+    }
     if (rc == BNZ_OK && v->h_stats[BNZ_STATS_TIMEOUTS] != 0)
         rc = fail(BNZ_ETIMEOUT, "a device-side wait timed out; output incomplete");
     return rc;

@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(NT, 1)
     uint64_t phase = 0;             // bit i: parity of the next completion of full barrier i
     uint64_t ephase = 0, eused = 0; // TMA issuer: free-signal parity, slots ever loaded
     uint32_t nfb = 0, nties = 0;
-    const long long T = (long long)p.tiles_x * p.h;
+    const long long T = (long long)p.tiles_x * (p.y_hi - p.y_lo);
     const long long L0 = T * blockIdx.x / gridDim.x, L1 = T * (blockIdx.x + 1) / gridDim.x;
     for (long long cur = L0; cur < L1;) {
         const Segment sg = make_segment(p, cur, L1);
@@ -170,6 +170,8 @@ void fill_decision_params(FusedParams *p, int h, int w, int W, int rule, double 
 {
     *p = FusedParams{};
     p->h = h;
+    p->y_lo = 0;
+    p->y_hi = h;
     p->w = w;
     p->W = W;
     p->r_lo = W / 2;
@@ -236,8 +238,10 @@ int ensure_smem_optin(const void *fn)
     return BNZ_OK;
 }
 
-int plan_fused(int h, int w, int ch, int W, const bnz_tile *tile, FusedPlan *pl)
+int plan_fused(int h, int w, int ch, int W, const bnz_tile *tile, FusedPlan *pl, int rows)
 {
+    if (rows < 0)
+        rows = h;
     int sms = 0;
     int rc = device_sm_count(&sms);
     if (rc != BNZ_OK)
@@ -250,7 +254,7 @@ int plan_fused(int h, int w, int ch, int W, const bnz_tile *tile, FusedPlan *pl)
     // one CTA per SM: 512 threads with up to 128 registers each take the whole register file
     const int occ = 1;
     // persistent grid: one CTA per resident slot, but at least ~2W rows of work per CTA
-    const long long T = (long long)pl->tiles_x * h;
+    const long long T = (long long)pl->tiles_x * rows;
     const long long min_rows = std::max(2 * W, 32);
     long long G = std::min<long long>((long long)sms * occ, (T + min_rows - 1) / min_rows);
     if (tile && tile->tile_h > 0)
@@ -288,10 +292,14 @@ void fill_fused_params(FusedParams *p, const FusedPlan &pl, int h, int w, int W,
 
 int launch_fused(const uint8_t *d_src, size_t src_pitch, int h, int w, int ch, int W, int rule, double k, double R,
                  uint8_t *d_dst, size_t dst_pitch, int packed, const bnz_tile *tile, cudaStream_t stream,
-                 unsigned long long *d_stats, unsigned int *d_err)
+                 unsigned long long *d_stats, unsigned int *d_err, int y_lo, int y_hi)
 {
+    if (y_hi < 0)
+        y_hi = h;
+    if (y_lo < 0 || y_lo >= y_hi || y_hi > h)
+        return fail(BNZ_EINVAL, "row range [%d, %d) outside [0, %d)", y_lo, y_hi, h);
     FusedPlan pl;
-    int rc = plan_fused(h, w, ch, W, tile, &pl);
+    int rc = plan_fused(h, w, ch, W, tile, &pl, y_hi - y_lo);
     if (rc != BNZ_OK)
         return rc;
     CUtensorMap map;
@@ -301,6 +309,8 @@ int launch_fused(const uint8_t *d_src, size_t src_pitch, int h, int w, int ch, i
         return rc;
     FusedParams p;
     fill_fused_params(&p, pl, h, w, W, rule, k, R, d_dst, dst_pitch, packed, d_stats, d_err);
+    p.y_lo = y_lo;
+    p.y_hi = y_hi;
     const void *fn = kernel_for(ch, rule, W);
     rc = ensure_smem_optin(fn);
     if (rc != BNZ_OK)

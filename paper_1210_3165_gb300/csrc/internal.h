@@ -51,6 +51,7 @@ struct FusedParams {
     unsigned long long *stats;
     unsigned int *err_flag; // library-owned device word, counts CTAs that gave up
     int h, w, W, r_lo, r_hi, o;
+    int y_lo, y_hi;  // output rows [y_lo, y_hi) of this launch (the window clips at 0 and h)
     int TW, CH, NS, NSS, SWP, RSW, ring_rows, tiles_x;
     uint32_t off_ring, off_stage, off_cb;
     int packed;     // 1: one bit per pixel
@@ -72,16 +73,20 @@ struct FusedParams {
 // Shape of the fused kernel for one page (strip width, ring, shared-memory
 // offsets); want_tw = 0 picks the widest strip that fits.
 int plan_shape(int h, int w, int ch, int W, int want_tw, FusedPlan *plan);
-int plan_fused(int h, int w, int ch, int W, const bnz_tile *tile, FusedPlan *plan);
+// rows: output rows of the launch (h for a whole page), which sets the grid.
+int plan_fused(int h, int w, int ch, int W, const bnz_tile *tile, FusedPlan *plan, int rows = -1);
 void fill_fused_params(FusedParams *p, const FusedPlan &pl, int h, int w, int W, int rule, double k, double R,
                        uint8_t *d_dst, size_t dst_pitch, int packed, unsigned long long *d_stats,
                        unsigned int *d_err);
 constexpr int kMaxBarriers = 96; // mbarriers reserved at the start of shared memory: full + empty per slot
 // Raise the kernel's dynamic shared-memory limit to the largest plan, once per device.
 int ensure_smem_optin(const void *fn);
+// Output rows [y_lo, y_hi) of the page (0, h: all); the kernel reads input rows
+// [y_lo - W/2, y_hi + W) at most, the ones past y_hi - 1 + (W - 1 - W/2) unused.
 int launch_fused(const uint8_t *d_src, size_t src_pitch, int h, int w, int ch, int W, int rule, double k,
                  double R, uint8_t *d_dst, size_t dst_pitch, int packed, const bnz_tile *tile,
-                 cudaStream_t stream, unsigned long long *d_stats, unsigned int *d_err);
+                 cudaStream_t stream, unsigned long long *d_stats, unsigned int *d_err, int y_lo = 0,
+                 int y_hi = -1);
 
 // Library-owned per-device error word (allocated on first use).
 int device_err_flag(unsigned int **flag);

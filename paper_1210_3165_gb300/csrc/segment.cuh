@@ -96,14 +96,16 @@ struct Segment {
     int x0, y0, th_eff, xs, ys, nchk, nk;
 };
 
-// The segment starting at strip-row `cur` (strip-major: cur = strip * h + row)
-// of page p, ending no later than strip-row `end`.
+// The segment starting at strip-row `cur` (strip-major over the launch's output
+// rows: cur = strip * (y_hi - y_lo) + row - y_lo) of page p, ending no later
+// than strip-row `end`.
 __device__ __forceinline__ Segment make_segment(const FusedParams &p, long long cur, long long end)
 {
     Segment sg;
-    const int tx = (int)(cur / p.h);
-    sg.y0 = (int)(cur - (long long)tx * p.h);
-    sg.th_eff = (int)min((long long)(p.h - sg.y0), end - cur);
+    const int nr = p.y_hi - p.y_lo;
+    const int tx = (int)(cur / nr);
+    sg.y0 = p.y_lo + (int)(cur - (long long)tx * nr);
+    sg.th_eff = (int)min((long long)(p.y_hi - sg.y0), end - cur);
     sg.x0 = tx * p.TW;
     sg.xs = sg.x0 - p.r_lo - p.o; // span start column (multiple of 16, may be < 0)
     sg.ys = sg.y0 - p.r_lo;       // first input row (may be < 0: zero-filled)

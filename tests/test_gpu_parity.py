@@ -135,6 +135,29 @@ def test_host_pointer_api(bnz):
     np.testing.assert_array_equal(bnz.bnz_niblack(img, 21, -0.2), ref)
 
 
+@pytest.mark.parametrize("h,w,ch,W,rule", [
+    (1030, 1100, 3, 101, "sauvola"),   # bands of 515, 258, 257 rows; windows reach 50 rows past each
+    (1031, 1024, 1, 15, "niblack"),    # 516, 258, 129, 128: odd heights
+    (2050, 700, 1, 61, "sauvola"),     # 1025, 513, 256, 256: narrow page (2 strips)
+    (1300, 1000, 3, 4, "niblack"),     # 650, 325, 163, 162: even window (r_lo = 2, r_hi = 1)
+    (1100, 1000, 1, 255, "sauvola"),   # 550, 550: the largest window, 127 rows past each band
+])
+def test_host_pointer_api_row_bands(bnz, h, w, ch, W, rule):
+    # pages of a megapixel and more go through the host API in row bands, each band's
+    # upload, kernel and download on their own streams
+    img = synth.page(h, w, 17, synth.STAINS if ch == 3 else synth.DOC, ch)
+    if rule == "sauvola":
+        ref, _ = oracle.sauvola(img, W, 0.5, 128.0, threads=NTHREADS)
+        got = bnz.bnz_sauvola(img, W, 0.5, 128.0)
+    else:
+        ref, _ = oracle.niblack(img, W, -0.2, threads=NTHREADS)
+        got = bnz.bnz_niblack(img, W, -0.2)
+    assert not np.any(got != ref), f"{int(np.sum(got != ref))} mismatches"
+    # twice in a row: the second call reuses the buffers, streams and events
+    again = bnz.bnz_sauvola(img, W, 0.5, 128.0) if rule == "sauvola" else bnz.bnz_niblack(img, W, -0.2)
+    np.testing.assert_array_equal(again, ref)
+
+
 def test_unaligned_pitch_rejected(bnz):
     t = torch.zeros((10, 33), dtype=torch.uint8, device="cuda")[:, :30]   # pitch 33
     out = torch.zeros((10, 30), dtype=torch.uint8, device="cuda")
