@@ -56,7 +56,6 @@ struct FusedParams {
     uint32_t off_ring, off_stage, off_cb;
     int packed;     // 1: one bit per pixel
     int vec_ok;     // dst and dst_pitch 16-byte aligned
-    int s1_magic;   // S1 < 2^23 for every window: exact int->float by bit tricks
     uint32_t nW;    // W*W
     double k, R;    // the caller's parameters, for the fp64 re-evaluation
     // fp32 constants of the filter for unclipped windows (n = W*W):

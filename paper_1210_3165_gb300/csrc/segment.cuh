@@ -51,6 +51,14 @@ __device__ __forceinline__ uint32_t byte_dyn(uint32_t w, int j)
     return (w >> (8 * j)) & 0xffu;
 }
 
+// Byte j of w as a float, exactly: one permute forms the bit pattern
+// 0x4B0000bb (= 2^23 + b) and one subtraction removes 2^23, instead of a
+// byte extract and an integer-to-float conversion.
+__device__ __forceinline__ float byte_float(uint32_t w, int j)
+{
+    return __fsub_rn(__uint_as_float(prmt(w, 0x4B000000u, 0x7440u + (uint32_t)j)), 8388608.0f);
+}
+
 // Word offset of 4-column group g in a column-sum row.  The groups are
 // XOR-swizzled within aligned blocks of four, g ^ ((g >> 3) & 3), so that
 // both access patterns hit eight distinct 16-byte bank groups per phase: the
@@ -465,7 +473,7 @@ __device__ __forceinline__ void consume(const FusedParams &p, const Segment &sg,
                         const uint32_t S2 = base2 + d2[t]; // exact: S2 < 2^32
                         const unsigned long long V =
                             (unsigned long long)p.nW * S2 - (unsigned long long)S1 * S1;
-                        const float ff = __uint2float_rn(byte_dyn(fw[qq], e));
+                        const float ff = byte_float(fw[qq], e);
                         dd[e] = filter_int<RULE>(ff, __uint2float_rn(S1), sqrt_approx(v_to_float(V)), p);
                         mn = fminf(mn, fabsf(dd[e]));
                     }
@@ -488,7 +496,7 @@ __device__ __forceinline__ void consume(const FusedParams &p, const Segment &sg,
                         const uint32_t n = (uint32_t)(nr * nc);
                         const uint32_t S1 = base1 + d1[t], S2 = base2 + d2[t];
                         const unsigned long long V = (unsigned long long)n * S2 - (unsigned long long)S1 * S1;
-                        const float ff = __uint2float_rn(byte_dyn(fw[qq], e));
+                        const float ff = byte_float(fw[qq], e);
                         const float invn = rcp_approx(__uint2float_rn(n));
                         dd[e] = filter_n<RULE>(ff, __uint2float_rn(S1), sqrt_approx(v_to_float(V)), invn, p);
                         mn = fminf(mn, xg < p.w ? fabsf(dd[e]) : INFINITY);
@@ -517,7 +525,7 @@ __device__ __forceinline__ void consume(const FusedParams &p, const Segment &sg,
                     const uint32_t n = (uint32_t)(nr * nc);
                     const uint32_t S1 = base1 + e1[t], S2 = base2 + e2[t];
                     const unsigned long long V = (unsigned long long)n * S2 - (unsigned long long)S1 * S1;
-                    const float ff = __uint2float_rn(byte_dyn(fw[t >> 2], t & 3));
+                    const float ff = byte_float(fw[t >> 2], t & 3);
                     const float sq = sqrt_approx(v_to_float(V));
                     const float d = (n == p.nW) ? filter_int<RULE>(ff, __uint2float_rn(S1), sq, p)
                                                 : filter_n<RULE>(ff, __uint2float_rn(S1), sq,
