@@ -76,6 +76,7 @@ typedef enum { BNZ_SAUVOLA = 0, BNZ_NIBLACK = 1 } bnz_rule;
 #define BNZ_STATS_FALLBACKS 0
 #define BNZ_STATS_TIES 1
 #define BNZ_STATS_TIMEOUTS 2
+#define BNZ_STATS_TIES_NIBLACK 3 /* bnz_dual_dev: ties of the Niblack mask (slot 1: the Sauvola mask's) */
 
 /* Optional tile shape for the fused kernel (autotuner hook).  Zero fields
  * mean "library default".  tile_w: output columns per strip, 128, 256 or 512.
@@ -122,6 +123,19 @@ BNZ_API int bnz_sauvola_dev(const uint8_t *d_src, size_t src_pitch, int height, 
 BNZ_API int bnz_niblack_dev(const uint8_t *d_src, size_t src_pitch, int height, int width, int channels, int W,
                     double k, uint8_t *d_dst, size_t dst_pitch, int packed, void *stream,
                     unsigned long long *d_stats);
+
+/* Both rules from one pass over the window sums (Sec. 1: Sauvola, Eq. 4, and
+ * Niblack share m and s; Eq. 3 is then taken once per rule): the page is read
+ * once and S1, S2 are formed once.  d_dst_sauvola and d_dst_niblack receive
+ * exactly what bnz_sauvola_dev(k_sauvola, R) and bnz_niblack_dev(k_niblack)
+ * would write (same layout: dst_pitch, packed).  The two masks must not
+ * overlap (BNZ_EINVAL).  d_stats (nullable, 4 counters): [0] pixels re-decided
+ * past the fp32 filter, both rules; [1] Sauvola ties; [2] timeouts;
+ * [3] Niblack ties.  Other arguments and errors as bnz_sauvola_dev. */
+BNZ_API int bnz_dual_dev(const uint8_t *d_src, size_t src_pitch, int height, int width, int channels, int W,
+                 double k_sauvola, double R, double k_niblack, uint8_t *d_dst_sauvola,
+                 uint8_t *d_dst_niblack, size_t dst_pitch, int packed, void *stream,
+                 unsigned long long *d_stats);
 
 /* Generic form of the two calls above with an explicit rule and optional
  * tile shape (tile may be NULL).  R is ignored for BNZ_NIBLACK. */

@@ -74,13 +74,14 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.bnz_sauvola_dev.argtypes = [P, sz, i, i, i, i, d, d, P, sz, i, P, P]
     lib.bnz_niblack_dev.argtypes = [P, sz, i, i, i, i, d, P, sz, i, P, P]
     lib.bnz_binarize_dev.argtypes = [P, sz, i, i, i, i, i, d, d, P, sz, i, P, P, P]
+    lib.bnz_dual_dev.argtypes = [P, sz, i, i, i, i, d, d, d, P, P, sz, i, P, P]
     lib.bnz_last_error.restype = ctypes.c_char_p
     lib.bnz_last_error.argtypes = []
     lib.bnz_version.argtypes = []
     lib.bnz_fused_plan.argtypes = [i, i, i, i, P, ctypes.POINTER(sz), ctypes.POINTER(i), ctypes.POINTER(i),
                                    ctypes.POINTER(i)]
     for name in ("bnz_sauvola", "bnz_niblack", "bnz_sauvola_dev", "bnz_niblack_dev", "bnz_binarize_dev",
-                 "bnz_version", "bnz_fused_plan"):
+                 "bnz_dual_dev", "bnz_version", "bnz_fused_plan"):
         getattr(lib, name).restype = ctypes.c_int
     _optional_symbols(lib)
     _lib = lib
@@ -247,6 +248,29 @@ def bnz_niblack_dev(d_src, W: int, k: float, d_dst, packed: bool = False, stream
     _check(load().bnz_niblack_dev(ptr, pitch, h, w, ch, int(W), float(k), d_dst.data_ptr(), dp,
                                   1 if packed else 0, _stream_ptr(stream),
                                   d_stats.data_ptr() if d_stats is not None else None))
+
+
+def bnz_dual_dev(d_src, W: int, k_sauvola: float, R: float, k_niblack: float, d_dst_sauvola, d_dst_niblack,
+                 packed: bool = False, stream=None, d_stats=None) -> None:
+    """Both rules from one pass over the window sums: the Sauvola and the Niblack mask of one page."""
+    ptr, pitch, h, w, ch = _dev_img(d_src)
+    dp = _out_pitch(d_dst_sauvola, w, packed)
+    if _out_pitch(d_dst_niblack, w, packed) != dp:
+        raise ValueError("both masks must have the same row pitch")
+    _check(load().bnz_dual_dev(ptr, pitch, h, w, ch, int(W), float(k_sauvola), float(R), float(k_niblack),
+                               d_dst_sauvola.data_ptr(), d_dst_niblack.data_ptr(), dp, 1 if packed else 0,
+                               _stream_ptr(stream), d_stats.data_ptr() if d_stats is not None else None))
+
+
+def binarize_dual(d_src, W: int, k_sauvola: float = 0.5, R: float = 128.0, k_niblack: float = -0.2,
+                  packed: bool = False, stream=None, d_stats=None):
+    """Sauvola and Niblack masks of a pitched uint8 CUDA image from one kernel; returns (sauvola, niblack)."""
+    _, _, h, w, _ = _dev_img(d_src)
+    row = (w + 7) // 8 if packed else w
+    out_s = alloc_pitched(h, row, d_src.device)
+    out_n = alloc_pitched(h, row, d_src.device)
+    bnz_dual_dev(d_src, W, k_sauvola, R, k_niblack, out_s, out_n, packed, stream, d_stats)
+    return out_s, out_n
 
 
 def bnz_copy2d_async(dst: int, dst_pitch: int, src: int, src_pitch: int, width_bytes: int, height: int,

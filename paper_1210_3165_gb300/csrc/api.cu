@@ -278,6 +278,11 @@ static int host_call_state(int d, size_t src_bytes, size_t dst_bytes, HostCallSt
     return BNZ_OK;
 }
 
+// Both rules from one pass over the window sums (dual.cu).
+int launch_dual(const uint8_t *d_src, size_t src_pitch, int h, int w, int ch, int W, double ks, double R, double kn,
+                uint8_t *d_dst_s, uint8_t *d_dst_n, size_t dst_pitch, int packed, const bnz_tile *tile,
+                cudaStream_t stream, unsigned long long *d_stats, unsigned int *d_err);
+
 // Row bands for a page of h rows, halving towards the end: band i starts at
 // row h - (h >> i) and the last one holds the final h >> (nb - 1) rows.  The
 // early, large bands' kernels and downloads run under the rest of the upload;
@@ -448,6 +453,33 @@ int bnz_binarize_dev(const uint8_t *d_src, size_t src_pitch, int height, int wid
 {
     return binarize_dev(d_src, src_pitch, height, width, channels, W, rule, k, R, d_dst, dst_pitch, packed, tile,
                         stream, d_stats);
+}
+
+int bnz_dual_dev(const uint8_t *d_src, size_t src_pitch, int height, int width, int channels, int W, double k_sauvola,
+                 double R, double k_niblack, uint8_t *d_dst_sauvola, uint8_t *d_dst_niblack, size_t dst_pitch,
+                 int packed, void *stream, unsigned long long *d_stats)
+{
+    int rc = check_common(d_src, src_pitch, height, width, channels, W, BNZ_SAUVOLA, k_sauvola, R, d_dst_sauvola,
+                          dst_pitch, packed);
+    if (rc != BNZ_OK)
+        return rc;
+    if (!d_dst_niblack)
+        return fail(BNZ_EINVAL, "null image pointer");
+    if (!std::isfinite(k_niblack))
+        return fail(BNZ_EINVAL, "k must be finite");
+    const size_t mask_bytes = (size_t)(height - 1) * dst_pitch + (packed ? ((size_t)width + 7) / 8 : (size_t)width);
+    const uintptr_t a = reinterpret_cast<uintptr_t>(d_dst_sauvola), b = reinterpret_cast<uintptr_t>(d_dst_niblack);
+    if (a < b + mask_bytes && b < a + mask_bytes)
+        return fail(BNZ_EINVAL, "the two masks overlap");
+    if ((reinterpret_cast<uintptr_t>(d_src) & 15u) || (src_pitch & 15u))
+        return fail(BNZ_EINVAL, "d_src must be 16-byte aligned with src_pitch a multiple of 16 (TMA)");
+    unsigned int *err = nullptr;
+    rc = device_err_flag(&err);
+    if (rc != BNZ_OK)
+        return rc;
+    return launch_dual(d_src, src_pitch, height, width, channels, W, k_sauvola, R, k_niblack, d_dst_sauvola,
+                       d_dst_niblack, dst_pitch, packed ? 1 : 0, nullptr, static_cast<cudaStream_t>(stream), d_stats,
+                       err);
 }
 
 size_t bnz_integral_scratch_bytes(int height, int width) { return integral_scratch_bytes(height, width); }
