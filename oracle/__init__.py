@@ -77,6 +77,9 @@ def _load():
                                      ctypes.POINTER(d)]
         lib.bnzref_integral.argtypes = [P, i, i, P, P]
         lib.bnzref_pack.argtypes = [P, i, i, ll, P, ll]
+        lib.bnzref_histogram.argtypes = [P, i, i, i, ll, P]
+        lib.bnzref_otsu_threshold.argtypes = [P, P]
+        lib.bnzref_otsu.argtypes = [P, i, i, i, ll, P, ll, ctypes.POINTER(i)]
         _lib = lib
         return lib
 
@@ -199,3 +202,32 @@ def pack(mask: np.ndarray) -> np.ndarray:
     out = np.empty((h, pb), np.uint8)
     _check(_load().bnzref_pack(_ptr(mask), h, w, w, _ptr(out), pb))
     return out
+
+
+def histogram(src: np.ndarray) -> np.ndarray:
+    """256-bin histogram of the Eq. 1 gray page (uint64)."""
+    src, h, w, ch = _img(src)
+    hist = np.zeros(256, np.uint64)
+    _check(_load().bnzref_histogram(_ptr(src), h, w, ch, w * ch, _ptr(hist)))
+    return hist
+
+
+def otsu_threshold(hist: np.ndarray):
+    """Otsu's T from a 256-bin histogram: returns (T, q) with q[t] the fp64 criterion (-1: no split)."""
+    hist = np.ascontiguousarray(hist, dtype=np.uint64)
+    if hist.shape != (256,):
+        raise ValueError("histogram must have 256 bins")
+    q = np.empty(256, np.float64)
+    T = _load().bnzref_otsu_threshold(_ptr(hist), _ptr(q))
+    return int(T), q
+
+
+def otsu(src: np.ndarray, packed: bool = False):
+    """Eq. 2 with Otsu's T: returns (mask, T); mask {0,255} bytes or packed bits."""
+    src, h, w, ch = _img(src)
+    out = np.empty((h, w), np.uint8)
+    T = ctypes.c_int(0)
+    _check(_load().bnzref_otsu(_ptr(src), h, w, ch, w * ch, _ptr(out), w, ctypes.byref(T)))
+    if packed:
+        out = pack(out)
+    return out, int(T.value)

@@ -400,3 +400,86 @@ int bnzref_pack(const uint8_t *mask, int h, int w, long long mask_pitch, uint8_t
     }
     return BNZREF_OK;
 }
+
+/* ---- Otsu's global threshold ------------------------------------------------
+ * Sec. 1 names Otsu's method as the best global technique; Eq. 2 applies one
+ * threshold T to every pixel: g = 0 if f < T, else 255.  The paper gives no
+ * formula for T; Otsu's published definition is used: over the histogram of f
+ * (Eq. 1 gray), T in [1, 255] splits the levels into [0, T-1] and [T, 255] with
+ * counts n0, n1 and level sums s0, s1 (N = n0 + n1, S = s0 + s1), and T
+ * maximises the between-class variance
+ *     w0 w1 (mu0 - mu1)^2 = (N s0 - S n0)^2 / (N^2 n0 n1).
+ * D = N s0 - S n0 is formed exactly in 128-bit integers; the criterion, an
+ * argmax decided in floating point, is q(T) = (d * d) / (a * b) in fp64 with
+ * d = (double)D, a = (double)n0, b = (double)n1.  The smallest T with the
+ * largest q wins; T = 0 (every pixel 255) when no T leaves both classes
+ * non-empty (a page of one gray level). */
+
+int bnzref_histogram(const uint8_t *src, int h, int w, int ch, long long pitch, uint64_t *hist)
+{
+    if (!src || !hist || h < 0 || w < 0 || (ch != 1 && ch != 3) || pitch < (long long)w * ch)
+        return BNZREF_EINVAL;
+    for (int i = 0; i < 256; ++i)
+        hist[i] = 0;
+    for (int y = 0; y < h; ++y) {
+        const uint8_t *row = src + (long long)y * pitch;
+        for (int x = 0; x < w; ++x)
+            hist[ch == 1 ? row[x] : bnzref_gray_px(row + 3 * x)]++;
+    }
+    return BNZREF_OK;
+}
+
+int bnzref_otsu_threshold(const uint64_t *hist, double *q_out)
+{
+    __int128 N = 0, S = 0;
+    for (int i = 0; i < 256; ++i) {
+        N += (__int128)hist[i];
+        S += (__int128)hist[i] * i;
+    }
+    __int128 n0 = 0, s0 = 0;
+    int best_t = 0;
+    double best_q = -1.0;
+    for (int t = 1; t < 256; ++t) {
+        n0 += (__int128)hist[t - 1];
+        s0 += (__int128)hist[t - 1] * (t - 1);
+        const __int128 n1 = N - n0;
+        double q = -1.0; /* no split */
+        if (n0 > 0 && n1 > 0) {
+            const __int128 D = N * s0 - S * n0;
+            const double d = (double)D, a = (double)n0, b = (double)n1;
+            q = (d * d) / (a * b);
+        }
+        if (q_out)
+            q_out[t] = q;
+        if (q > best_q) {
+            best_q = q;
+            best_t = t;
+        }
+    }
+    if (q_out)
+        q_out[0] = -1.0;
+    return best_q < 0.0 ? 0 : best_t;
+}
+
+int bnzref_otsu(const uint8_t *src, int h, int w, int ch, long long pitch, uint8_t *dst, long long dst_pitch,
+                int *T_out)
+{
+    uint64_t hist[256];
+    int rc = bnzref_histogram(src, h, w, ch, pitch, hist);
+    if (rc != BNZREF_OK)
+        return rc;
+    if (!dst || dst_pitch < w)
+        return BNZREF_EINVAL;
+    const int T = bnzref_otsu_threshold(hist, NULL);
+    for (int y = 0; y < h; ++y) {
+        const uint8_t *row = src + (long long)y * pitch;
+        uint8_t *out = dst + (long long)y * dst_pitch;
+        for (int x = 0; x < w; ++x) {
+            const int f = ch == 1 ? row[x] : bnzref_gray_px(row + 3 * x);
+            out[x] = f < T ? 0 : 255; /* Eq. 2 */
+        }
+    }
+    if (T_out)
+        *T_out = T;
+    return BNZREF_OK;
+}

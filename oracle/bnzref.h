@@ -27,6 +27,11 @@ int bnzref_pixel(const uint8_t *src, int h, int w, int ch, long long src_pitch, 
                  double R, int y, int x, int *tie, double *t_out);
 int bnzref_integral(const uint8_t *f, int h, int w, int64_t *I1, int64_t *I2);
 int bnzref_pack(const uint8_t *mask, int h, int w, long long mask_pitch, uint8_t *packed, long long packed_pitch);
+/* Otsu's global threshold and the Eq. 2 mask (see bnzref.c for the definition and the readings). */
+int bnzref_histogram(const uint8_t *src, int h, int w, int ch, long long pitch, uint64_t *hist);
+int bnzref_otsu_threshold(const uint64_t *hist, double *q_out);
+int bnzref_otsu(const uint8_t *src, int h, int w, int ch, long long pitch, uint8_t *dst, long long dst_pitch,
+                int *T_out);
 
 #ifdef __cplusplus
 }
