@@ -366,6 +366,7 @@ def run_ours(args):
         result["e2e"] = e2e_host_api(bnz, page, 5)
     if not args.case:
         result["dual"] = dual_runs(bnz, srcs, outs, stream, dev, args.steps, max(args.warmup, 3))
+        result["otsu"] = otsu_runs(bnz, srcs, outs, stream, dev, args.steps, max(args.warmup, 3))
     if rank == 0 and world == 1 and not args.no_cpu:
         import oracle
         threads = os.cpu_count() or 1
@@ -425,6 +426,40 @@ def dual_runs(bnz, srcs, outs, stream, dev, steps, warmup):
             "ms_per_step": total / steps, "Mpixel/s": masks / (total / 1e3) / 1e6, "us_per_launch": per,
             "note": "the same 8 masks as a step of the single-rule runs, two per launch from one pass over the "
                     "window sums; every mask equals the single-rule kernel's"}
+
+
+def otsu_runs(bnz, srcs, outs, stream, dev, steps, warmup):
+    """Eq. 2 with Otsu's threshold on the same page (bnz_otsu_dev: histogram, selection, mask; 3 kernels per call),
+    each call on its own input copy; algorithmic bytes: two reads of the RGB page and the byte mask."""
+    import torch
+    scratch = torch.zeros(bnz.BNZ_OTSU_SCRATCH_BYTES, dtype=torch.uint8, device=dev)
+    rot = [0]
+
+    def call():
+        c = rot[0] % NCOPY
+        rot[0] += 1
+        bnz.bnz_otsu_dev(srcs[c], outs[c], scratch, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            call()
+    stream.synchronize()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    with torch.cuda.stream(stream):
+        evs[0].record(stream)
+        for s in range(steps):
+            call()
+            evs[s + 1].record(stream)
+    stream.synchronize()
+    ts = sorted(evs[s].elapsed_time(evs[s + 1]) for s in range(steps))
+    ms = ts[len(ts) // 2]
+    peak, _ = measured_peak()
+    bytes_call = H * W_IMG * (2 * CH + 1)
+    gbs = bytes_call / (ms / 1e3) / 1e9
+    T = int(scratch[2048:2052].view(torch.int32).item())
+    return {"kernels": "otsu_hist, otsu_select, otsu_mask", "launches_per_call": 3, "us_per_call": round(ms * 1e3, 2),
+            "Mpixel/s": H * W_IMG / (ms / 1e3) / 1e6, "algorithmic_bytes_per_call": bytes_call,
+            "GB/s": round(gbs, 1), "frac": round(gbs / peak, 4), "T": T}
 
 
 def e2e_host_api(bnz, page, steps):

@@ -137,6 +137,23 @@ BNZ_API int bnz_dual_dev(const uint8_t *d_src, size_t src_pitch, int height, int
                  uint8_t *d_dst_niblack, size_t dst_pitch, int packed, void *stream,
                  unsigned long long *d_stats);
 
+/* Global binarization, Eq. 2 (g = 0 if f < T, else 255, one T for the page),
+ * with Otsu's threshold (Sec. 1 cites it as the best global method; the paper
+ * gives no formula, Otsu's published definition is used): over the 256-bin
+ * histogram of f (Eq. 1 gray), T in [1, 255] maximises the between-class
+ * variance of the levels [0, T-1] and [T, 255], evaluated as
+ * q = (D*D) / (n0*n1) in fp64 with D = N*s0 - S*n0 exact; the smallest T
+ * among equal q wins; T = 0 (all 255) for a page of one gray level.
+ * d_src: as bnz_sauvola_dev (16-byte aligned, pitch a multiple of 16); at most
+ * 2^28 pixels.  d_dst: byte or packed mask as bnz_sauvola_dev.  d_scratch:
+ * caller-owned device memory of BNZ_OTSU_SCRATCH_BYTES, 16-byte aligned; the
+ * call leaves the histogram (256 x uint64) at offset 0 and T (int32) at offset
+ * 2048.  Three kernels on `stream`, no host synchronization.  Errors: BNZ_EINVAL
+ * for bad arguments, BNZ_ECUDA for a failed launch. */
+#define BNZ_OTSU_SCRATCH_BYTES 4096
+BNZ_API int bnz_otsu_dev(const uint8_t *d_src, size_t src_pitch, int height, int width, int channels,
+                 uint8_t *d_dst, size_t dst_pitch, int packed, void *d_scratch, void *stream);
+
 /* Generic form of the two calls above with an explicit rule and optional
  * tile shape (tile may be NULL).  R is ignored for BNZ_NIBLACK. */
 BNZ_API int bnz_binarize_dev(const uint8_t *d_src, size_t src_pitch, int height, int width, int channels, int W,

@@ -75,13 +75,14 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.bnz_niblack_dev.argtypes = [P, sz, i, i, i, i, d, P, sz, i, P, P]
     lib.bnz_binarize_dev.argtypes = [P, sz, i, i, i, i, i, d, d, P, sz, i, P, P, P]
     lib.bnz_dual_dev.argtypes = [P, sz, i, i, i, i, d, d, d, P, P, sz, i, P, P]
+    lib.bnz_otsu_dev.argtypes = [P, sz, i, i, i, P, sz, i, P, P]
     lib.bnz_last_error.restype = ctypes.c_char_p
     lib.bnz_last_error.argtypes = []
     lib.bnz_version.argtypes = []
     lib.bnz_fused_plan.argtypes = [i, i, i, i, P, ctypes.POINTER(sz), ctypes.POINTER(i), ctypes.POINTER(i),
                                    ctypes.POINTER(i)]
     for name in ("bnz_sauvola", "bnz_niblack", "bnz_sauvola_dev", "bnz_niblack_dev", "bnz_binarize_dev",
-                 "bnz_dual_dev", "bnz_version", "bnz_fused_plan"):
+                 "bnz_dual_dev", "bnz_otsu_dev", "bnz_version", "bnz_fused_plan"):
         getattr(lib, name).restype = ctypes.c_int
     _optional_symbols(lib)
     _lib = lib
@@ -271,6 +272,32 @@ def binarize_dual(d_src, W: int, k_sauvola: float = 0.5, R: float = 128.0, k_nib
     out_n = alloc_pitched(h, row, d_src.device)
     bnz_dual_dev(d_src, W, k_sauvola, R, k_niblack, out_s, out_n, packed, stream, d_stats)
     return out_s, out_n
+
+
+BNZ_OTSU_SCRATCH_BYTES = 4096
+
+
+def bnz_otsu_dev(d_src, d_dst, d_scratch, packed: bool = False, stream=None) -> None:
+    """Enqueue Eq. 2 with Otsu's threshold; d_scratch: uint8 CUDA tensor of BNZ_OTSU_SCRATCH_BYTES."""
+    ptr, pitch, h, w, ch = _dev_img(d_src)
+    dp = _out_pitch(d_dst, w, packed)
+    if d_scratch.numel() * d_scratch.element_size() < BNZ_OTSU_SCRATCH_BYTES:
+        raise ValueError(f"d_scratch must hold {BNZ_OTSU_SCRATCH_BYTES} bytes")
+    _check(load().bnz_otsu_dev(ptr, pitch, h, w, ch, d_dst.data_ptr(), dp, 1 if packed else 0,
+                               d_scratch.data_ptr(), _stream_ptr(stream)))
+
+
+def otsu(d_src, packed: bool = False, stream=None):
+    """Global binarization with Otsu's threshold: returns (mask, T, histogram) on the device; T and the
+    histogram are views into the scratch the call writes (read them after the stream's work)."""
+    import torch
+    _, _, h, w, _ = _dev_img(d_src)
+    out = alloc_pitched(h, (w + 7) // 8 if packed else w, d_src.device)
+    scratch = torch.empty(BNZ_OTSU_SCRATCH_BYTES, dtype=torch.uint8, device=d_src.device)
+    bnz_otsu_dev(d_src, out, scratch, packed, stream)
+    hist = scratch[:2048].view(torch.int64)
+    T = scratch[2048:2052].view(torch.int32)
+    return out, T, hist
 
 
 def bnz_copy2d_async(dst: int, dst_pitch: int, src: int, src_pitch: int, width_bytes: int, height: int,

@@ -283,6 +283,10 @@ int launch_dual(const uint8_t *d_src, size_t src_pitch, int h, int w, int ch, in
                 uint8_t *d_dst_s, uint8_t *d_dst_n, size_t dst_pitch, int packed, const bnz_tile *tile,
                 cudaStream_t stream, unsigned long long *d_stats, unsigned int *d_err);
 
+// Eq. 2 with Otsu's threshold (otsu.cu).
+int launch_otsu(const uint8_t *d_src, size_t src_pitch, int h, int w, int ch, uint8_t *d_dst, size_t dst_pitch,
+                int packed, void *d_scratch, cudaStream_t stream);
+
 // Row bands for a page of h rows, halving towards the end: band i starts at
 // row h - (h >> i) and the last one holds the final h >> (nb - 1) rows.  The
 // early, large bands' kernels and downloads run under the rest of the upload;
@@ -480,6 +484,24 @@ int bnz_dual_dev(const uint8_t *d_src, size_t src_pitch, int height, int width, 
     return launch_dual(d_src, src_pitch, height, width, channels, W, k_sauvola, R, k_niblack, d_dst_sauvola,
                        d_dst_niblack, dst_pitch, packed ? 1 : 0, nullptr, static_cast<cudaStream_t>(stream), d_stats,
                        err);
+}
+
+int bnz_otsu_dev(const uint8_t *d_src, size_t src_pitch, int height, int width, int channels, uint8_t *d_dst,
+                 size_t dst_pitch, int packed, void *d_scratch, void *stream)
+{
+    // the window arguments of the shared checks do not apply: valid placeholders
+    int rc = check_common(d_src, src_pitch, height, width, channels, 1, BNZ_SAUVOLA, 0.5, 1.0, d_dst, dst_pitch,
+                          packed);
+    if (rc != BNZ_OK)
+        return rc;
+    if ((long long)height * width > (1ll << 28))
+        return fail(BNZ_EINVAL, "Otsu: at most 2^28 pixels (got %lld)", (long long)height * width);
+    if ((reinterpret_cast<uintptr_t>(d_src) & 15u) || (src_pitch & 15u))
+        return fail(BNZ_EINVAL, "d_src must be 16-byte aligned with src_pitch a multiple of 16");
+    if (!d_scratch || (reinterpret_cast<uintptr_t>(d_scratch) & 15u))
+        return fail(BNZ_EINVAL, "d_scratch must be a 16-byte aligned buffer of BNZ_OTSU_SCRATCH_BYTES");
+    return launch_otsu(d_src, src_pitch, height, width, channels, d_dst, dst_pitch, packed ? 1 : 0, d_scratch,
+                       static_cast<cudaStream_t>(stream));
 }
 
 size_t bnz_integral_scratch_bytes(int height, int width) { return integral_scratch_bytes(height, width); }
