@@ -93,3 +93,43 @@ def test_native_server_needs_a_device_and_checks_its_config():
         pytest.skip("a GPU is present")
     ok = bnz.bnz_server_config(1 << 30, 16, 2, 1, 0)
     assert lib.bnz_server_create(ctypes.byref(ok), ctypes.byref(h)) == bnz.BNZ_ENODEV and not h.value
+
+
+def _aligned(buf):
+    return (buf.ctypes.data + 15) & ~15
+
+
+def test_dual_and_otsu_argument_checks(lib):
+    # the checks run before any device work, so host addresses stand in for device buffers
+    buf = np.zeros(8192, np.uint8)
+    a = _aligned(buf)
+    nan = float("nan")
+    rc = lib.bnz_dual_dev(a, 16, 8, 16, 1, 5, 0.5, 128.0, -0.2, a + 1024, a + 1024 + 8, 16, 0, None, None)
+    assert rc == bnz.BNZ_EINVAL and "overlap" in bnz.bnz_last_error()
+    rc = lib.bnz_dual_dev(a, 16, 8, 16, 1, 5, 0.5, 128.0, nan, a + 1024, a + 2048, 16, 0, None, None)
+    assert rc == bnz.BNZ_EINVAL and "k must be finite" in bnz.bnz_last_error()
+    rc = lib.bnz_dual_dev(a, 16, 8, 16, 1, 5, 0.5, 128.0, -0.2, a + 1024, None, 16, 0, None, None)
+    assert rc == bnz.BNZ_EINVAL and "null" in bnz.bnz_last_error()
+    rc = lib.bnz_dual_dev(a, 16, 8, 16, 1, 256, 0.5, 128.0, -0.2, a + 1024, a + 2048, 16, 0, None, None)
+    assert rc == bnz.BNZ_EINVAL and "window size" in bnz.bnz_last_error()
+    rc = lib.bnz_otsu_dev(a, 16384, 16385, 16384, 1, a, 16384, 0, a, None)
+    assert rc == bnz.BNZ_EINVAL and "2^28" in bnz.bnz_last_error()
+    rc = lib.bnz_otsu_dev(a, 16, 8, 16, 1, a + 1024, 16, 0, a + 2049, None)
+    assert rc == bnz.BNZ_EINVAL and "d_scratch" in bnz.bnz_last_error()
+    rc = lib.bnz_otsu_dev(a + 1, 16, 8, 16, 1, a + 1024, 16, 0, a + 2048, None)
+    assert rc == bnz.BNZ_EINVAL and "16-byte aligned" in bnz.bnz_last_error()
+    rc = lib.bnz_otsu_dev(a, 16, 8, 16, 2, a + 1024, 16, 0, a + 2048, None)
+    assert rc == bnz.BNZ_EINVAL and "channels" in bnz.bnz_last_error()
+
+
+def test_dual_and_otsu_need_a_device():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    lib = bnz.load()
+    buf = np.zeros(8192, np.uint8)
+    a = _aligned(buf)
+    assert lib.bnz_dual_dev(a, 16, 8, 16, 1, 5, 0.5, 128.0, -0.2, a + 1024, a + 2048, 16, 0, None,
+                            None) == bnz.BNZ_ENODEV
+    assert lib.bnz_otsu_dev(a, 16, 8, 16, 1, a + 1024, 16, 0, a + 2048, None) == bnz.BNZ_ENODEV
+    assert (buf == 0).all()
