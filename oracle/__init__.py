@@ -11,11 +11,16 @@ is a single IEEE-rounded step in the order the C source states:
 * clipped W x W window sums (Sec. 2), exact int64, by two independent paths:
   naive O(W^2) per pixel and the O(W)-per-pixel sliding scheme (Sec. 3);
 * m, s and the Sauvola threshold of Eq. 4 or the Niblack threshold in fp64;
-* the decision of Eq. 3, with ties ``|f - t| < 1e-9`` counted.
+* the decision of Eq. 3, with ties ``|f - t| < 1e-9`` counted;
+* the global rule of Eq. 2 with Otsu's threshold (cited in Sec. 1; Otsu's
+  published definition: the T maximising the between-class variance of the
+  gray histogram, exact 128-bit class difference, fp64 criterion, smallest T
+  among equal values).
 
 Pins (tests/test_oracle_*.py) tie it to things other than itself: brute force
 on tiny images, a library box filter, exact rational arithmetic, closed forms
-(constant image, step edge, impulse) and symmetry invariants.
+(constant image, step edge, impulse; one- and two-level pages for Otsu) and
+symmetry and offset invariants.
 """
 from __future__ import annotations
 
