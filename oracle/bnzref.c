@@ -29,10 +29,13 @@
  *       Sauvola: t = m * (1.0 + k * (s / R - 1.0))
  *       Niblack: t = m + k * s
  *   A "tie" is a pixel with |f - t| < 1e-9; ties are counted.
+ *   - Global rule, Eq. 2 (g = 0 if f < T, else 255) with Otsu's T (cited in
+ *     Sec. 1 as the best global method, formula not printed): see
+ *     bnzref_otsu_threshold below.
  *
  * Two independent window-sum paths are provided:
  *   A. naive: sum over the clipped window for every pixel, O(W^2) per pixel
- *      (the "algorithmic implementation" of Sec. 1, O(W^2 N^2) overall).
+ *      (the direct evaluation the paper measures against, O(W^2 N^2) overall).
  *   B. sliding: along each row, the window sum of pixel x+1 is that of pixel
  *      x plus the entering column minus the leaving column, each a sum over
  *      the window's rows -- O(W) per pixel and no extra image-sized memory,
