@@ -105,6 +105,14 @@ BNZ_API int bnz_sauvola(const uint8_t *src, int height, int width, int channels,
 /* Niblack rule t = m + k*s (k may be negative, e.g. -0.2). */
 BNZ_API int bnz_niblack(const uint8_t *src, int height, int width, int channels, int W, double k, uint8_t *dst);
 
+/* The row bands the two calls above use for a page (host logic only, no
+ * device needed): returns the band count nb (>= 1) and, if starts is not NULL,
+ * writes the nb + 1 boundaries starts[0] = 0 < ... < starts[nb] = height
+ * (max_bands: entries available in starts, at least nb + 1).  Band i starts at
+ * row height - (height >> i); the smallest band has at least max(128, 2W)
+ * rows; pages under 2^20 pixels are one band.  -BNZ_EINVAL for bad arguments. */
+BNZ_API int bnz_host_bands(int height, int width, int W, int *starts, int max_bands);
+
 /* ---- asynchronous device-pointer API -------------------------------------
  * d_src: device pointer, 16-byte aligned, rows src_pitch bytes apart,
  *   src_pitch a multiple of 16 and >= width*channels (TMA requirement).

@@ -76,13 +76,14 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.bnz_binarize_dev.argtypes = [P, sz, i, i, i, i, i, d, d, P, sz, i, P, P, P]
     lib.bnz_dual_dev.argtypes = [P, sz, i, i, i, i, d, d, d, P, P, sz, i, P, P]
     lib.bnz_otsu_dev.argtypes = [P, sz, i, i, i, P, sz, i, P, P]
+    lib.bnz_host_bands.argtypes = [i, i, i, P, i]
     lib.bnz_last_error.restype = ctypes.c_char_p
     lib.bnz_last_error.argtypes = []
     lib.bnz_version.argtypes = []
     lib.bnz_fused_plan.argtypes = [i, i, i, i, P, ctypes.POINTER(sz), ctypes.POINTER(i), ctypes.POINTER(i),
                                    ctypes.POINTER(i)]
     for name in ("bnz_sauvola", "bnz_niblack", "bnz_sauvola_dev", "bnz_niblack_dev", "bnz_binarize_dev",
-                 "bnz_dual_dev", "bnz_otsu_dev", "bnz_version", "bnz_fused_plan"):
+                 "bnz_dual_dev", "bnz_otsu_dev", "bnz_host_bands", "bnz_version", "bnz_fused_plan"):
         getattr(lib, name).restype = ctypes.c_int
     _optional_symbols(lib)
     _lib = lib
@@ -298,6 +299,16 @@ def otsu(d_src, packed: bool = False, stream=None):
     hist = scratch[:2048].view(torch.int64)
     T = scratch[2048:2052].view(torch.int32)
     return out, T, hist
+
+
+def host_bands(height: int, width: int, W: int) -> list:
+    """Row-band boundaries [0, ..., height] the host-pointer calls use for a page (host logic, no device)."""
+    import numpy as np
+    starts = np.zeros(64, np.int32)
+    nb = load().bnz_host_bands(int(height), int(width), int(W), starts.ctypes.data, len(starts))
+    if nb < 0:
+        raise BnzError(-nb, bnz_last_error())
+    return [int(v) for v in starts[:nb + 1]]
 
 
 def bnz_copy2d_async(dst: int, dst_pitch: int, src: int, src_pitch: int, width_bytes: int, height: int,

@@ -504,6 +504,21 @@ int bnz_otsu_dev(const uint8_t *d_src, size_t src_pitch, int height, int width, 
                        static_cast<cudaStream_t>(stream));
 }
 
+int bnz_host_bands(int height, int width, int W, int *starts, int max_bands)
+{
+    if (height < 1 || width < 1 || W < 1 || W > BNZ_MAX_W)
+        return -fail(BNZ_EINVAL, "height, width >= 1 and W in [1, %d] required", BNZ_MAX_W);
+    const int nb = host_bands(height, width, W);
+    if (starts) {
+        if (max_bands < nb + 1)
+            return -fail(BNZ_EINVAL, "starts must hold %d entries", nb + 1);
+        for (int i = 0; i < nb; ++i)
+            starts[i] = band_start(height, i);
+        starts[nb] = height;
+    }
+    return nb;
+}
+
 size_t bnz_integral_scratch_bytes(int height, int width) { return integral_scratch_bytes(height, width); }
 
 int bnz_binarize_integral_dev(const uint8_t *d_src, size_t src_pitch, int height, int width, int channels, int W,

@@ -133,3 +133,32 @@ def test_dual_and_otsu_need_a_device():
                             None) == bnz.BNZ_ENODEV
     assert lib.bnz_otsu_dev(a, 16, 8, 16, 1, a + 1024, 16, 0, a + 2048, None) == bnz.BNZ_ENODEV
     assert (buf == 0).all()
+
+
+@pytest.mark.parametrize("h,w,W", [(4096, 4096, 15), (4096, 4096, 101), (1030, 1100, 101), (1031, 1024, 15),
+                                   (2050, 700, 61), (1300, 1000, 4), (1100, 1000, 255), (16384, 16384, 101),
+                                   (7016, 4960, 61), (512, 512, 15), (1023, 1024, 15), (300, 5000, 15),
+                                   (1, 1 << 21, 1), (1 << 21, 1, 1)])
+def test_host_bands_plan(h, w, W):
+    # the row bands of the host-pointer calls: host logic, checked without a device
+    b = bnz.host_bands(h, w, W)
+    nb = len(b) - 1
+    assert b[0] == 0 and b[-1] == h and all(b[i] < b[i + 1] for i in range(nb))
+    sizes = [b[i + 1] - b[i] for i in range(nb)]
+    if h * w < (1 << 20):
+        assert nb == 1
+        return
+    assert 1 <= nb <= 4
+    assert all(sizes[i] >= sizes[i + 1] for i in range(nb - 1))     # halving towards the page end
+    assert b[:nb] == [h - (h >> i) for i in range(nb)]
+    if nb > 1:
+        assert min(sizes) >= max(128, 2 * W)
+    if nb < 4:                                                       # as many bands as the rule allows
+        assert (h >> nb) < max(128, 2 * W)
+
+
+def test_host_bands_rejects_bad_arguments():
+    with pytest.raises(bnz.BnzError):
+        bnz.host_bands(0, 10, 3)
+    with pytest.raises(bnz.BnzError):
+        bnz.host_bands(10, 10, 256)

@@ -145,6 +145,7 @@ def test_host_pointer_api(bnz):
 def test_host_pointer_api_row_bands(bnz, h, w, ch, W, rule):
     # pages of a megapixel and more go through the host API in row bands, each band's
     # upload, kernel and download on their own streams
+    assert len(bnz.host_bands(h, w, W)) > 2                       # the case really runs in bands
     img = synth.page(h, w, 17, synth.STAINS if ch == 3 else synth.DOC, ch)
     if rule == "sauvola":
         ref, _ = oracle.sauvola(img, W, 0.5, 128.0, threads=NTHREADS)
