@@ -73,6 +73,11 @@ typedef enum {
 typedef enum { BNZ_SAUVOLA = 0, BNZ_NIBLACK = 1 } bnz_rule;
 
 #define BNZ_MAX_W 255
+/* Accepted threshold parameters: |k| <= BNZ_MAX_ABS_K and, for Sauvola,
+ * R >= BNZ_MIN_R.  Within this range every output equals the fp64 decision;
+ * outside it the calls return BNZ_EINVAL. */
+#define BNZ_MAX_ABS_K 1.0e6
+#define BNZ_MIN_R 1.0e-6
 #define BNZ_STATS_FALLBACKS 0
 #define BNZ_STATS_TIES 1
 #define BNZ_STATS_TIMEOUTS 2
@@ -93,8 +98,8 @@ typedef struct {
 
 /* src: height rows of width*channels bytes, tightly packed, host memory.
  * dst: height*width bytes, {0,255}, host memory.  Blocks until done.
- * k: any finite value; R > 0 (the dynamic range of the standard deviation,
- * Sec. 1 after Eq. 4).
+ * k: |k| <= BNZ_MAX_ABS_K; R >= BNZ_MIN_R (the dynamic range of the standard
+ * deviation, Sec. 1 after Eq. 4).
  * Page-locked host buffers copy fastest.  Pages of a megapixel or more are
  * processed in up to 4 row bands whose uploads, kernels and downloads overlap
  * on the calling thread's library streams; the result is the same as in one

@@ -144,10 +144,13 @@ int check_common(const void *src, size_t src_pitch, int height, int width, int c
         return fail(BNZ_EINVAL, "window size W must be in [1, %d] (got %d)", BNZ_MAX_W, W);
     if (rule != BNZ_SAUVOLA && rule != BNZ_NIBLACK)
         return fail(BNZ_EINVAL, "unknown rule %d", rule);
-    if (!std::isfinite(k))
-        return fail(BNZ_EINVAL, "k must be finite");
-    if (rule == BNZ_SAUVOLA && !(R > 0.0 && std::isfinite(R)))
-        return fail(BNZ_EINVAL, "R must be finite and > 0 for Sauvola (got %g)", R);
+    // the range within which every fp32 and double-float constant of the
+    // decision, and every intermediate of the filters, stays finite (so the
+    // proven error bounds apply and every output equals the fp64 decision)
+    if (!(std::fabs(k) <= BNZ_MAX_ABS_K))
+        return fail(BNZ_EINVAL, "k must be finite with |k| <= %g (got %g)", BNZ_MAX_ABS_K, k);
+    if (rule == BNZ_SAUVOLA && !(R >= BNZ_MIN_R && std::isfinite(R)))
+        return fail(BNZ_EINVAL, "R must be finite and >= %g for Sauvola (got %g)", BNZ_MIN_R, R);
     if (src_pitch < (size_t)width * channels)
         return fail(BNZ_EINVAL, "src_pitch %zu < width*channels %zu", src_pitch, (size_t)width * channels);
     const size_t row_out = packed ? ((size_t)width + 7) / 8 : (size_t)width;

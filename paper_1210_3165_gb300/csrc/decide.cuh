@@ -139,10 +139,11 @@ __device__ __forceinline__ df df_sqrt_v(unsigned long long V)
 
 // Eq. 3 for a pixel the fp32 filter could not decide.  f - t in double-float
 // (Niblack t = m + k s; Sauvola t = m (1-k) + m s (k/R), m = S1/n, s = sqrt(V)/n),
-// absolute error < 1e-10 for every f, m <= 255, s <= 128, |k| <= 16.  When it
-// is farther than 1e-9 + 1e-10 + 1e-12 from zero, neither the exact value nor
-// the fp64 definition (within 1e-12 of it) is a tie and the sign decides;
-// otherwise the fp64 sequence of the definition decides (and counts the tie).
+// whose absolute error the host bounds from k and R (double_float_error; below
+// 1e-10 for the usual |k| <= 1, R >= 64).  When it is farther than p.Tdf =
+// 1e-9 + that bound + the fp64 definition's own error from zero, the fp64
+// definition sees no tie and the same sign, so the sign decides; otherwise the
+// fp64 sequence of the definition decides (and counts the tie).
 template <int RULE>
 __device__ uint32_t decide_exact(uint32_t f, uint32_t n, uint32_t S1, uint32_t S2, const FusedParams &p)
 {
@@ -158,7 +159,7 @@ __device__ uint32_t decide_exact(uint32_t f, uint32_t n, uint32_t S1, uint32_t S
         t = df_add(m, df_mul({p.kh, p.kl}, sd));
     const df d = df_add({__uint2float_rn(f), 0.0f}, {-t.hi, -t.lo});
     const float dv = __fadd_rn(d.hi, d.lo);
-    if (fabsf(dv) > 1.2e-9f)
+    if (fabsf(dv) > p.Tdf)
         return dv < 0.0f ? 0u : 255u;
     return decide_fp64<RULE>(f, n, S1, S2, p);
 }

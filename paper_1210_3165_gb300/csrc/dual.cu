@@ -16,97 +16,36 @@
 namespace bnz {
 namespace {
 
-// The lane's 16 fp32 filters of one rule in the pixels whose |d| lies inside
-// the rule's margin: the exact decision (double-float, then fp64 near ties)
-// for those pixels, patched into the lane's output words.  Counts re-evaluated
-// pixels and ties.
-template <int RULE, int KO, int KI>
-__device__ __forceinline__ void fix_margin(const FusedParams &p, const uint32_t *C1, const uint32_t *C2, int ao,
-                                           int ai, uint32_t base1, uint32_t base2, const uint32_t (&fw)[4], int y,
-                                           int xg0, uint32_t (&outw)[4], uint32_t &nfb, uint32_t &nties)
+// Fast decision of both rules for the lane's 16 pixels when every window of the
+// warp is W x W: the sums, V, sqrt(V), S1 and the pixel values are formed
+// once, then each rule's fp32 filter gives its own mask word and margin.
+__device__ __forceinline__ void decide_lane_int_dual(const FusedParams &ps, const FusedParams &pn, uint32_t base1,
+                                                     uint32_t base2, const uint32_t (&d1)[L], const uint32_t (&d2)[L],
+                                                     const uint32_t (&fw)[4], uint32_t (&outs)[4], uint32_t (&outn)[4],
+                                                     float &mns, float &mnn)
 {
-    const int nr = min(y + p.r_hi, p.h - 1) - max(y - p.r_lo, 0) + 1;
-    uint32_t e1[L], e2[L], t1, t2;
-    lane_deltas<KO, KI>(C1, C2, ao, ai, e1, e2, t1, t2);
-    uint32_t amask = 0;
-#pragma unroll
-    for (int t = 0; t < L; ++t) {
-        const int xg = xg0 + t;
-        const int nc = min(xg + p.r_hi, p.w - 1) - max(xg - p.r_lo, 0) + 1;
-        const uint32_t n = (uint32_t)(nr * nc);
-        const uint32_t S1 = base1 + e1[t], S2 = base2 + e2[t];
-        const unsigned long long V = (unsigned long long)n * S2 - (unsigned long long)S1 * S1;
-        const float ff = byte_float(fw[t >> 2], t & 3);
-        const float sq = sqrt_approx(v_to_float(V));
-        const float d = (n == p.nW) ? filter_int<RULE>(ff, __uint2float_rn(S1), sq, p)
-                                    : filter_n<RULE>(ff, __uint2float_rn(S1), sq, rcp_approx(__uint2float_rn(n)), p);
-        if (xg < p.w && fabsf(d) < p.E)
-            amask |= 1u << t;
-    }
-    uint32_t white = 0;
-    for (uint32_t m = amask; m; m &= m - 1) {
-        const int t = __ffs(m) - 1;
-        uint32_t S1 = base1, S2 = base2, word = fw[0];
-#pragma unroll
-        for (int u = 0; u < L; ++u)
-            if (u == t) {
-                S1 += e1[u];
-                S2 += e2[u];
-            }
-#pragma unroll
-        for (int qq = 1; qq < 4; ++qq)
-            if ((t >> 2) == qq)
-                word = fw[qq];
-        const uint32_t f = (word >> (8 * (t & 3))) & 0xffu;
-        const int xg = xg0 + t;
-        const int nc = min(xg + p.r_hi, p.w - 1) - max(xg - p.r_lo, 0) + 1;
-        const uint32_t r = decide_exact<RULE>(f, (uint32_t)(nr * nc), S1, S2, p);
-        ++nfb;
-        nties += (r >> 9) & 1u;
-        white |= (r & 1u) << t;
-    }
+    const long long NB2 = (long long)((unsigned long long)ps.nW * base2);
+    const int nb1 = -(int)base1;
+    const int nW = (int)ps.nW;
 #pragma unroll
     for (int qq = 0; qq < 4; ++qq) {
-        const uint32_t mm = ((((amask >> (4 * qq)) & 15u) * 0x00204081u) & 0x01010101u) * 0xffu;
-        const uint32_t vv = ((((white >> (4 * qq)) & 15u) * 0x00204081u) & 0x01010101u) * 0xffu;
-        outw[qq] = (outw[qq] & ~mm) | (vv & mm);
-    }
-}
-
-// The lane's 16 outputs of row y into p.dst: byte mask or packed bits.
-__device__ __forceinline__ void store_lane(const FusedParams &p, int y, int xg0, const uint32_t (&outw)[4])
-{
-    if (!p.packed) {
-        uint8_t *drow = p.dst + (size_t)y * p.dst_pitch + xg0;
-        if (p.vec_ok && xg0 + L <= p.w) {
-            *reinterpret_cast<uint4 *>(drow) = make_uint4(outw[0], outw[1], outw[2], outw[3]);
-        } else {
+        float2 nf01, nf23;
+        neg_bytes(fw[qq], nf01, nf23);
+        float s[4], q[4];
 #pragma unroll
-            for (int t = 0; t < L; ++t)
-                if (xg0 + t < p.w)
-                    drow[t] = (uint8_t)byte_dyn(outw[t >> 2], t & 3);
-        }
-    } else {
-        uint32_t bits = 0; // bit t <-> pixel xg0 + t: the msb of each byte
-#pragma unroll
-        for (int qq = 0; qq < 4; ++qq)
-            bits |= ((((outw[qq] >> 7) & 0x01010101u) * 0x01020408u) >> 24) << (4 * qq);
-        const int valid = p.w - xg0;
-        if (valid < L)
-            bits &= (1u << valid) - 1u;
-        uint8_t *drow = p.dst + (size_t)y * p.dst_pitch + (xg0 >> 3);
-        drow[0] = (uint8_t)(bits & 0xffu);
-        if (valid > 8)
-            drow[1] = (uint8_t)(bits >> 8);
+        for (int e = 0; e < 4; ++e)
+            stats_int(base1, nb1, NB2, nW, d1[4 * qq + e], d2[4 * qq + e], s[e], q[e]);
+        const float2 s01 = make_float2(s[0], s[1]), s23 = make_float2(s[2], s[3]);
+        const float2 q01 = make_float2(q[0], q[1]), q23 = make_float2(q[2], q[3]);
+        const float2 a = filter2_int<BNZ_SAUVOLA>(s01, q01, nf01, ps);
+        const float2 c = filter2_int<BNZ_SAUVOLA>(s23, q23, nf23, ps);
+        const float2 an = filter2_int<BNZ_NIBLACK>(s01, q01, nf01, pn);
+        const float2 cn = filter2_int<BNZ_NIBLACK>(s23, q23, nf23, pn);
+        mns = fminf(mns, fminf(fminf(fabsf(a.x), fabsf(a.y)), fminf(fabsf(c.x), fabsf(c.y))));
+        mnn = fminf(mnn, fminf(fminf(fabsf(an.x), fabsf(an.y)), fminf(fabsf(cn.x), fabsf(cn.y))));
+        outs[qq] = sign_bytes(a.x, a.y, c.x, c.y);
+        outn[qq] = sign_bytes(an.x, an.y, cn.x, cn.y);
     }
-}
-
-// byte = 0xFF where d >= +0, 0x00 where d < 0 (sign bit replicated)
-__device__ __forceinline__ uint32_t mask_word(const float (&dd)[4])
-{
-    const uint32_t lo = prmt(__float_as_uint(dd[0]), __float_as_uint(dd[1]), 0xFBu);
-    const uint32_t hi = prmt(__float_as_uint(dd[2]), __float_as_uint(dd[3]), 0xFBu);
-    return ~prmt(lo, hi, 0x5410u);
 }
 
 // Consumers of the dual kernel: horizontal sums as in consume(), then the
@@ -118,123 +57,48 @@ __device__ __forceinline__ void consume_dual(const FusedParams &ps, const FusedP
                                              volatile int *s_abort)
 {
     const FusedParams &p = ps; // geometry, shared by both rules
+    constexpr int KO = Align<WM8>::KO, KI = Align<WM8>::KI;
     const int SWP = p.SWP;
-    constexpr int KO = (4 - ((WM8 >> 1) & 3)) & 3;
-    constexpr int KI = (KO + WM8) & 3;
     const uint8_t *ring = smem + p.off_ring;
     const uint32_t *cb = reinterpret_cast<const uint32_t *>(smem + p.off_cb);
-    const int q = threadIdx.x - NTP;
-    const int lane = q & 31, ii = q >> 5;
-    const int W = p.W;
-    const bool active = lane * L < p.TW;
-    const int fcol = active ? lane * L + p.o + p.r_lo : 0;
-    const uint8_t *fbase = ring + fcol;
-    const int xg0 = sg.x0 + lane * L;
-    const bool xclip = xg0 < p.r_lo || xg0 + L - 1 + p.r_hi > p.w - 1;
+    const LaneGeo g = lane_geo<KO>(p, sg);
+    const uint8_t *fbase = ring + g.fcol;
 
-    int rc = (ii + p.r_lo) % p.ring_rows;
+    int rc = (g.ii + p.r_lo) % p.ring_rows;
     for (int k = 0; k < sg.nk; ++k, rc = (rc + CH < p.ring_rows) ? rc + CH : rc + CH - p.ring_rows) {
         const int b = k & 1;
         bar_sync(BAR_FULL + b, NTX);
         const int rows_k = min(CH, sg.th_eff - k * CH);
-        if (ii < rows_k && !*s_abort) {
-            const int y = sg.y0 + k * CH + ii;
-            const uint32_t *C1 = cb + (size_t)(2 * b) * CH * p.RSW + ii * p.RSW;
-            const uint32_t *C2 = C1 + (size_t)CH * p.RSW;
-            const int cw = lane * L + p.o;
-            const int ao = cw >> 2, ai = (cw + W) >> 2;
-
-            uint32_t d1[L], d2[L];
-            uint32_t a1 = 0, a2 = 0;
-            if (active) {
-                lane_deltas<KO, KI>(C1, C2, ao, ai, d1, d2, a1, a2);
-            } else {
-#pragma unroll
-                for (int t = 0; t < L; ++t)
-                    d1[t] = d2[t] = 0u;
-            }
-            uint32_t s1 = 0, s2 = 0;
-            for (int c = p.o + lane; c < p.o + W; c += 32) {
-                const int qc = cpos(c);
-                s1 += C1[qc];
-                s2 += C2[qc];
-            }
-            s1 = __reduce_add_sync(0xffffffffu, s1);
-            s2 = __reduce_add_sync(0xffffffffu, s2);
-            uint32_t x1 = a1, x2 = a2;
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const uint32_t t1 = __shfl_up_sync(0xffffffffu, x1, off);
-                const uint32_t t2 = __shfl_up_sync(0xffffffffu, x2, off);
-                if (lane >= off) {
-                    x1 += t1;
-                    x2 += t2;
-                }
-            }
-            const uint32_t base1 = s1 + x1 - a1, base2 = s2 + x2 - a2;
+        if (g.ii < rows_k && !*s_abort) {
+            const int y = sg.y0 + k * CH + g.ii;
+            const uint32_t *C1 = cb + (size_t)(2 * b) * C2O + g.ii * RS;
+            uint32_t d1[L], d2[L], base1, base2;
+            row_sums<KO, KI, WM8>(p, g, C1, d1, d2, base1, base2);
 
             const uint4 fv = *reinterpret_cast<const uint4 *>(fbase + (size_t)rc * SWP);
             const uint32_t fw[4] = {fv.x, fv.y, fv.z, fv.w};
             const bool yclip = (y < p.r_lo) || (y + p.r_hi > p.h - 1);
-            const bool lane_clip = active && xg0 < p.w && (yclip || xclip);
+            const bool lane_clip = g.active && g.xg0 < p.w && (yclip || g.xclip);
             uint32_t outs[4], outn[4];
             float mns = INFINITY, mnn = INFINITY;
             if (!__any_sync(0xffffffffu, lane_clip)) {
-#pragma unroll
-                for (int qq = 0; qq < 4; ++qq) {
-                    float ds[4], dn[4];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int t = 4 * qq + e;
-                        const uint32_t S1 = base1 + d1[t];
-                        const uint32_t S2 = base2 + d2[t];
-                        const unsigned long long V =
-                            (unsigned long long)p.nW * S2 - (unsigned long long)S1 * S1;
-                        const float ff = byte_float(fw[qq], e);
-                        const float S1f = __uint2float_rn(S1);
-                        const float sq = sqrt_approx(v_to_float(V));
-                        ds[e] = filter_int<BNZ_SAUVOLA>(ff, S1f, sq, ps);
-                        dn[e] = filter_int<BNZ_NIBLACK>(ff, S1f, sq, pn);
-                        mns = fminf(mns, fabsf(ds[e]));
-                        mnn = fminf(mnn, fabsf(dn[e]));
-                    }
-                    outs[qq] = mask_word(ds);
-                    outn[qq] = mask_word(dn);
-                }
+                decide_lane_int_dual(ps, pn, base1, base2, d1, d2, fw, outs, outn, mns, mnn);
             } else {
-                const int nr = min(y + p.r_hi, p.h - 1) - max(y - p.r_lo, 0) + 1;
-#pragma unroll
-                for (int qq = 0; qq < 4; ++qq) {
-                    float ds[4], dn[4];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int t = 4 * qq + e;
-                        const int xg = xg0 + t;
-                        const int nc = min(xg + p.r_hi, p.w - 1) - max(xg - p.r_lo, 0) + 1;
-                        const uint32_t n = (uint32_t)(nr * nc);
-                        const uint32_t S1 = base1 + d1[t], S2 = base2 + d2[t];
-                        const unsigned long long V = (unsigned long long)n * S2 - (unsigned long long)S1 * S1;
-                        const float ff = byte_float(fw[qq], e);
-                        const float S1f = __uint2float_rn(S1);
-                        const float invn = rcp_approx(__uint2float_rn(n));
-                        const float sq = sqrt_approx(v_to_float(V));
-                        ds[e] = filter_n<BNZ_SAUVOLA>(ff, S1f, sq, invn, ps);
-                        dn[e] = filter_n<BNZ_NIBLACK>(ff, S1f, sq, invn, pn);
-                        mns = fminf(mns, xg < p.w ? fabsf(ds[e]) : INFINITY);
-                        mnn = fminf(mnn, xg < p.w ? fabsf(dn[e]) : INFINITY);
-                    }
-                    outs[qq] = mask_word(ds);
-                    outn[qq] = mask_word(dn);
-                }
+                decide_lane_border<BNZ_SAUVOLA>(ps, y, g.xg0, base1, base2, d1, d2, fw, outs, mns);
+                decide_lane_border<BNZ_NIBLACK>(pn, y, g.xg0, base1, base2, d1, d2, fw, outn, mnn);
             }
             // rare: values inside a rule's fp32 margin take that rule's exact path
-            if (mns < ps.E && active)
-                fix_margin<BNZ_SAUVOLA, KO, KI>(ps, C1, C2, ao, ai, base1, base2, fw, y, xg0, outs, nfb, nties_s);
-            if (mnn < pn.E && active)
-                fix_margin<BNZ_NIBLACK, KO, KI>(pn, C1, C2, ao, ai, base1, base2, fw, y, xg0, outn, nfb, nties_n);
-            if (active && xg0 < p.w) {
-                store_lane(ps, y, xg0, outs);
-                store_lane(pn, y, xg0, outn);
+            if ((mns < ps.E || mnn < pn.E) && g.active) {
+                uint32_t e1[L], e2[L];
+                lane_sums_again<KO, KI, WM8>(p, g, C1, e1, e2);
+                if (mns < ps.E)
+                    fix_margin<BNZ_SAUVOLA>(ps, y, g.xg0, base1, base2, e1, e2, fw, outs, nfb, nties_s);
+                if (mnn < pn.E)
+                    fix_margin<BNZ_NIBLACK>(pn, y, g.xg0, base1, base2, e1, e2, fw, outn, nfb, nties_n);
+            }
+            if (g.active && g.xg0 < p.w) {
+                store_lane(ps, y, g.xg0, outs);
+                store_lane(pn, y, g.xg0, outn);
             }
         }
         if (k + 2 < sg.nk)
@@ -324,6 +188,7 @@ int launch_dual(const uint8_t *d_src, size_t src_pitch, int h, int w, int ch, in
     pn.omk = dn.omk;
     pn.kR = dn.kR;
     pn.E = dn.E;
+    pn.Tdf = dn.Tdf;
     pn.kh = dn.kh;
     pn.kl = dn.kl;
     pn.c1h = dn.c1h;

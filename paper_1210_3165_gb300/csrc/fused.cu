@@ -109,9 +109,15 @@ bool layout(int ch, int W, int tw, int NSS, FusedPlan *pl)
     pl->o = (16 - (r_lo % 16)) % 16;
     const int need = pl->o + tw + W + 4;
     pl->SWP = (need + 15) / 16 * 16;
-    if (pl->SWP * ch > 256 * 8 || pl->SWP / 4 > NTPW)
+    if (pl->SWP * ch > 256 * 8)
         return false;
-    pl->RSW = (pl->SWP + 4 + 31) / 32 * 32; // words per column-sum row (swizzled, unpadded)
+    // column-sum groups read by the consumers: leaving streams 4j + i, entering
+    // streams 4j + wq + i (i <= 4, j < tw/16), first window below wq
+    pl->o4 = pl->o >> 2;
+    pl->wq = (W + (pl->o & 3)) >> 2;
+    pl->ngo = tw / 4 + pl->wq + 1;
+    if (pl->ngo > NTPW || pl->ngo > 4 * QG)
+        return false;
     const int D = (CH + W - 1) / CH;
     // ring: chunks in use (D + 1), one more because producers run a chunk ahead
     // of the consumers' centre rows, and for gray the chunks loaded ahead
@@ -127,7 +133,7 @@ bool layout(int ch, int W, int tw, int NSS, FusedPlan *pl)
     pl->off_stage = (uint32_t)off;
     off = round128(off + (size_t)pl->NSS * CH * pl->SWP * ch);
     pl->off_cb = (uint32_t)off;
-    off += (size_t)4 * CH * pl->RSW * 4; // 2 buffers x {c1, c2}
+    off += (size_t)4 * C2O * 4; // 2 buffers x {c1, c2} x CH rows x RS words
     pl->smem = off;
     return off <= (size_t)MAX_DYN_SMEM;
 }
@@ -160,10 +166,57 @@ float decision_margin(int rule, double k, double R)
     } else {
         em = 4.0 * u * m + u * 510.0 + ak * smax * (7.0 * u + e) + u * (510.0 + ak * smax);
     }
-    double E = 2.0 * em + 1e-6;
+    double E = 2.0 * em + 1e-6 + 2.0 * fp64_definition_error(rule, k, R);
     if (!(E < 1e30))
         E = 1e30;
     return (float)E;
+}
+
+// Absolute error of the fp64 sequence of the definition (m = S1/n, s =
+// sqrt(V)/n, then the rule left to right; V exact) against exact arithmetic:
+// each correctly rounded operation adds at most w = 2^-53 of its result, and
+// the results are bounded by 255 (m), 127.5 (s), T (t).  Counted generously.
+double fp64_definition_error(int rule, double k, double R)
+{
+    const double w = 1.0 / 9007199254740992.0;
+    const double m = 255.0, s = 127.5, ak = std::fabs(k);
+    if (rule == BNZ_SAUVOLA)
+        return 16.0 * w * (m + m * std::fabs(1.0 - k) + m * ak * (s / R + 1.0));
+    return 8.0 * w * (m + ak * s);
+}
+
+// Absolute error of decide_exact's double-float f - t (pairs of fp32, u^2 =
+// 2^-48 per operation): m = S1/n and sqrt(V)/n within 1 and 6 u^2 relative,
+// the constants 1-k, k, k/R within 1.1 u^2 relative, each product adds 6 u^2,
+// each sum 3 u^2 of its operands' magnitudes (cancellation allowed):
+//   Sauvola |t~ - t| <= 12 u^2 m|1-k| + 24 u^2 m s |k|/R
+//   Niblack |t~ - t| <= 4 u^2 m + 17 u^2 |k| s
+// plus 3 u^2 (255 + T) for f - t; doubled for the final rounding and margin.
+double double_float_error(int rule, double k, double R)
+{
+    const double u2 = 1.0 / 281474976710656.0;
+    const double m = 255.0, s = 127.5, ak = std::fabs(k);
+    double et, T;
+    if (rule == BNZ_SAUVOLA) {
+        et = 12.0 * u2 * m * std::fabs(1.0 - k) + 24.0 * u2 * m * s * ak / R;
+        T = m * std::fabs(1.0 - k) + m * s * ak / R;
+    } else {
+        et = 4.0 * u2 * m + 17.0 * u2 * ak * s;
+        T = m + ak * s;
+    }
+    return 2.0 * (et + 3.0 * u2 * (255.0 + T));
+}
+
+// A pixel whose double-float |f - t| exceeds 1e-9 + both error bounds is no tie
+// of the fp64 definition and has the same sign there; the others run the fp64
+// sequence.  Never below 1.2e-9; rounded up to fp32.
+float double_float_cut(int rule, double k, double R)
+{
+    double c = 1e-9 + double_float_error(rule, k, R) + fp64_definition_error(rule, k, R);
+    c = std::max(c, 1.2e-9) * (1.0 + 1e-6);
+    if (!(c < 1e30))
+        c = 1e30;
+    return (float)c;
 }
 
 void fill_decision_params(FusedParams *p, int h, int w, int W, int rule, double k, double R)
@@ -188,6 +241,7 @@ void fill_decision_params(FusedParams *p, int h, int w, int W, int rule, double 
     p->omk = (float)(1.0 - k);
     p->kR = (float)(k / R);
     p->E = decision_margin(rule, k, R);
+    p->Tdf = double_float_cut(rule, k, R);
     auto split = [](double x, float *hi, float *lo) {
         *hi = (float)x;
         *lo = (float)(x - (double)*hi);
@@ -279,7 +333,9 @@ void fill_fused_params(FusedParams *p, const FusedPlan &pl, int h, int w, int W,
     p->NS = pl.NS;
     p->NSS = pl.NSS;
     p->SWP = pl.SWP;
-    p->RSW = pl.RSW;
+    p->o4 = pl.o4;
+    p->wq = pl.wq;
+    p->ngo = pl.ngo;
     p->ring_rows = pl.ring_rows;
     p->tiles_x = pl.tiles_x;
     p->off_ring = pl.off_ring;

@@ -35,13 +35,14 @@ struct FusedPlan {
     int NS;         // ring slots (chunks) of gray rows in shared memory
     int NSS;        // staging slots for RGB chunks (0 for gray)
     int SWP;        // span width in pixels: one TMA box of SWP*channels bytes per chunk
-    int RSW;        // row stride (32-bit words) of each column-sum array, a multiple of 32
     int ring_rows;  // NS * CH
     int o;          // span start offset: (x0 - r_lo) - floor16(x0 - r_lo)
+    int o4, wq;     // o >> 2; (W + (o & 3)) >> 2: group of the entering stream's first column
+    int ngo;        // 4-column groups whose column sums the consumers read (from group o4 on)
     int tiles_x;    // strips across the image
     int grid;       // persistent CTAs
     int rows_per_cta;
-    uint32_t off_ring, off_stage, off_cb; // column sums: 2 buffers x {c1, c2} x CH rows x RSW words
+    uint32_t off_ring, off_stage, off_cb; // column sums: 2 buffers x {c1, c2} x CH rows x RS words
     size_t smem;
 };
 
@@ -52,7 +53,8 @@ struct FusedParams {
     unsigned int *err_flag; // library-owned device word, counts CTAs that gave up
     int h, w, W, r_lo, r_hi, o;
     int y_lo, y_hi;  // output rows [y_lo, y_hi) of this launch (the window clips at 0 and h)
-    int TW, CH, NS, NSS, SWP, RSW, ring_rows, tiles_x;
+    int TW, CH, NS, NSS, SWP, ring_rows, tiles_x;
+    int o4, wq, ngo; // column-sum groups: origin, entering-stream offset, count (see FusedPlan)
     uint32_t off_ring, off_stage, off_cb;
     int packed;     // 1: one bit per pixel
     int vec_ok;     // dst and dst_pitch 16-byte aligned
@@ -66,6 +68,9 @@ struct FusedParams {
     float E;           // proven bound on |d32 - (f - t)|, with safety factor
     // double-float constants of the second stage: k, 1-k, k/R as hi + lo
     float kh, kl, c1h, c1l, c2h, c2l;
+    // the second stage decides by the sign of its f - t when |f - t| > Tdf =
+    // 1e-9 + its own error bound + the fp64 definition's (double_float_cut)
+    float Tdf;
     long long timeout_cycles;
 };
 
@@ -98,6 +103,11 @@ constexpr double kRcpApproxRelErr = 1.0 / (1 << 22);
 
 // fp32 decision margin E (see fused.cu for the derivation).
 float decision_margin(int rule, double k, double R);
+// Error bounds, for m <= 255 and s <= 127.5, of the double-float evaluation of
+// f - t and of the fp64 definition's t; and the cut Tdf built from them.
+double double_float_error(int rule, double k, double R);
+double fp64_definition_error(int rule, double k, double R);
+float double_float_cut(int rule, double k, double R);
 
 // Fills the geometry and threshold constants of `p` shared by every kernel
 // that takes the Eq. 3 decision (window radii, k, R, fp32 constants, margin).

@@ -1,6 +1,7 @@
 // segment.cuh -- device code of the fused tile kernel shared by the
-// single-page launch (fused.cu) and the batched persistent launch (batch.cu):
-// one strip segment processed by 8 producer and 8 consumer warps.
+// single-page launch (fused.cu), the batched persistent launch (batch.cu) and
+// the two-rule launch (dual.cu): one strip segment processed by 8 producer and
+// 8 consumer warps.
 #pragma once
 #include <cstdint>
 
@@ -25,9 +26,19 @@ constexpr int CH = 8;               // rows per chunk (TMA box height, one consu
 constexpr int kLeadGray = 3;        // gray: chunks loaded ahead of the ones in use
 constexpr int MAX_DYN_SMEM = 232448 - 1024; // 227 KB opt-in limit, minus slack
 
-// Shared memory holds rows row-major: the gray ring (ring_rows x SWP bytes)
-// and, for RGB, the staging slots (CH x 3*SWP bytes each), each chunk of rows
-// one TMA box of 8-byte elements.
+// Column-sum rows.  Column c of a strip's span belongs to the 4-column group
+// g = (c >> 2) - o4, counted from the group holding the first column of the
+// leaving stream (span column o).  Group g is stored at group position
+// (g & 3) * QG + (g >> 2): four interleaved quarters of QG groups, so that
+//   - the consumers' 128-bit loads (lane j reads groups 4j + i, the same i in
+//     every lane) hit consecutive positions: no bank conflict, and every
+//     offset is a compile-time constant plus 16 bytes per lane;
+//   - the producers' 128-bit stores (thread g writes group g) fall on eight
+//     distinct 16-byte bank groups per phase, because QG = 2 (mod 4);
+//   - column c + 32 sits 8 words after column c (first-window loop).
+constexpr int QG = 42;              // groups per quarter; QG % 4 == 2
+constexpr int RS = 16 * QG;         // words per column-sum row
+constexpr int C2O = CH * RS;        // words from the c1 rows of a buffer to its c2 rows
 
 __device__ __forceinline__ void bar_sync(int id, int n)
 {
@@ -51,53 +62,44 @@ __device__ __forceinline__ uint32_t byte_dyn(uint32_t w, int j)
     return (w >> (8 * j)) & 0xffu;
 }
 
-// Byte j of w as a float, exactly: one permute forms the bit pattern
-// 0x4B0000bb (= 2^23 + b) and one subtraction removes 2^23, instead of a
-// byte extract and an integer-to-float conversion.
-__device__ __forceinline__ float byte_float(uint32_t w, int j)
+// Minus byte J of w as a float, exactly: one permute forms the bit pattern
+// 0xCB0000bb (= -(2^23 + b)); adding 2^23 (paired, two pixels per
+// instruction) leaves -b.
+template <int J>
+__device__ __forceinline__ float neg_byte_pattern(uint32_t w)
 {
-    return __fsub_rn(__uint_as_float(prmt(w, 0x4B000000u, 0x7440u + (uint32_t)j)), 8388608.0f);
+    return __uint_as_float(prmt(w, 0xCB000000u, 0x7440u + J));
 }
 
-// Word offset of 4-column group g in a column-sum row.  The groups are
-// XOR-swizzled within aligned blocks of four, g ^ ((g >> 3) & 3), so that
-// both access patterns hit eight distinct 16-byte bank groups per phase: the
-// producers' 128-bit stores (consecutive groups, one per thread) and the
-// consumers' 128-bit loads (groups four apart, one per lane, any offset).
-__device__ __forceinline__ int gpos(int g)
+// Eq. 1 for one pixel, x = 299 r + 587 g + 114 b + 500 formed by two 16x8-bit
+// dot products over the bytes where r, g, b sit, then q = floor(x / 1000) as
+// the high word of x * ceil(2^32 / 1000): division by a constant through a
+// multiply-high reciprocal (Granlund and Montgomery), exact because
+// x * (1000 * ceil(2^32/1000) - 2^32) < 2^32 for x < 6.1e6 (x <= 255500 here).
+__device__ __forceinline__ uint32_t div1000(uint32_t x)
 {
-    return 4 * (g ^ ((g >> 3) & 3));
-}
-
-// Word offset of span column c.
-__device__ __forceinline__ int cpos(int c)
-{
-    return gpos(c >> 2) + (c & 3);
-}
-
-__device__ __forceinline__ uint4 ld_group(const uint32_t *C, int a) // columns 4a..4a+3
-{
-    return *reinterpret_cast<const uint4 *>(C + gpos(a));
-}
-
-// Eq. 1 for one pixel whose r, g, b are bytes 0..2 of px (byte 3 ignored):
-// x = 299 r + 587 g + 114 b + 500 = (43 r + 75 g + 114 b) + 256 (r + 2 g) + 500,
-// q = floor(x / 1000) = high word of x * ceil(2^32 / 1000) (exact for x < 6.1e6).
-__device__ __forceinline__ uint32_t gray1(uint32_t px)
-{
-    const uint32_t hi = __dp4a(px, 0x00000201u, 0u);
-    const uint32_t x = __dp4a(px, 0x00724B2Bu, hi * 256u + 500u);
     return __umulhi(x, 4294968u);
 }
 
-// Four gray pixels from 12 interleaved bytes r0 g0 b0 r1 | g1 b1 r2 g2 | b2 r3 g3 b3.
+// Eq. 1 for one pixel whose r, g, b are bytes 0..2 of px (byte 3 ignored).
+__device__ __forceinline__ uint32_t gray1(uint32_t px)
+{
+    return div1000(__dp2a_hi(0x00000072u, px, __dp2a_lo(0x024B012Bu, px, 500u)));
+}
+
+// Four gray pixels from 12 interleaved bytes r0 g0 b0 r1 | g1 b1 r2 g2 | b2 r3 g3 b3,
+// packed into one word (pixel i in byte i).  Each pixel's three bytes are
+// reached where they lie, by the low or high byte pair of a word, so no
+// realignment is needed.
 __device__ __forceinline__ uint32_t gray4(uint32_t w0, uint32_t w1, uint32_t w2)
 {
-    const uint32_t g0 = gray1(w0);
-    const uint32_t g1 = gray1(__funnelshift_r(w0, w1, 24));
-    const uint32_t g2 = gray1(__funnelshift_r(w1, w2, 16));
-    const uint32_t g3 = gray1(w2 >> 8);
-    return g0 | (g1 << 8) | (g2 << 16) | (g3 << 24);
+    const uint32_t x0 = __dp2a_hi(0x00000072u, w0, __dp2a_lo(0x024B012Bu, w0, 500u));  // r0 g0 | b0
+    const uint32_t x1 = __dp2a_lo(0x0072024Bu, w1, __dp2a_hi(0x012B0000u, w0, 500u));  // r1 | g1 b1
+    const uint32_t x2 = __dp2a_lo(0x00000072u, w2, __dp2a_hi(0x024B012Bu, w1, 500u));  // r2 g2 | b2
+    const uint32_t x3 = __dp2a_hi(0x0072024Bu, w2, __dp2a_lo(0x012B0000u, w2, 500u));  // r3 | g3 b3
+    const uint32_t lo = prmt(div1000(x0), div1000(x1), 0x0040u);
+    const uint32_t hi = prmt(div1000(x2), div1000(x3), 0x0040u);
+    return prmt(lo, hi, 0x5410u);
 }
 
 struct Segment {
@@ -121,12 +123,6 @@ __device__ __forceinline__ Segment make_segment(const FusedParams &p, long long 
     sg.nk = (sg.th_eff + CH - 1) / CH;
     return sg;
 }
-
-// One segment with the 16 warps split into producers and consumers.
-template <int CIN, int RULE, int WM8>
-__device__ __forceinline__ void run_segment(const CUtensorMap *tmap, const FusedParams &p, const Segment &sg,
-                                            uint8_t *smem, uint64_t &phase, uint64_t &ephase, uint64_t &eused,
-                                            uint32_t &nfb, uint32_t &nties, volatile int *s_abort);
 
 // ---------------------------------------------------------------------------
 // producers: TMA ring, RGB->gray, column sums (a1-a3)
@@ -182,16 +178,17 @@ __device__ __forceinline__ void produce(const CUtensorMap *tmap, const FusedPara
         return;
     }
 
-    // ---- warps 0-6: RGB->gray (a2) and column sums (a3), 4 columns per thread
-    const bool owner = tid < (SWP >> 2);
-    const int gcol = tid * 4;
-    const int gofs = cpos(gcol);
-    uint8_t *gbase = ring + gcol;              // this thread's 4 columns, ring row 0
-    const uint8_t *sbase = stage + 3 * gcol;   // the same columns in staging slot 0
+    // ---- warps 0-6: RGB->gray (a2) and column sums (a3) of one 4-column
+    // group per thread: group g = tid, span columns scol .. scol + 3.
+    const bool owner = tid < p.ngo;
+    const int scol = 4 * (tid + p.o4);
+    const int gofs = 4 * ((tid & 3) * QG + (tid >> 2)); // word offset of the group in a column-sum row
+    uint8_t *gbase = ring + scol;              // this thread's 4 columns, ring row 0
+    const uint8_t *sbase = stage + 3 * scol;   // the same columns in staging slot 0
     const int ring_bytes = p.ring_rows * SWP;
     // columns at or right of the image edge must read as zero; the last 8-byte
     // element of a row may carry up to 7 padding bytes past the edge
-    const int xg = sg.xs + gcol;
+    const int xg = sg.xs + scol;
     uint32_t keep = 0xffffffffu;
     if (xg + 4 > p.w)
         keep = xg >= p.w ? 0u : (0xffffffffu >> (8 * (4 - (p.w - xg))));
@@ -300,8 +297,7 @@ __device__ __forceinline__ void produce(const CUtensorMap *tmap, const FusedPara
         const int rows_k = min(CH, sg.th_eff - k * CH);
         if (good && owner) {
             const bool last = (k + 1 == sg.nk);
-            uint32_t *C1 = cb + (size_t)(2 * b) * CH * p.RSW + gofs;
-            uint32_t *C2 = C1 + (size_t)CH * p.RSW;
+            uint32_t *C1 = cb + (size_t)(2 * b) * C2O + gofs;
             uint32_t vi[CH], vo[CH];
 #pragma unroll
             for (int r = 0; r < CH; ++r) { // load first, then add: no smem latency per row
@@ -314,18 +310,17 @@ __device__ __forceinline__ void produce(const CUtensorMap *tmap, const FusedPara
 #pragma unroll
             for (int r = 0; r < CH; ++r) {
                 if (r < rows_k) {
-                    *reinterpret_cast<uint4 *>(C1 + r * p.RSW) = make_uint4(c1[0], c1[1], c1[2], c1[3]);
-                    *reinterpret_cast<uint4 *>(C2 + r * p.RSW) = make_uint4(c2[0], c2[1], c2[2], c2[3]);
+                    *reinterpret_cast<uint4 *>(C1 + r * RS) = make_uint4(c1[0], c1[1], c1[2], c1[3]);
+                    *reinterpret_cast<uint4 *>(C1 + C2O + r * RS) = make_uint4(c2[0], c2[1], c2[2], c2[3]);
                     if (!(last && r + 1 == rows_k)) { // slide to the next row
                         const uint32_t a = vi[r], o = vo[r];
-                        c1[0] = c1[0] + byte_at<0>(a) - byte_at<0>(o);
-                        c1[1] = c1[1] + byte_at<1>(a) - byte_at<1>(o);
-                        c1[2] = c1[2] + byte_at<2>(a) - byte_at<2>(o);
-                        c1[3] = c1[3] + byte_at<3>(a) - byte_at<3>(o);
-                        c2[0] = c2[0] + byte_at<0>(a) * byte_at<0>(a) - byte_at<0>(o) * byte_at<0>(o);
-                        c2[1] = c2[1] + byte_at<1>(a) * byte_at<1>(a) - byte_at<1>(o) * byte_at<1>(o);
-                        c2[2] = c2[2] + byte_at<2>(a) * byte_at<2>(a) - byte_at<2>(o) * byte_at<2>(o);
-                        c2[3] = c2[3] + byte_at<3>(a) * byte_at<3>(a) - byte_at<3>(o) * byte_at<3>(o);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const uint32_t aj = __byte_perm(a, 0u, 0x4440u | j);
+                            const uint32_t oj = __byte_perm(o, 0u, 0x4440u | j);
+                            c1[j] = c1[j] + aj - oj;
+                            c2[j] = c2[j] + aj * aj - oj * oj;
+                        }
                     }
                 }
             }
@@ -348,27 +343,39 @@ __device__ __forceinline__ void produce(const CUtensorMap *tmap, const FusedPara
         release_to(sg.nchk);
 }
 
+// ---------------------------------------------------------------------------
+// consumers: horizontal sums (a4)
+// ---------------------------------------------------------------------------
+
 // A lane's 16 outputs: running offsets d[t] = S(x0 + t) - S(x0) of the window
-// sums (leaving stream from column group ao, entering from ai, realigned at
-// compile time by KO / KI), and their total a = S(x0 + 16) - S(x0).
-template <int KO, int KI>
-__device__ __forceinline__ void lane_deltas(const uint32_t *C1, const uint32_t *C2, int ao, int ai, uint32_t (&d1)[L],
+// sums and their total a = S(x0 + 16) - S(x0), from the leaving stream (groups
+// 4j + i of the lane, Lb = the c1 row + 4j words) and the entering stream
+// (groups 4j + wq + i, Eb = the c1 row + 4(j + (wq >> 2)) words, WR = wq & 3),
+// realigned at compile time by KO and KI (first column within its group).
+template <int KO, int KI, int WR>
+__device__ __forceinline__ void lane_deltas(const uint32_t *Lb, const uint32_t *Eb, uint32_t (&d1)[L],
                                             uint32_t (&d2)[L], uint32_t &a1, uint32_t &a2)
 {
+    auto lo = [&](int i, int arr) {
+        return *reinterpret_cast<const uint4 *>(Lb + arr * C2O + 4 * ((i & 3) * QG + (i >> 2)));
+    };
+    auto li = [&](int i, int arr) {
+        return *reinterpret_cast<const uint4 *>(Eb + arr * C2O + 4 * (((WR + i) & 3) * QG + ((WR + i) >> 2)));
+    };
     a1 = 0;
     a2 = 0;
-    uint4 o1 = ld_group(C1, ao), o2 = ld_group(C2, ao);
-    uint4 i1 = ld_group(C1, ai), i2 = ld_group(C2, ai);
+    uint4 o1 = lo(0, 0), o2 = lo(0, 1);
+    uint4 i1 = li(0, 0), i2 = li(0, 1);
 #pragma unroll
     for (int j = 0; j < L / 4; ++j) {
         uint4 o1n = make_uint4(0, 0, 0, 0), o2n = o1n, i1n = o1n, i2n = o1n;
         if (KO != 0 || j + 1 < L / 4) {
-            o1n = ld_group(C1, ao + j + 1);
-            o2n = ld_group(C2, ao + j + 1);
+            o1n = lo(j + 1, 0);
+            o2n = lo(j + 1, 1);
         }
         if (KI != 0 || j + 1 < L / 4) {
-            i1n = ld_group(C1, ai + j + 1);
-            i2n = ld_group(C2, ai + j + 1);
+            i1n = li(j + 1, 0);
+            i2n = li(j + 1, 1);
         }
         const uint32_t vo1[8] = {o1.x, o1.y, o1.z, o1.w, o1n.x, o1n.y, o1n.z, o1n.w};
         const uint32_t vo2[8] = {o2.x, o2.y, o2.z, o2.w, o2n.x, o2n.y, o2n.z, o2n.w};
@@ -388,209 +395,351 @@ __device__ __forceinline__ void lane_deltas(const uint32_t *C1, const uint32_t *
     }
 }
 
+// Geometry of a consumer lane that stays fixed over a segment.
+struct LaneGeo {
+    int lane, ii;       // lane, and this warp's row within each chunk
+    bool active;        // lane * 16 < strip width (256-wide strips leave lanes 16..31 idle)
+    int xg0;            // image column of the lane's first output
+    bool xclip;         // some window of the lane leaves the image horizontally
+    int fo;             // word offset of first-window column KO + lane in a column-sum row
+    int fcol;           // span column of the lane's first centre pixel (a multiple of 16)
+};
+
+template <int KO>
+__device__ __forceinline__ LaneGeo lane_geo(const FusedParams &p, const Segment &sg)
+{
+    LaneGeo g;
+    const int q = threadIdx.x - NTP;
+    g.lane = q & 31;
+    g.ii = q >> 5;
+    g.active = g.lane * L < p.TW;
+    g.xg0 = sg.x0 + g.lane * L;
+    g.xclip = g.xg0 < p.r_lo || g.xg0 + L - 1 + p.r_hi > p.w - 1;
+    const int c = KO + g.lane; // first-window column relative to the group origin
+    g.fo = 4 * (((c >> 2) & 3) * QG + (c >> 4)) + (c & 3);
+    g.fcol = g.active ? g.lane * L + p.o + p.r_lo : 0;
+    return g;
+}
+
+// Exact window sums of the lane's 16 pixels in one output row: S1 = base1 +
+// d1[t], S2 = base2 + d2[t] (mod 2^32; S1 < 2^24 and S2 < 2^32 for W <= 255).
+// C1 = the row's c1 column sums (c2 at C1 + C2O).
+template <int KO, int KI, int WM8>
+__device__ __forceinline__ void row_sums(const FusedParams &p, const LaneGeo &g, const uint32_t *C1,
+                                         uint32_t (&d1)[L], uint32_t (&d2)[L], uint32_t &base1, uint32_t &base2)
+{
+    // wq = (W + KO) >> 2; for a given W mod 8 its low two bits take one of two
+    // values, chosen by bit 3 of W
+    constexpr int WR0 = ((WM8 + KO) >> 2) & 3;
+    constexpr int WR1 = (WR0 + 2) & 3;
+    uint32_t a1 = 0, a2 = 0;
+    if (g.active) {
+        const uint32_t *Lb = C1 + 4 * g.lane;
+        const uint32_t *Eb = Lb + 4 * (p.wq >> 2);
+        if (p.W & 8)
+            lane_deltas<KO, KI, WR1>(Lb, Eb, d1, d2, a1, a2);
+        else
+            lane_deltas<KO, KI, WR0>(Lb, Eb, d1, d2, a1, a2);
+    } else {
+#pragma unroll
+        for (int t = 0; t < L; ++t)
+            d1[t] = d2[t] = 0u;
+    }
+    // the window of the strip's first output: relative columns [KO, KO + W)
+    uint32_t s1 = 0, s2 = 0;
+    for (int c = g.lane, off = g.fo; c < p.W; c += 32, off += 8) {
+        s1 += C1[off];
+        s2 += C1[C2O + off];
+    }
+    s1 = __reduce_add_sync(0xffffffffu, s1);
+    s2 = __reduce_add_sync(0xffffffffu, s2);
+    uint32_t x1 = a1, x2 = a2;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t t1 = __shfl_up_sync(0xffffffffu, x1, off);
+        const uint32_t t2 = __shfl_up_sync(0xffffffffu, x2, off);
+        if (g.lane >= off) {
+            x1 += t1;
+            x2 += t2;
+        }
+    }
+    base1 = s1 + x1 - a1;
+    base2 = s2 + x2 - a2;
+}
+
+// The same sums again (after the fast decision let go of them), for the rare
+// lanes with pixels inside the fp32 margin.
+template <int KO, int KI, int WM8>
+__device__ __forceinline__ void lane_sums_again(const FusedParams &p, const LaneGeo &g, const uint32_t *C1,
+                                                uint32_t (&e1)[L], uint32_t (&e2)[L])
+{
+    constexpr int WR0 = ((WM8 + KO) >> 2) & 3;
+    constexpr int WR1 = (WR0 + 2) & 3;
+    uint32_t t1, t2;
+    const uint32_t *Lb = C1 + 4 * g.lane;
+    const uint32_t *Eb = Lb + 4 * (p.wq >> 2);
+    if (p.W & 8)
+        lane_deltas<KO, KI, WR1>(Lb, Eb, e1, e2, t1, t2);
+    else
+        lane_deltas<KO, KI, WR0>(Lb, Eb, e1, e2, t1, t2);
+}
+
 // ---------------------------------------------------------------------------
-// consumers: horizontal sums, threshold, output (a4-a7)
+// consumers: m, s, t and Eq. 3 (a5, a6)
 // ---------------------------------------------------------------------------
+
+// Per-pixel statistics of the fp32 filter for an unclipped window (n = W*W):
+// sqrt(V) by sqrt.approx from V = n*S2 - S1^2, exact in 64 bits and rounded to
+// fp32 (hi word exact, lo word rounded, one more rounding in the fma: relative
+// error <= 2u), and S1 as fp32 (exact, S1 < 2^24).
+__device__ __forceinline__ void stats_int(uint32_t base1, int nb1, long long NB2, int nW, uint32_t d1, uint32_t d2,
+                                          float &s1f, float &sq)
+{
+    const uint32_t S1 = base1 + d1;
+    const int nS1 = nb1 - (int)d1;                              // -S1
+    const long long P = NB2 + (long long)nW * (int)d2;          // n * S2
+    const long long V = P + (long long)(int)S1 * nS1;           // n * S2 - S1^2 >= 0
+    const float vf = __fmaf_rn(__uint2float_rn((uint32_t)((unsigned long long)V >> 32)), 4294967296.0f,
+                               __uint2float_rn((uint32_t)V));
+    sq = sqrt_approx(vf);
+    s1f = __uint2float_rn(S1);
+}
+
+// Two pixels' fp32 filters, nd ~ t - f (= -d), for an unclipped window:
+//   Sauvola nd = S1 * (omkn + kRn2 * sqrt(V)) - f
+//   Niblack nd = S1 * invn + (kn * sqrt(V) - f)
+template <int RULE>
+__device__ __forceinline__ float2 filter2_int(float2 s1f, float2 sq, float2 nff, const FusedParams &p)
+{
+    if (RULE == BNZ_SAUVOLA) {
+        const float2 x = __ffma2_rn(make_float2(p.kRn2, p.kRn2), sq, make_float2(p.omkn, p.omkn));
+        return __ffma2_rn(s1f, x, nff);
+    }
+    const float2 y = __ffma2_rn(make_float2(p.kn, p.kn), sq, nff);
+    return __ffma2_rn(s1f, make_float2(p.invn, p.invn), y);
+}
+
+// Byte i of the result = 0xFF where nd[i] has its sign bit set (t < f: white),
+// 0x00 otherwise; nd = +-0 lies inside every margin and is re-decided.
+__device__ __forceinline__ uint32_t sign_bytes(float n0, float n1, float n2, float n3)
+{
+    const uint32_t lo = prmt(__float_as_uint(n0), __float_as_uint(n1), 0xFBu);
+    const uint32_t hi = prmt(__float_as_uint(n2), __float_as_uint(n3), 0xFBu);
+    return prmt(lo, hi, 0x5410u);
+}
+
+// -b as fp32 for the four bytes of w, paired
+__device__ __forceinline__ void neg_bytes(uint32_t w, float2 &n01, float2 &n23)
+{
+    const float2 bias = make_float2(8388608.0f, 8388608.0f);
+    n01 = __fadd2_rn(make_float2(neg_byte_pattern<0>(w), neg_byte_pattern<1>(w)), bias);
+    n23 = __fadd2_rn(make_float2(neg_byte_pattern<2>(w), neg_byte_pattern<3>(w)), bias);
+}
+
+// Fast decision of the lane's 16 pixels when every window of the warp is W x W.
+// outw: byte t of word t/4 = 255 (white) or 0; mn: smallest |nd|.
+template <int RULE>
+__device__ __forceinline__ void decide_lane_int(const FusedParams &p, uint32_t base1, uint32_t base2,
+                                                const uint32_t (&d1)[L], const uint32_t (&d2)[L],
+                                                const uint32_t (&fw)[4], uint32_t (&outw)[4], float &mn)
+{
+    const long long NB2 = (long long)((unsigned long long)p.nW * base2);
+    const int nb1 = -(int)base1;
+    const int nW = (int)p.nW;
+#pragma unroll
+    for (int qq = 0; qq < 4; ++qq) {
+        float2 nf01, nf23;
+        neg_bytes(fw[qq], nf01, nf23);
+        float s[4], q[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            stats_int(base1, nb1, NB2, nW, d1[4 * qq + e], d2[4 * qq + e], s[e], q[e]);
+        const float2 a = filter2_int<RULE>(make_float2(s[0], s[1]), make_float2(q[0], q[1]), nf01, p);
+        const float2 c = filter2_int<RULE>(make_float2(s[2], s[3]), make_float2(q[2], q[3]), nf23, p);
+        mn = fminf(mn, fminf(fminf(fabsf(a.x), fabsf(a.y)), fminf(fabsf(c.x), fabsf(c.y))));
+        outw[qq] = sign_bytes(a.x, a.y, c.x, c.y);
+    }
+}
+
+// The general filter for one pixel with its own (clipped) count n, as nd = -d.
+template <int RULE>
+__device__ __forceinline__ float filter_general(uint32_t f, uint32_t n, uint32_t S1, uint32_t S2,
+                                                const FusedParams &p)
+{
+    const unsigned long long V = (unsigned long long)n * S2 - (unsigned long long)S1 * S1;
+    const float sq = sqrt_approx(v_to_float(V));
+    const float ff = __uint2float_rn(f), S1f = __uint2float_rn(S1);
+    const float d = (n == p.nW) ? filter_int<RULE>(ff, S1f, sq, p)
+                                : filter_n<RULE>(ff, S1f, sq, rcp_approx(__uint2float_rn(n)), p);
+    return -d;
+}
+
+// Clipped count of the window around column xg: n = nr * nc.
+__device__ __forceinline__ uint32_t clipped_n(const FusedParams &p, int nr, int xg)
+{
+    const int nc = min(xg + p.r_hi, p.w - 1) - max(xg - p.r_lo, 0) + 1;
+    return (uint32_t)(nr * nc);
+}
+
+__device__ __forceinline__ int clipped_rows(const FusedParams &p, int y)
+{
+    return min(y + p.r_hi, p.h - 1) - max(y - p.r_lo, 0) + 1;
+}
+
+// Fast decision of the lane's 16 pixels in a warp that touches the image
+// border: each pixel with its own clipped count.
+template <int RULE>
+__device__ __forceinline__ void decide_lane_border(const FusedParams &p, int y, int xg0, uint32_t base1,
+                                                   uint32_t base2, const uint32_t (&d1)[L], const uint32_t (&d2)[L],
+                                                   const uint32_t (&fw)[4], uint32_t (&outw)[4], float &mn)
+{
+    const int nr = clipped_rows(p, y);
+#pragma unroll
+    for (int qq = 0; qq < 4; ++qq) {
+        float nd[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int t = 4 * qq + e;
+            const int xg = xg0 + t;
+            nd[e] = filter_general<RULE>(byte_dyn(fw[qq], e), clipped_n(p, nr, xg), base1 + d1[t], base2 + d2[t], p);
+            mn = fminf(mn, xg < p.w ? fabsf(nd[e]) : INFINITY);
+        }
+        outw[qq] = sign_bytes(nd[0], nd[1], nd[2], nd[3]);
+    }
+}
+
+// The pixels of the lane inside the fp32 margin, decided exactly (double-float,
+// then fp64 near ties) and patched into outw.  Any pixel whose true |f - t| is
+// at most the filters' error bound has |nd| < E = 2 * bound + 1e-6 in every
+// filter, so this general recomputation flags every pixel the fast filter
+// might have decided wrongly, whichever fast filter ran.
+template <int RULE>
+__device__ __forceinline__ void fix_margin(const FusedParams &p, int y, int xg0, uint32_t base1, uint32_t base2,
+                                           const uint32_t (&e1)[L], const uint32_t (&e2)[L],
+                                           const uint32_t (&fw)[4], uint32_t (&outw)[4], uint32_t &nfb,
+                                           uint32_t &nties)
+{
+    const int nr = clipped_rows(p, y);
+    uint32_t amask = 0;
+#pragma unroll
+    for (int t = 0; t < L; ++t) {
+        const int xg = xg0 + t;
+        const float nd = filter_general<RULE>(byte_dyn(fw[t >> 2], t & 3), clipped_n(p, nr, xg), base1 + e1[t],
+                                              base2 + e2[t], p);
+        if (xg < p.w && fabsf(nd) < p.E)
+            amask |= 1u << t;
+    }
+    uint32_t white = 0; // bit t: the exact decision of pixel t is 255
+    for (uint32_t m = amask; m; m &= m - 1) {
+        const int t = __ffs(m) - 1;
+        // register arrays are indexed with compile-time constants only
+        uint32_t S1 = base1, S2 = base2, word = fw[0];
+#pragma unroll
+        for (int u = 0; u < L; ++u)
+            if (u == t) {
+                S1 += e1[u];
+                S2 += e2[u];
+            }
+#pragma unroll
+        for (int qq = 1; qq < 4; ++qq)
+            if ((t >> 2) == qq)
+                word = fw[qq];
+        const uint32_t r = decide_exact<RULE>(byte_dyn(word, t & 3), clipped_n(p, nr, xg0 + t), S1, S2, p);
+        ++nfb;
+        nties += (r >> 9) & 1u;
+        white |= (r & 1u) << t;
+    }
+#pragma unroll
+    for (int qq = 0; qq < 4; ++qq) { // bits 4qq..4qq+3 -> bytes 0..3 of word qq
+        const uint32_t mm = ((((amask >> (4 * qq)) & 15u) * 0x00204081u) & 0x01010101u) * 0xffu;
+        const uint32_t vv = ((((white >> (4 * qq)) & 15u) * 0x00204081u) & 0x01010101u) * 0xffu;
+        outw[qq] = (outw[qq] & ~mm) | (vv & mm);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// consumers: output (a7)
+// ---------------------------------------------------------------------------
+
+// The lane's 16 outputs of row y into p.dst: byte mask or packed bits.
+__device__ __forceinline__ void store_lane(const FusedParams &p, int y, int xg0, const uint32_t (&outw)[4])
+{
+    if (!p.packed) {
+        uint8_t *drow = p.dst + (size_t)y * p.dst_pitch + xg0;
+        if (p.vec_ok && xg0 + L <= p.w) {
+            *reinterpret_cast<uint4 *>(drow) = make_uint4(outw[0], outw[1], outw[2], outw[3]);
+        } else {
+            for (int t = 0; t < L && xg0 + t < p.w; ++t)
+                drow[t] = (uint8_t)byte_dyn(outw[t >> 2], t & 3);
+        }
+    } else {
+        uint32_t bits = 0; // bit t <-> pixel xg0 + t: the msb of each byte
+#pragma unroll
+        for (int qq = 0; qq < 4; ++qq)
+            bits |= ((((outw[qq] >> 7) & 0x01010101u) * 0x01020408u) >> 24) << (4 * qq);
+        const int valid = p.w - xg0;
+        if (valid < L)
+            bits &= (1u << valid) - 1u;
+        uint8_t *drow = p.dst + (size_t)y * p.dst_pitch + (xg0 >> 3);
+        drow[0] = (uint8_t)(bits & 0xffu);
+        if (valid > 8)
+            drow[1] = (uint8_t)(bits >> 8);
+    }
+}
+
+// Compile-time alignment of the two horizontal streams.  o = (-r_lo) mod 16
+// and r_lo = W/2: the leaving stream starts KO columns into its group and the
+// entering stream (W columns later) KI columns into its group.
+template <int WM8>
+struct Align {
+    static constexpr int KO = (4 - ((WM8 >> 1) & 3)) & 3;
+    static constexpr int KI = (KO + WM8) & 3;
+};
+
 template <int CIN, int RULE, int WM8>
 __device__ __forceinline__ void consume(const FusedParams &p, const Segment &sg, uint8_t *smem, uint32_t &nfb,
                                         uint32_t &nties, volatile int *s_abort)
 {
+    constexpr int KO = Align<WM8>::KO, KI = Align<WM8>::KI;
     const int SWP = p.SWP;
-    // o = (-r_lo) mod 16 and r_lo = W/2: the misalignments of the leaving
-    // (span column o + x) and entering (o + W + x) streams depend on W mod 8
-    constexpr int KO = (4 - ((WM8 >> 1) & 3)) & 3;
-    constexpr int KI = (KO + WM8) & 3;
     const uint8_t *ring = smem + p.off_ring;
     const uint32_t *cb = reinterpret_cast<const uint32_t *>(smem + p.off_cb);
-    const int q = threadIdx.x - NTP;
-    const int lane = q & 31, ii = q >> 5; // this warp's row within each chunk
-    const int W = p.W;
-    const bool active = lane * L < p.TW; // 256-wide strips leave lanes 16..31 idle
-    // centre pixels of this lane's 16 outputs start at span column lane*16 + o + r_lo (a multiple of 16)
-    const int fcol = active ? lane * L + p.o + p.r_lo : 0;
-    const uint8_t *fbase = ring + fcol;
-    const int xg0 = sg.x0 + lane * L;
-    const bool xclip = xg0 < p.r_lo || xg0 + L - 1 + p.r_hi > p.w - 1; // some window of the lane leaves the image
+    const LaneGeo g = lane_geo<KO>(p, sg);
+    const uint8_t *fbase = ring + g.fcol;
 
-    int rc = (ii + p.r_lo) % p.ring_rows; // ring row of this warp's centre row in chunk k
+    int rc = (g.ii + p.r_lo) % p.ring_rows; // ring row of this warp's centre row in chunk k
     for (int k = 0; k < sg.nk; ++k, rc = (rc + CH < p.ring_rows) ? rc + CH : rc + CH - p.ring_rows) {
         const int b = k & 1;
         bar_sync(BAR_FULL + b, NTX);
         const int rows_k = min(CH, sg.th_eff - k * CH);
-        if (ii < rows_k && !*s_abort) {
-            const int i = k * CH + ii;
-            const int y = sg.y0 + i;
-            const uint32_t *C1 = cb + (size_t)(2 * b) * CH * p.RSW + ii * p.RSW;
-            const uint32_t *C2 = C1 + (size_t)CH * p.RSW;
-            const int cw = lane * L + p.o; // leaving-stream start; entering = cw + W
-            const int ao = cw >> 2, ai = (cw + W) >> 2;
-
-            uint32_t d1[L], d2[L];
-            uint32_t a1 = 0, a2 = 0;
-            if (active) {
-                lane_deltas<KO, KI>(C1, C2, ao, ai, d1, d2, a1, a2);
-            } else {
-#pragma unroll
-                for (int t = 0; t < L; ++t)
-                    d1[t] = d2[t] = 0u;
-            }
-            // the window of the strip's first output: span columns [o, o + W)
-            uint32_t s1 = 0, s2 = 0;
-            for (int c = p.o + lane; c < p.o + W; c += 32) {
-                const int qc = cpos(c);
-                s1 += C1[qc];
-                s2 += C2[qc];
-            }
-            s1 = __reduce_add_sync(0xffffffffu, s1);
-            s2 = __reduce_add_sync(0xffffffffu, s2);
-            uint32_t x1 = a1, x2 = a2;
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const uint32_t t1 = __shfl_up_sync(0xffffffffu, x1, off);
-                const uint32_t t2 = __shfl_up_sync(0xffffffffu, x2, off);
-                if (lane >= off) {
-                    x1 += t1;
-                    x2 += t2;
-                }
-            }
-            const uint32_t base1 = s1 + x1 - a1, base2 = s2 + x2 - a2;
+        if (g.ii < rows_k && !*s_abort) {
+            const int y = sg.y0 + k * CH + g.ii;
+            const uint32_t *C1 = cb + (size_t)(2 * b) * C2O + g.ii * RS;
+            uint32_t d1[L], d2[L], base1, base2;
+            row_sums<KO, KI, WM8>(p, g, C1, d1, d2, base1, base2);
 
             const uint4 fv = *reinterpret_cast<const uint4 *>(fbase + (size_t)rc * SWP);
             const uint32_t fw[4] = {fv.x, fv.y, fv.z, fv.w};
             const bool yclip = (y < p.r_lo) || (y + p.r_hi > p.h - 1);
-            const bool lane_clip = active && xg0 < p.w && (yclip || xclip);
+            const bool lane_clip = g.active && g.xg0 < p.w && (yclip || g.xclip);
             uint32_t outw[4];
-            float mn = INFINITY; // smallest |d| of the lane's pixels inside the image
-            if (!__any_sync(0xffffffffu, lane_clip)) {
-                // every window of the warp is W x W: shared constants
-#pragma unroll
-                for (int qq = 0; qq < 4; ++qq) {
-                    float dd[4];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int t = 4 * qq + e;
-                        const uint32_t S1 = base1 + d1[t];
-                        const uint32_t S2 = base2 + d2[t]; // exact: S2 < 2^32
-                        const unsigned long long V =
-                            (unsigned long long)p.nW * S2 - (unsigned long long)S1 * S1;
-                        const float ff = byte_float(fw[qq], e);
-                        dd[e] = filter_int<RULE>(ff, __uint2float_rn(S1), sqrt_approx(v_to_float(V)), p);
-                        mn = fminf(mn, fabsf(dd[e]));
-                    }
-                    // byte = 0xFF where d >= +0, 0x00 where d < 0 (sign bit replicated)
-                    const uint32_t lo = prmt(__float_as_uint(dd[0]), __float_as_uint(dd[1]), 0xFBu);
-                    const uint32_t hi = prmt(__float_as_uint(dd[2]), __float_as_uint(dd[3]), 0xFBu);
-                    outw[qq] = ~prmt(lo, hi, 0x5410u);
-                }
-            } else {
-                // border warp: each pixel with its own clipped count n = nr * nc
-                const int nr = min(y + p.r_hi, p.h - 1) - max(y - p.r_lo, 0) + 1;
-#pragma unroll
-                for (int qq = 0; qq < 4; ++qq) {
-                    float dd[4];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int t = 4 * qq + e;
-                        const int xg = xg0 + t;
-                        const int nc = min(xg + p.r_hi, p.w - 1) - max(xg - p.r_lo, 0) + 1;
-                        const uint32_t n = (uint32_t)(nr * nc);
-                        const uint32_t S1 = base1 + d1[t], S2 = base2 + d2[t];
-                        const unsigned long long V = (unsigned long long)n * S2 - (unsigned long long)S1 * S1;
-                        const float ff = byte_float(fw[qq], e);
-                        const float invn = rcp_approx(__uint2float_rn(n));
-                        dd[e] = filter_n<RULE>(ff, __uint2float_rn(S1), sqrt_approx(v_to_float(V)), invn, p);
-                        mn = fminf(mn, xg < p.w ? fabsf(dd[e]) : INFINITY);
-                    }
-                    const uint32_t lo = prmt(__float_as_uint(dd[0]), __float_as_uint(dd[1]), 0xFBu);
-                    const uint32_t hi = prmt(__float_as_uint(dd[2]), __float_as_uint(dd[3]), 0xFBu);
-                    outw[qq] = ~prmt(lo, hi, 0x5410u);
-                }
+            float mn = INFINITY; // smallest |nd| of the lane's pixels inside the image
+            if (!__any_sync(0xffffffffu, lane_clip))
+                decide_lane_int<RULE>(p, base1, base2, d1, d2, fw, outw, mn);
+            else
+                decide_lane_border<RULE>(p, y, g.xg0, base1, base2, d1, d2, fw, outw, mn);
+            if (mn < p.E && g.active) { // rare: a value inside the fp32 margin
+                uint32_t e1[L], e2[L];
+                lane_sums_again<KO, KI, WM8>(p, g, C1, e1, e2);
+                fix_margin<RULE>(p, y, g.xg0, base1, base2, e1, e2, fw, outw, nfb, nties);
             }
-            if (mn < p.E && active) { // rare: a value inside the fp32 margin -> fp64 for those pixels
-                // (1) which pixels: the 16 filters again, unrolled and independent (with
-                // each pixel's own n, as the border path), into a bit mask;
-                // (2) the fp64 sequence for the set bits only, typically one.  Register
-                // arrays are indexed with compile-time constants only, so nothing of the
-                // fast path moves to local memory.
-                const int nr = min(y + p.r_hi, p.h - 1) - max(y - p.r_lo, 0) + 1;
-                // the sums again from the column-sum buffer (still valid: it is released
-                // after this row), so the fast path's offsets need not live until here
-                uint32_t e1[L], e2[L], t1, t2;
-                lane_deltas<KO, KI>(C1, C2, ao, ai, e1, e2, t1, t2);
-                uint32_t amask = 0;
-#pragma unroll
-                for (int t = 0; t < L; ++t) {
-                    const int xg = xg0 + t;
-                    const int nc = min(xg + p.r_hi, p.w - 1) - max(xg - p.r_lo, 0) + 1;
-                    const uint32_t n = (uint32_t)(nr * nc);
-                    const uint32_t S1 = base1 + e1[t], S2 = base2 + e2[t];
-                    const unsigned long long V = (unsigned long long)n * S2 - (unsigned long long)S1 * S1;
-                    const float ff = byte_float(fw[t >> 2], t & 3);
-                    const float sq = sqrt_approx(v_to_float(V));
-                    const float d = (n == p.nW) ? filter_int<RULE>(ff, __uint2float_rn(S1), sq, p)
-                                                : filter_n<RULE>(ff, __uint2float_rn(S1), sq,
-                                                                 rcp_approx(__uint2float_rn(n)), p);
-                    if (xg < p.w && fabsf(d) < p.E)
-                        amask |= 1u << t;
-                }
-                uint32_t white = 0; // bit t: the fp64 decision of pixel t is 255
-                for (uint32_t m = amask; m; m &= m - 1) {
-                    const int t = __ffs(m) - 1;
-                    uint32_t S1 = base1, S2 = base2, word = fw[0];
-#pragma unroll
-                    for (int u = 0; u < L; ++u)
-                        if (u == t) {
-                            S1 += e1[u];
-                            S2 += e2[u];
-                        }
-#pragma unroll
-                    for (int qq = 1; qq < 4; ++qq)
-                        if ((t >> 2) == qq)
-                            word = fw[qq];
-                    const uint32_t f = (word >> (8 * (t & 3))) & 0xffu;
-                    const int xg = xg0 + t;
-                    const int nc = min(xg + p.r_hi, p.w - 1) - max(xg - p.r_lo, 0) + 1;
-                    const uint32_t r = decide_exact<RULE>(f, (uint32_t)(nr * nc), S1, S2, p);
-                    ++nfb;
-                    nties += (r >> 9) & 1u;
-                    white |= (r & 1u) << t;
-                }
-#pragma unroll
-                for (int qq = 0; qq < 4; ++qq) { // bits 4qq..4qq+3 -> bytes 0..3 of word qq
-                    const uint32_t mm = ((((amask >> (4 * qq)) & 15u) * 0x00204081u) & 0x01010101u) * 0xffu;
-                    const uint32_t vv = ((((white >> (4 * qq)) & 15u) * 0x00204081u) & 0x01010101u) * 0xffu;
-                    outw[qq] = (outw[qq] & ~mm) | (vv & mm);
-                }
-            }
-            if (active && xg0 < p.w) {
-                if (!p.packed) {
-                    uint8_t *drow = p.dst + (size_t)y * p.dst_pitch + xg0;
-                    if (p.vec_ok && xg0 + L <= p.w) {
-                        *reinterpret_cast<uint4 *>(drow) = make_uint4(outw[0], outw[1], outw[2], outw[3]);
-                    } else {
-                        for (int t = 0; t < L && xg0 + t < p.w; ++t)
-                            drow[t] = (uint8_t)byte_dyn(outw[t >> 2], t & 3);
-                    }
-                } else {
-                    uint32_t bits = 0; // bit t <-> pixel xg0 + t: the msb of each byte
-#pragma unroll
-                    for (int qq = 0; qq < 4; ++qq)
-                        bits |= ((((outw[qq] >> 7) & 0x01010101u) * 0x01020408u) >> 24) << (4 * qq);
-                    const int valid = p.w - xg0;
-                    if (valid < L)
-                        bits &= (1u << valid) - 1u;
-                    uint8_t *drow = p.dst + (size_t)y * p.dst_pitch + (xg0 >> 3);
-                    drow[0] = (uint8_t)(bits & 0xffu);
-                    if (valid > 8)
-                        drow[1] = (uint8_t)(bits >> 8);
-                }
-            }
+            if (g.active && g.xg0 < p.w)
+                store_lane(p, y, g.xg0, outw);
         }
         if (k + 2 < sg.nk)
             bar_arrive(BAR_EMPTY + b, NTX);
     }
 }
-
 
 template <int CIN, int RULE, int WM8>
 __device__ __forceinline__ void run_segment(const CUtensorMap *tmap, const FusedParams &p, const Segment &sg,
