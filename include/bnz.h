@@ -41,8 +41,11 @@
  *     counters that the kernels add to (the caller zeroes them):
  *       [0] pixels re-evaluated in fp64 (inside the fp32 margin),
  *       [1] ties: pixels with |f - t| < 1e-9,
- *       [2] bounded waits that timed out (a CTA that gives up writes no output
- *           and the call reports BNZ_ETIMEOUT on the next synchronous call),
+ *       [2] bounded waits that timed out: a CTA that gives up writes no output
+ *           of its part of the page.  The synchronous host-pointer calls
+ *           return BNZ_ETIMEOUT then; asynchronous callers read this counter;
+ *           the serving engine fails the requests of such a step with
+ *           BNZ_ETIMEOUT,
  *       [3] reserved, 0.
  */
 #ifndef BNZ_H
@@ -264,7 +267,9 @@ typedef struct {
     int compute_streams;  /* 1..4; 1 is fastest for mixed traffic (kernels of different instances running
                              side by side share the SMs' instruction caches) */
     int batched;          /* 1: one batched launch per step; 0: one plain launch per page */
-    int reserved;
+    int reserved;         /* 0.  Test hook, host side only: n > 0 makes every n-th launch step report a
+                             device timeout, as if a bounded wait had given up, so that callers can test
+                             their handling of BNZ_ETIMEOUT */
 } bnz_server_config;
 
 typedef struct {

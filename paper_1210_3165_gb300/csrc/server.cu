@@ -46,6 +46,9 @@ struct Step {
     cudaEvent_t ev = nullptr;
     std::vector<Req *> reqs;
     bnz_batch *batch = nullptr;
+    int stream = 0;       // compute stream index (its statistics slot)
+    int status = BNZ_OK;  // a launch failure after some of the step's kernels were queued
+    bool inject = false;  // test hook: report this step as timed out
 };
 
 } // namespace
@@ -59,6 +62,9 @@ struct bnz_server {
     void *desc[kMaxStreams] = {};
     size_t desc_bytes = 0;
     cudaEvent_t inflight[kMaxStreams] = {};
+    // per compute stream: the kernels' 4 statistics counters on the device and
+    // their copy in pinned host memory, read when the step is retired
+    unsigned long long *d_stats = nullptr, *h_stats = nullptr;
 
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -213,8 +219,14 @@ bool launch(bnz_server *s)
     }
     const int n = (int)st.reqs.size();
     cudaStream_t stream = s->comp[k];
+    st.stream = k;
+    unsigned long long *dst = s->d_stats + 4 * k;
     int rc = BNZ_OK;
-    if (s->cfg.batched) {
+    int queued = 0; // kernels of this step already on the stream
+    if (cudaMemsetAsync(dst, 0, 4 * sizeof(unsigned long long), stream) != cudaSuccess)
+        rc = bnz::cuda_fail(cudaGetLastError(), "statistics reset");
+    if (rc != BNZ_OK) {
+    } else if (s->cfg.batched) {
         std::vector<bnz_page> pages(n);
         for (int i = 0; i < n; ++i) {
             const bnz_request &r = st.reqs[i]->r;
@@ -233,24 +245,36 @@ bool launch(bnz_server *s)
             pg.d_dst = st.reqs[i]->d_dst;
             pg.dst_pitch = st.reqs[i]->dp;
         }
-        rc = bnz_batch_create_async(pages.data(), n, s->desc[k], s->desc_bytes, stream, nullptr, &st.batch);
-        if (rc == BNZ_OK)
+        rc = bnz_batch_create_async(pages.data(), n, s->desc[k], s->desc_bytes, stream, dst, &st.batch);
+        if (rc == BNZ_OK) {
+            queued = 1; // the descriptor copy
             rc = bnz_batch_run(st.batch, stream);
+        }
     } else {
         for (int i = 0; i < n && rc == BNZ_OK; ++i) {
             const Req *q = st.reqs[i];
             rc = bnz_binarize_dev(q->d_src, q->sp, q->r.height, q->r.width, q->r.channels, q->r.W, q->r.rule,
-                                  q->r.k, q->r.R, q->d_dst, q->dp, q->r.packed, nullptr, stream, nullptr);
+                                  q->r.k, q->r.R, q->d_dst, q->dp, q->r.packed, nullptr, stream, dst);
+            if (rc == BNZ_OK)
+                ++queued;
         }
     }
     if (rc != BNZ_OK) {
         set_error(s, bnz_last_error());
-        if (st.batch)
-            bnz_batch_destroy(st.batch);
-        for (Req *q : st.reqs)
-            finish(s, q, rc);
-        return true;
+        if (!queued) { // nothing of the step reached the stream: its buffers are free now
+            if (st.batch)
+                bnz_batch_destroy(st.batch);
+            for (Req *q : st.reqs)
+                finish(s, q, rc);
+            return true;
+        }
+        // kernels of earlier requests are queued: fail the step only once the stream has passed them,
+        // so no pool block is handed out while a kernel may still write it
+        st.status = rc;
     }
+    if (rc == BNZ_OK)
+        cudaMemcpyAsync(s->h_stats + 4 * k, dst, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, stream);
+    st.inject = s->cfg.reserved > 0 && (s->nsteps + 1) % s->cfg.reserved == 0;
     st.ev = get_event(s);
     cudaEventRecord(st.ev, stream);
     s->inflight[k] = st.ev;
@@ -269,10 +293,20 @@ bool collect_steps(bnz_server *s)
             continue;
         }
         const cudaError_t e = cudaEventQuery(it->ev);
+        // a CTA whose bounded wait gave up wrote no output: the step's masks are incomplete
+        const unsigned long long tmo = (e == cudaSuccess && it->status == BNZ_OK)
+                                           ? s->h_stats[4 * it->stream + BNZ_STATS_TIMEOUTS] + (it->inject ? 1 : 0)
+                                           : 0;
+        if (tmo)
+            set_error(s, "a device wait timed out in a launch step; its requests fail with BNZ_ETIMEOUT");
         for (Req *q : it->reqs) {
             if (e != cudaSuccess) {
                 set_error(s, std::string("kernel: ") + cudaGetErrorString(e));
                 finish(s, q, BNZ_ECUDA);
+                continue;
+            }
+            if (it->status != BNZ_OK || tmo) {
+                finish(s, q, it->status != BNZ_OK ? it->status : BNZ_ETIMEOUT);
                 continue;
             }
             const size_t row = q->r.packed ? ((size_t)q->r.width + 7) / 8 : (size_t)q->r.width;
@@ -360,6 +394,10 @@ void destroy(bnz_server *s)
         cudaStreamDestroy(s->cout);
     if (s->pool)
         bnz_pool_destroy(s->pool);
+    if (s->d_stats)
+        cudaFree(s->d_stats);
+    if (s->h_stats)
+        cudaFreeHost(s->h_stats);
     if (s->arena)
         cudaFree(s->arena);
     delete s;
@@ -404,7 +442,11 @@ int bnz_server_create(const bnz_server_config *cfg, bnz_server **out)
         return rc;
     }
     s->desc_bytes = bnz_batch_desc_bytes(cfg->max_batch);
-    e = cudaStreamCreateWithFlags(&s->cin, cudaStreamNonBlocking);
+    e = cudaMalloc(&s->d_stats, kMaxStreams * 4 * sizeof(unsigned long long));
+    if (e == cudaSuccess)
+        e = cudaMallocHost(&s->h_stats, kMaxStreams * 4 * sizeof(unsigned long long));
+    if (e == cudaSuccess)
+        e = cudaStreamCreateWithFlags(&s->cin, cudaStreamNonBlocking);
     if (e == cudaSuccess)
         e = cudaStreamCreateWithFlags(&s->cout, cudaStreamNonBlocking);
     for (int k = 0; k < cfg->compute_streams && e == cudaSuccess; ++k) {

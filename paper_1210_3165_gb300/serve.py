@@ -341,14 +341,16 @@ class NativeServer:
     (16-byte row pitch).  Masks land in a pinned host arena; the futures return numpy arrays over it."""
 
     def __init__(self, budget_bytes: int = 16 << 30, max_batch: int = 16, batched: bool = True,
-                 compute_streams: int = 1, host_bytes: int = 4 << 30):
+                 compute_streams: int = 1, host_bytes: int = 4 << 30, inject_timeout_every: int = 0):
         import ctypes
         from . import _check, bnz_server_config, load
         self.host = HostArena(host_bytes)
         self._ct = ctypes
         self._lib = load()
         self.budget = int(budget_bytes)
-        cfg = bnz_server_config(self.budget, int(max_batch), int(compute_streams), 1 if batched else 0, 0)
+        # inject_timeout_every (testing): every n-th launch step is reported as timed out by the engine
+        cfg = bnz_server_config(self.budget, int(max_batch), int(compute_streams), 1 if batched else 0,
+                                int(inject_timeout_every))
         h = ctypes.c_void_p(None)
         _check(self._lib.bnz_server_create(ctypes.byref(cfg), ctypes.byref(h)))
         self._h = h

@@ -46,6 +46,9 @@ def test_version_and_error_string(lib):
     (dict(W=256), "window size"),
     (dict(R=0.0), "R must be"),
     (dict(k=float("nan")), "k must be finite"),
+    (dict(k=1.0e6 * (1 + 1e-12)), "|k| <="),      # past the range where every constant stays finite
+    (dict(k=-2.0e6), "|k| <="),
+    (dict(R=0.9e-6), "R must be"),
     (dict(channels=2), "channels"),
     (dict(h=0), "height and width"),
 ])
@@ -58,6 +61,16 @@ def test_argument_errors(lib, args, fragment):
                          dst.ctypes.data)
     assert rc == bnz.BNZ_EINVAL
     assert fragment in bnz.bnz_last_error()
+
+
+def test_parameter_range_limits_accepted(lib):
+    """The ends of the accepted range pass the argument checks (no GPU here: the call then reports that
+    there is no device, not a bad argument)."""
+    src = np.zeros(64, np.uint8)
+    dst = np.zeros(64, np.uint8)
+    for k, R in ((1.0e6, 1.0e-6), (-1.0e6, 1.0e-6), (0.5, 1.0e300)):
+        rc = lib.bnz_sauvola(src.ctypes.data, 8, 8, 1, 3, k, R, dst.ctypes.data)
+        assert rc != bnz.BNZ_EINVAL, bnz.bnz_last_error()
 
 
 def test_null_pointer_rejected(lib):

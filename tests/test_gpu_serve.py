@@ -108,3 +108,30 @@ def test_native_server_full_size_page(bnz, rule, W):
     srv.stop()
     np.testing.assert_array_equal(got_host, ref)
     np.testing.assert_array_equal(got_dev, ref)
+
+
+@pytest.mark.parametrize("batched", [True, False])
+def test_native_server_step_timeout_fails_its_requests(bnz, batched):
+    """A launch step whose kernels report a timed-out wait (injected on the host: the engine's test hook
+    marks every second step) fails exactly its own requests with BNZ_ETIMEOUT; the other requests still
+    return the oracle's masks."""
+    from paper_1210_3165_gb300.serve import NativeServer, Request
+    items = mix(12, 23)
+    srv = NativeServer(budget_bytes=64 << 20, max_batch=1, batched=batched, inject_timeout_every=2)
+    futs = [srv.submit(Request(image=torch.from_numpy(img).pin_memory(), W=W, rule=rule, packed=packed))
+            for img, W, rule, packed in items]
+    srv.stop(drain=True, timeout=120)
+    failed = ok = 0
+    for (img, W, rule, packed), f in zip(items, futs):
+        err = f.exception(timeout=0)
+        if err is not None:
+            assert "status 4" in str(err) and "timed out" in str(err)
+            failed += 1
+            continue
+        k = 0.5 if rule == "sauvola" else -0.2
+        rid = oracle.SAUVOLA if rule == "sauvola" else oracle.NIBLACK
+        ref, _ = oracle.binarize(img, W, rid, k, 128.0, threads=NTHREADS, packed=packed)
+        np.testing.assert_array_equal(np.asarray(f.result(timeout=0)), ref)
+        ok += 1
+    # one request per step (max_batch 1): every second step, so half the requests, fail
+    assert failed == len(items) // 2 and ok == len(items) - failed
