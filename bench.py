@@ -294,14 +294,16 @@ def run_ours(args):
 
     rot = [0]
 
-    def step(evs=None):
+    def launch(j):
+        W, rule, k, R = RUNS[j]
+        c = rot[0] % NCOPY
+        rot[0] += 1
+        bnz.bnz_binarize_dev(srcs[c], W, rule_id[rule], k, R, outs[c], stream=stream)
+
+    def step():
         # every launch reads the next of the NCOPY input copies, so none finds its input in L2
-        for j, (W, rule, k, R) in enumerate(RUNS):
-            if evs is not None:
-                evs[j].record(stream)
-            c = rot[0] % NCOPY
-            rot[0] += 1
-            bnz.bnz_binarize_dev(srcs[c], W, rule_id[rule], k, R, outs[c], stream=stream)
+        for j in range(len(RUNS)):
+            launch(j)
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -311,40 +313,60 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
 
-    # timed region: K steps, an event before every launch and one at the end
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(RUNS))] for _ in range(args.steps)]
-    end = torch.cuda.Event(enable_timing=True)
+    # timed region: passes of exactly K steps, each bracketed by an event pair and a
+    # synchronize, repeated until at least --min-seconds have passed (so the clock record
+    # has samples under load); the job's time per pass is the median pass
     clocks = ClockSampler(local, gpu_uuid(dev))
     clocks.start()
-    with torch.cuda.stream(stream):
-        for s in range(args.steps):
-            step(evs[s])
-        end.record(stream)
-    stream.synchronize()
+    pass_ms = []
+    t_start = time.perf_counter()
+    while True:
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            a.record(stream)
+            for _ in range(args.steps):
+                step()
+            b.record(stream)
+        stream.synchronize()
+        pass_ms.append(a.elapsed_time(b))
+        if time.perf_counter() - t_start >= args.min_seconds or len(pass_ms) >= 2000:
+            break
     clk = clocks.stop()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    total_ms = evs[0][0].elapsed_time(end)
-    per_launch = {j: [] for j in range(len(RUNS))}
-    for s in range(args.steps):
-        for j in range(len(RUNS)):
-            nxt = evs[s][j + 1] if j + 1 < len(RUNS) else (evs[s + 1][0] if s + 1 < args.steps else end)
-            per_launch[j].append(evs[s][j].elapsed_time(nxt))
+    total_ms = statistics.median(pass_ms)
     total_ms = max_over_ranks(total_ms, world, dev)
+
+    # per-W times: blocks of BLOCK back-to-back launches of one run between one event pair
+    # (lifts the per-launch figure above the event timer's resolution), median of 5 blocks
+    BLOCK = 20
+    per_block = {j: [] for j in range(len(RUNS))}
+    with torch.cuda.stream(stream):
+        for _ in range(5):
+            for j in range(len(RUNS)):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                for _ in range(BLOCK):
+                    launch(j)
+                b.record(stream)
+                per_block[j].append((a, b))
+    stream.synchronize()
 
     px_step = H * W_IMG * len(RUNS)
     value = job_value(world, args.steps, px_step, total_ms)
     peak, peak_kind = measured_peak()
     bytes_launch = H * W_IMG * BYTES_PER_PX
-    avg_launch_ms = statistics.mean(sum(v) / len(v) for v in per_launch.values())
-    achieved = bytes_launch / (avg_launch_ms / 1e3) / 1e9
     per_w = {}
+    launch_ms = []
     for j, (W, rule, k, R) in enumerate(RUNS):
-        ms = sorted(per_launch[j])[len(per_launch[j]) // 2]
+        ms = statistics.median(a.elapsed_time(b) / BLOCK for a, b in per_block[j])
+        launch_ms.append(ms)
         gbs = bytes_launch / (ms / 1e3) / 1e9
         per_w[f"{rule}_W{W}"] = {"us": round(ms * 1e3, 2), "Mpixel/s": round(H * W_IMG / (ms / 1e3) / 1e6, 1),
                                  "GB/s": round(gbs, 1), "frac": round(gbs / peak, 4)}
+    avg_launch_ms = total_ms / (args.steps * len(RUNS))
+    achieved = bytes_launch / (avg_launch_ms / 1e3) / 1e9
 
     result = {
         "metric": METRIC, "value": value, "unit": "Mpixel/s", "n_gpus": world, "steps": args.steps,
@@ -353,20 +375,31 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "h": H, "w": W_IMG, "channels": CH, "runs_per_step": len(RUNS),
                    "l2": "each launch reads its own input copy (8 copies, 400 MB > 129 MB L2)",
                    "parallelism": f"replicas x{world}"},
+        "timing": {"passes": len(pass_ms), "steps_per_pass": args.steps,
+                   "ms_per_pass": {"median": total_ms, "min": min(pass_ms), "max": max(pass_ms)},
+                   "timed_seconds": round(sum(pass_ms) / 1e3, 3),
+                   "per_W": f"blocks of {BLOCK} back-to-back launches per run, median of 5 blocks"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": ncu_traffic(),
                      "kernel": "fused_kernel", "algorithmic_bytes_per_launch": bytes_launch,
                      "peak_kind": peak_kind},
         "per_W": per_w,
-        "gpu_launches": args.steps * len(RUNS),
+        "gpu_launches": len(pass_ms) * args.steps * len(RUNS),
         "clocks": clk,
     }
 
     if rank == 0 and not args.no_e2e:
-        result["e2e"] = e2e_host_api(bnz, page, 5)
+        result["e2e"] = e2e_host_api(bnz, page, 7)
     if not args.case:
         result["dual"] = dual_runs(bnz, srcs, outs, stream, dev, args.steps, max(args.warmup, 3))
         result["otsu"] = otsu_runs(bnz, srcs, outs, stream, dev, args.steps, max(args.warmup, 3))
+    if not args.case and not args.no_extra and rank == 0:
+        del srcs, outs
+        torch.cuda.empty_cache()
+        result["config1"] = config1_latency(bnz, dev)
+        result["config3"] = config3_large(bnz, dev)
+        result["batch"] = batch_summary(bnz, dev)
+        result["serve"] = serve_summary(bnz, args)
     if rank == 0 and world == 1 and not args.no_cpu:
         import oracle
         threads = os.cpu_count() or 1
@@ -388,44 +421,246 @@ def run_ours(args):
 
 def dual_runs(bnz, srcs, outs, stream, dev, steps, warmup):
     """Both rules per W from one kernel (bnz_dual_dev): one launch per W writes the Sauvola (k=0.5, R=128) and the
-    Niblack (k=-0.2) mask, timed like the single-rule runs (events before every launch, own input copy each)."""
+    Niblack (k=-0.2) mask; each W timed as blocks of 20 back-to-back launches (own input copy each), median of 5."""
     import torch
     Ws = sorted({W for W, _, _, _ in RUNS})
     outs2 = [bnz.alloc_pitched(H, W_IMG, dev) for _ in range(NCOPY)]
     rot = [0]
 
-    def step(evs=None):
-        for j, W in enumerate(Ws):
-            if evs is not None:
-                evs[j].record(stream)
-            c = rot[0] % NCOPY
-            rot[0] += 1
-            bnz.bnz_dual_dev(srcs[c], W, 0.5, 128.0, -0.2, outs[c], outs2[c], stream=stream)
+    def launch(W):
+        c = rot[0] % NCOPY
+        rot[0] += 1
+        bnz.bnz_dual_dev(srcs[c], W, 0.5, 128.0, -0.2, outs[c], outs2[c], stream=stream)
 
     with torch.cuda.stream(stream):
         for _ in range(warmup):
-            step()
+            for W in Ws:
+                launch(W)
     stream.synchronize()
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in Ws] for _ in range(steps)]
-    end = torch.cuda.Event(enable_timing=True)
-    with torch.cuda.stream(stream):
-        for s in range(steps):
-            step(evs[s])
-        end.record(stream)
-    stream.synchronize()
-    total = evs[0][0].elapsed_time(end)
     per = {}
-    for j, W in enumerate(Ws):
-        ts = []
-        for s in range(steps):
-            nxt = evs[s][j + 1] if j + 1 < len(Ws) else (evs[s + 1][0] if s + 1 < steps else end)
-            ts.append(evs[s][j].elapsed_time(nxt))
-        per[f"W{W}"] = round(sorted(ts)[len(ts) // 2] * 1e3, 2)
-    masks = steps * len(Ws) * 2 * H * W_IMG
+    with torch.cuda.stream(stream):
+        ev = {W: [] for W in Ws}
+        for _ in range(5):
+            for W in Ws:
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                for _ in range(20):
+                    launch(W)
+                b.record(stream)
+                ev[W].append((a, b))
+    stream.synchronize()
+    peak, _ = measured_peak()
+    bytes_launch = H * W_IMG * (CH + 2)
+    total = 0.0
+    for W in Ws:
+        ms = statistics.median(a.elapsed_time(b) / 20 for a, b in ev[W])
+        total += ms
+        per[f"W{W}"] = {"us": round(ms * 1e3, 2), "frac": round(bytes_launch / (ms / 1e3) / 1e9 / peak, 4)}
+    masks = len(Ws) * 2 * H * W_IMG
     return {"kernel": "dual_kernel", "launches_per_step": len(Ws), "masks_per_step": 2 * len(Ws),
-            "ms_per_step": total / steps, "Mpixel/s": masks / (total / 1e3) / 1e6, "us_per_launch": per,
+            "ms_per_step": total, "Mpixel/s": masks / (total / 1e3) / 1e6, "per_W": per,
+            "algorithmic_bytes_per_launch": bytes_launch,
             "note": "the same 8 masks as a step of the single-rule runs, two per launch from one pass over the "
                     "window sums; every mask equals the single-rule kernel's"}
+
+
+def _block_ms(fn, stream, n, reps=5):
+    """Median over `reps` blocks of n back-to-back calls between one event pair, in ms per call."""
+    import torch
+    out = []
+    with torch.cuda.stream(stream):
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(n):
+                fn()
+            b.record(stream)
+            out.append((a, b))
+    stream.synchronize()
+    return statistics.median(a.elapsed_time(b) / n for a, b in out)
+
+
+def config1_latency(bnz, dev):
+    """512x512 gray page, Sauvola W=15 k=0.5 R=128: device latency of one launch (events around each launch,
+    median of 200), back-to-back throughput, and the host-pointer call's latency (copies included)."""
+    import numpy as np
+    import torch
+    import synth
+    img = synth.page(512, 512, 1)
+    src = bnz.to_device_pitched(img, dev)
+    out = bnz.alloc_pitched(512, 512, dev)
+    stream = torch.cuda.Stream(device=dev)
+
+    def call():
+        bnz.bnz_binarize_dev(src, 15, bnz.BNZ_SAUVOLA, 0.5, 128.0, out, stream=stream)
+    with torch.cuda.stream(stream):
+        for _ in range(20):
+            call()
+    stream.synchronize()
+    lat = []
+    for _ in range(200):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            a.record(stream)
+            call()
+            b.record(stream)
+        stream.synchronize()
+        lat.append(a.elapsed_time(b))
+    tput_ms = _block_ms(call, stream, 200, 3)
+    host = np.ascontiguousarray(img)
+    hdst = np.empty((512, 512), np.uint8)
+    lib = bnz.load()
+    hl = []
+    for i in range(220):
+        t0 = time.perf_counter()
+        rc = lib.bnz_sauvola(host.ctypes.data, 512, 512, 1, 15, 0.5, 128.0, hdst.ctypes.data)
+        hl.append(time.perf_counter() - t0)
+        if rc != 0:
+            raise RuntimeError(bnz.bnz_last_error())
+    hl = hl[20:]
+    return {"workload": "512x512 gray page (seed 1), Sauvola W=15 k=0.5 R=128, byte mask",
+            "device_latency_us": {"median": round(statistics.median(lat) * 1e3, 2), "p99": round(sorted(lat)[197] * 1e3, 2),
+                                  "calls": 200},
+            "back_to_back_us_per_launch": round(tput_ms * 1e3, 2),
+            "Mpixel/s_back_to_back": round(512 * 512 / (tput_ms / 1e3) / 1e6, 1),
+            "host_call_latency_us": {"median": round(statistics.median(hl) * 1e6, 1), "calls": 200,
+                                     "api": "bnz_sauvola, pageable host buffers, copies included"}}
+
+
+def integral_traffic():
+    """DRAM bytes per launch of the integral-image path from the committed ncu summary (same source only)."""
+    p = os.path.join(ROOT, "profiles", "integral_traffic.json")
+    try:
+        d = json.load(open(p))
+        h = hashlib.sha256()
+        for f in ("integral.cu", "decide.cuh"):
+            h.update(open(os.path.join(ROOT, "paper_1210_3165_gb300", "csrc", f), "rb").read())
+        if d.get("source_sha") == h.hexdigest()[:16]:
+            return d
+    except Exception:
+        pass
+    return None
+
+
+def config3_large(bnz, dev):
+    """16384x16384 gray page (vignetting, sigma 15), Sauvola W=101 k=0.34 R=128: the fused kernel (int32 sums)
+    and the integral-image comparison path (int64 tables), each as blocks of back-to-back launches."""
+    import torch
+    import synth
+    h = w = 16384
+    img = synth.page(h, w, 3, synth.VIGNETTE, 1)
+    src = bnz.to_device_pitched(img, dev)
+    del img
+    out = bnz.alloc_pitched(h, w, dev)
+    stream = torch.cuda.Stream(device=dev)
+    peak, _ = measured_peak()
+
+    def fused():
+        bnz.bnz_binarize_dev(src, 101, bnz.BNZ_SAUVOLA, 0.34, 128.0, out, stream=stream)
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            fused()
+    ms_f = _block_ms(fused, stream, 10, 3)
+    nbytes = h * w * 2
+    res = {"workload": "16384x16384 gray page (seed 3, vignetting, sigma 15), Sauvola W=101 k=0.34 R=128, byte mask",
+           "fused": {"ms": round(ms_f, 4), "Mpixel/s": round(h * w / (ms_f / 1e3) / 1e6, 1),
+                     "GB/s": round(nbytes / (ms_f / 1e3) / 1e9, 1),
+                     "frac": round(nbytes / (ms_f / 1e3) / 1e9 / peak, 4), "algorithmic_bytes": nbytes,
+                     "sums": "int32 window sums"}}
+    scratch = bnz.alloc_scratch(bnz.bnz_integral_scratch_bytes(h, w), dev)
+
+    def integral():
+        bnz.bnz_binarize_integral_dev(src, 101, bnz.BNZ_SAUVOLA, 0.34, 128.0, out, scratch, stream=stream)
+    with torch.cuda.stream(stream):
+        integral()
+    ms_i = _block_ms(integral, stream, 3, 3)
+    tr = integral_traffic()
+    res["integral"] = {"ms": round(ms_i, 4), "Mpixel/s": round(h * w / (ms_i / 1e3) / 1e6, 1),
+                       "scratch_bytes": int(scratch.numel()), "sums": "int64 integral images",
+                       "dram_bytes_per_call": (tr or {}).get("dram_bytes_per_call"),
+                       "dram_bytes_source": (tr or {}).get("source"),
+                       "fused_speedup": round(ms_i / ms_f, 2)}
+    del scratch, src, out
+    torch.cuda.empty_cache()
+    return res
+
+
+def batch_summary(bnz, dev):
+    """Config 4: 256 uneven gray pages in one persistent launch replayed from a CUDA graph, against one plain
+    launch per page (same pages, same stream)."""
+    import torch
+    import synth
+    from paper_1210_3165_gb300 import tune
+    specs = synth.batch_specs(256, seed=4)
+    table = tune.load_table()
+    pages, px = [], 0
+    for sp in specs:
+        img = synth.page(sp["h"], sp["w"], sp["seed"], synth.DOC, 1, random_dir=True)
+        pages.append(dict(src=bnz.to_device_pitched(img, dev), dst=bnz.alloc_pitched(sp["h"], sp["w"], dev),
+                          W=sp["W"], rule="sauvola", k=0.5, R=128.0, tile_w=tune.tile_for(table, 1, sp["W"])))
+        px += sp["h"] * sp["w"]
+    batch = bnz.Batch(pages, use_graph=True)
+    stream = torch.cuda.Stream(device=dev)
+
+    def run_batch():
+        batch.run(stream)
+
+    def per_page():
+        for pg in pages:
+            bnz.bnz_binarize_dev(pg["src"], pg["W"], bnz.BNZ_SAUVOLA, 0.5, 128.0, pg["dst"], stream=stream)
+    with torch.cuda.stream(stream):
+        run_batch()
+        per_page()
+    ms_b = _block_ms(run_batch, stream, 3, 5)
+    ms_p = _block_ms(per_page, stream, 1, 3)
+    peak, _ = measured_peak()
+    gbs = px * 2 / (ms_b / 1e3) / 1e9
+    info = batch.info()
+    batch.close()
+    del pages
+    torch.cuda.empty_cache()
+    return {"workload": BATCH_WORKLOAD, "pages": len(specs), "pixels": px,
+            "batched": {"ms": round(ms_b, 3), "pages_per_s": round(len(specs) / (ms_b / 1e3), 1),
+                        "Mpixel/s": round(px / (ms_b / 1e3) / 1e6, 1), "frac": round(gbs / peak, 4),
+                        "launches": info.get("launches")},
+            "per_page_launches": {"ms": round(ms_p, 3), "pages_per_s": round(len(specs) / (ms_p / 1e3), 1),
+                                  "Mpixel/s": round(px / (ms_p / 1e3) / 1e6, 1)},
+            "speedup_vs_per_page": round(ms_p / ms_b, 3), "tile_table": "cached" if table else "library default"}
+
+
+def serve_summary(bnz, args):
+    """Config 5 on a reduced request count: the native serving engine, batched steps vs one plain launch per
+    page, pages from pinned host memory ("host") and already on the device ("resident"): closed-loop capacity,
+    then the Poisson trace at 0.8 of the batched arm's capacity with p50/p99 latency."""
+    import torch
+    import synth
+    from paper_1210_3165_gb300.serve import NativeServer
+    n = args.extra_serve_requests
+    ch, cw = SERVE_CANVAS
+    canvases = [torch.from_numpy(synth.page(ch, cw, 50 + j, prof, 3, random_dir=True)).pin_memory()
+                for j, prof in enumerate((synth.STAINS, synth.DOC))]
+    budget = 16 << 30
+    arms = {"batched": lambda: NativeServer(budget, args.max_batch, batched=True, compute_streams=1),
+            "per_image": lambda: NativeServer(budget, args.max_batch, batched=False, compute_streams=1)}
+    out = {}
+    dev_canvases = [c.to("cuda") for c in canvases]
+    for mode, cvs in (("host", canvases), ("resident", dev_canvases)):
+        reqs = serve_requests(n, 5, cvs)
+        res = {}
+        for name, mk in arms.items():
+            serve_once(mk, reqs[:32], None)
+            cap = serve_once(mk, reqs, None)
+            res[name] = {"capacity_pages_per_s": round(cap["pages_per_s"], 1)}
+        load = 0.8 * res["batched"]["capacity_pages_per_s"]
+        for name, mk in arms.items():
+            st = serve_once(mk, reqs, load)
+            res[name].update({"offered_pages_per_s": round(load, 1), "pages_per_s": round(st["pages_per_s"], 1),
+                              "p50_ms": round(st["p50_ms"], 3), "p99_ms": round(st["p99_ms"], 3)})
+        out[mode] = res
+    del dev_canvases
+    torch.cuda.empty_cache()
+    return {"workload": SERVE_WORKLOAD, "requests": n, "note": f"the first {n} requests of the 10,000-request "
+            "trace (full runs: bench.py --workload serve)", "engine": "native", "modes": out}
 
 
 def otsu_runs(bnz, srcs, outs, stream, dev, steps, warmup):
@@ -463,16 +698,29 @@ def otsu_runs(bnz, srcs, outs, stream, dev, steps, warmup):
 
 
 def e2e_host_api(bnz, page, steps):
-    """Same metric through the host-pointer C ABI: pinned host page in, host mask out, copies timed."""
+    """Same metric through the host-pointer C ABI, copies inside the timed region: a step uploads the pinned
+    page once and brings back its 8 masks with bnz_binarize_runs (one page, eight settings; uploads, kernels and
+    downloads overlapped band by band).  Also reported: the same step as 8 one-setting calls (bnz_sauvola /
+    bnz_niblack), each uploading the page again."""
     import numpy as np
     import torch
     src = torch.empty(page.shape, dtype=torch.uint8, pin_memory=True)
     src.numpy()[...] = page
-    dst = torch.empty((H, W_IMG), dtype=torch.uint8, pin_memory=True)
+    dsts = [torch.empty((H, W_IMG), dtype=torch.uint8, pin_memory=True) for _ in RUNS]
     lib = bnz.load()
-    sp, dp = src.numpy(), dst.numpy()
+    sp = src.numpy()
+    arr = (bnz.bnz_run * len(RUNS))()
+    for j, (W, rule, k, R) in enumerate(RUNS):
+        arr[j] = bnz.bnz_run(W, bnz.BNZ_SAUVOLA if rule == "sauvola" else bnz.BNZ_NIBLACK, k, R,
+                             dsts[j].numpy().ctypes.data)
 
-    def one():
+    def runs():
+        rc = lib.bnz_binarize_runs(sp.ctypes.data, H, W_IMG, CH, arr, len(RUNS))
+        if rc != 0:
+            raise RuntimeError(bnz.bnz_last_error())
+
+    def per_call():
+        dp = dsts[0].numpy()
         for W, rule, k, R in RUNS:
             if rule == "sauvola":
                 rc = lib.bnz_sauvola(sp.ctypes.data, H, W_IMG, CH, W, k, R, dp.ctypes.data)
@@ -480,18 +728,27 @@ def e2e_host_api(bnz, page, steps):
                 rc = lib.bnz_niblack(sp.ctypes.data, H, W_IMG, CH, W, k, dp.ctypes.data)
             if rc != 0:
                 raise RuntimeError(bnz.bnz_last_error())
-    one()
-    torch.cuda.synchronize()
-    ts = []
-    for _ in range(steps):
-        t0 = time.perf_counter()
-        one()
-        ts.append(time.perf_counter() - t0)
-    dt = statistics.median(ts)  # a step is 8 synchronous calls; the median step is robust to host hiccups
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(steps):
+            t0 = time.perf_counter()
+            fn()
+            ts.append(time.perf_counter() - t0)
+        return statistics.median(ts), ts  # the median step is robust to host hiccups
+
+    dt, ts = timed(runs)
+    dt1, _ = timed(per_call)
     return {"value": H * W_IMG * len(RUNS) / dt / 1e6, "unit": "Mpixel/s",
-            "h2d_bytes_per_step": H * W_IMG * CH * len(RUNS), "d2h_bytes_per_step": H * W_IMG * len(RUNS),
-            "api": "bnz_sauvola / bnz_niblack (host pointers, pinned)", "steps": steps,
-            "ms_per_step": {"median": dt * 1e3, "min": min(ts) * 1e3, "max": max(ts) * 1e3}}
+            "h2d_bytes_per_step": H * W_IMG * CH, "d2h_bytes_per_step": H * W_IMG * len(RUNS),
+            "api": "bnz_binarize_runs (host pointers, pinned): the page up once, its 8 masks down", "steps": steps,
+            "ms_per_step": {"median": dt * 1e3, "min": min(ts) * 1e3, "max": max(ts) * 1e3},
+            "one_setting_calls": {"value": H * W_IMG * len(RUNS) / dt1 / 1e6, "unit": "Mpixel/s",
+                                  "h2d_bytes_per_step": H * W_IMG * CH * len(RUNS),
+                                  "d2h_bytes_per_step": H * W_IMG * len(RUNS),
+                                  "api": "8 calls of bnz_sauvola / bnz_niblack, each uploading the page"}}
 
 
 BATCH_WORKLOAD = "batch of 256 uint8 gray pages, width U[600,2480] x height U[800,3508], W from {15,25,45,75}, " \
@@ -673,6 +930,32 @@ def run_serve(args):
     return 0
 
 
+def run_integral(args):
+    """The integral-image comparison path alone on an N x N gray page (vignetting, sigma 15), Sauvola W=101
+    k=0.34 R=128: --warmup calls, then --steps timed calls (for profiler captures of one call)."""
+    import torch
+    import synth
+    import paper_1210_3165_gb300 as bnz
+    torch.cuda.set_device(0)
+    bnz.load()
+    n = args.integral_size
+    img = synth.page(n, n, 3, synth.VIGNETTE, 1)
+    src = bnz.to_device_pitched(img)
+    out = bnz.alloc_pitched(n, n)
+    scratch = bnz.alloc_scratch(bnz.bnz_integral_scratch_bytes(n, n))
+    stream = torch.cuda.Stream()
+
+    def call():
+        bnz.bnz_binarize_integral_dev(src, 101, bnz.BNZ_SAUVOLA, 0.34, 128.0, out, scratch, stream=stream)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            call()
+    ms = _block_ms(call, stream, max(args.steps, 1), 1)
+    print(json.dumps({"workload": f"integral-image path, {n}x{n} gray page, Sauvola W=101 k=0.34 R=128",
+                      "ms_per_call": ms, "Mpixel/s": n * n / (ms / 1e3) / 1e6, "kernels_per_call": 5}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -681,16 +964,22 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="page", choices=["page", "batch", "serve"],
+    ap.add_argument("--no-extra", action="store_true", help="skip the other configurations' keys")
+    ap.add_argument("--min-seconds", type=float, default=1.0,
+                    help="repeat the K-step timed pass until this much time has passed (median pass reported)")
+    ap.add_argument("--workload", default="page", choices=["page", "batch", "serve", "integral"],
                     help="page: the 4096x4096 RGB page (default); batch: 256 uneven gray pages; "
                          "serve: Poisson stream of RGB pages through the serving loop")
     ap.add_argument("--case", default=None,
                     help="page workload restricted to one configuration CH,W,RULE (e.g. 3,15,sauvola): "
                          "one launch per step, for profiler captures")
+    ap.add_argument("--integral-size", type=int, default=8192, help="page side of --workload integral")
     ap.add_argument("--serve-requests", type=int, default=10000)
     ap.add_argument("--serve-capacity", type=int, default=2000, help="requests of the closed-loop capacity run")
     ap.add_argument("--serve-loads", default="0.5,0.8,0.95", help="offered loads, fractions of batched capacity")
     ap.add_argument("--max-batch", type=int, default=16)
+    ap.add_argument("--extra-serve-requests", type=int, default=1000,
+                    help="requests of the serving summary in the default page run")
     ap.add_argument("--serve-engine", default="both", choices=["native", "python", "both"])
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
@@ -700,6 +989,8 @@ def main():
         return run_batch(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "integral":
+        return run_integral(args)
     if args.case:
         global CH, RUNS, NCOPY, BYTES_PER_PX, WORKLOAD
         ch, W, rule = args.case.split(",")

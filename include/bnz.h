@@ -113,7 +113,24 @@ BNZ_API int bnz_sauvola(const uint8_t *src, int height, int width, int channels,
 /* Niblack rule t = m + k*s (k may be negative, e.g. -0.2). */
 BNZ_API int bnz_niblack(const uint8_t *src, int height, int width, int channels, int W, double k, uint8_t *dst);
 
-/* The row bands the two calls above use for a page (host logic only, no
+/* One page, several settings: binarizes the host page src (as bnz_sauvola)
+ * once for every entry of runs, each with its own rule (BNZ_SAUVOLA or
+ * BNZ_NIBLACK; R ignored for Niblack), W, k and host output dst (height*width
+ * bytes, {0,255}).  The page is copied to the device once, in the row bands
+ * bnz_host_bands gives for the largest W; every band's kernels run as soon as
+ * the rows their windows reach are up, and each mask band comes back while
+ * later bands upload and compute.  Each dst equals what bnz_sauvola /
+ * bnz_niblack writes for that setting.  1 <= nruns <= 1024.  Blocks until
+ * done; BNZ_ETIMEOUT if a device wait gave up.  Thread-safe as bnz_sauvola. */
+typedef struct {
+    int W, rule;
+    double k, R;
+    uint8_t *dst;
+} bnz_run;
+BNZ_API int bnz_binarize_runs(const uint8_t *src, int height, int width, int channels, const bnz_run *runs,
+                              int nruns);
+
+/* The row bands bnz_sauvola and bnz_niblack use for a page (host logic only, no
  * device needed): returns the band count nb (>= 1) and, if starts is not NULL,
  * writes the nb + 1 boundaries starts[0] = 0 < ... < starts[nb] = height
  * (max_bands: entries available in starts, at least nb + 1).  Band i starts at
@@ -345,7 +362,9 @@ BNZ_API int bnz_integral_images_dev(const uint8_t *d_src, size_t src_pitch, int 
  * (once per device); make that first call before any stream capture.  Every
  * call on a device uses the same array: calls that overlap on the GPU (other
  * streams, other host threads) race and must be serialized by the caller.
- * The call itself allocates nothing.  Arguments as bnz_binarize_dev. */
+ * The call itself allocates nothing.  The looked-up address is kept for the
+ * life of the process: resetting a device (cudaDeviceReset) while the library
+ * is loaded is not supported by this call.  Arguments as bnz_binarize_dev. */
 #define BNZ_INTEGRAL_STATIC_MAX_BYTES (32u << 20)
 BNZ_API int bnz_binarize_integral_static_dev(const uint8_t *d_src, size_t src_pitch, int height, int width,
                                              int channels, int W, int rule, double k, double R, uint8_t *d_dst,
@@ -384,6 +403,25 @@ BNZ_API int bnz_selftest_sqrt_approx(float lo, float hi, double *max_rel_err);
 /* Same for the hardware reciprocal approximation over the integers
  * n_lo <= n < n_hi (the clipped window counts; assumed <= 2^-22). */
 BNZ_API int bnz_selftest_rcp_approx(unsigned int n_lo, unsigned int n_hi, double *max_rel_err);
+
+/* Device self-test of the fused kernel's Eq. 1 conversion (the producers'
+ * code, four pixels per step): d_rgb holds npix interleaved r,g,b pixels,
+ * d_gray receives npix gray bytes f = (299 r + 587 g + 114 b + 500) / 1000.
+ * Asynchronous on `stream`; for tests and diagnostics. */
+BNZ_API int bnz_selftest_gray(const uint8_t *d_rgb, size_t npix, uint8_t *d_gray, void *stream);
+
+/* Self-test of the fused kernel's own abort path: one launch (byte mask, no
+ * tile) in which every wait of the producers and of the TMA issuer gives up
+ * as soon as its barrier phase is not already complete, so CTAs give up
+ * while their first copies are still in flight; the issuer's final wait for
+ * its copies in flight keeps the normal limit, so no CTA exits with a copy
+ * outstanding.  d_stats (required, 4 counters zeroed by the caller) receives
+ * the count of CTAs that gave up in [2].  Synchronizes `stream`; returns
+ * BNZ_ETIMEOUT when any CTA gave up (the output is then incomplete), else
+ * BNZ_OK.  Other arguments as bnz_binarize_dev.  For tests and diagnostics. */
+BNZ_API int bnz_selftest_fused_timeout(const uint8_t *d_src, size_t src_pitch, int height, int width, int channels,
+                                       int W, int rule, double k, double R, uint8_t *d_dst, size_t dst_pitch,
+                                       void *stream, unsigned long long *d_stats);
 
 /* Device self-test of the bounded wait every kernel uses on its mbarriers:
  * one thread waits for a barrier phase with a limit of `limit_cycles` SM

@@ -50,6 +50,11 @@ class bnz_request(ctypes.Structure):
                 ("dst", ctypes.c_void_p), ("dst_pitch", ctypes.c_size_t), ("tag", ctypes.c_ulonglong)]
 
 
+class bnz_run(ctypes.Structure):
+    _fields_ = [("W", ctypes.c_int), ("rule", ctypes.c_int), ("k", ctypes.c_double), ("R", ctypes.c_double),
+                ("dst", ctypes.c_void_p)]
+
+
 class bnz_tile(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int), ("chunk", ctypes.c_int),
                 ("reserved", ctypes.c_int)]
@@ -117,6 +122,9 @@ def _optional_symbols(lib):
         "bnz_pool_destroy": ([P], ctypes.c_int),
         "bnz_selftest_sqrt_approx": ([ctypes.c_float, ctypes.c_float, ctypes.POINTER(ctypes.c_double)],
                                      ctypes.c_int),
+        "bnz_binarize_runs": ([P, i, i, i, P, i], ctypes.c_int),
+        "bnz_selftest_gray": ([ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p], i),
+        "bnz_selftest_fused_timeout": ([P, sz, i, i, i, i, i, d, d, P, sz, P, P], ctypes.c_int),
         "bnz_selftest_rcp_approx": ([ctypes.c_uint, ctypes.c_uint, ctypes.POINTER(ctypes.c_double)],
                                     ctypes.c_int),
         "bnz_selftest_wait_timeout": ([ctypes.c_longlong, i, ctypes.POINTER(i), ctypes.POINTER(ctypes.c_longlong)],
@@ -177,6 +185,20 @@ def bnz_niblack(src, W: int, k: float = -0.2) -> np.ndarray:
 # ---------------------------------------------------------------------------
 # device-pointer calls (torch CUDA tensors)
 # ---------------------------------------------------------------------------
+
+def binarize_runs(src, runs, out=None) -> list:
+    """One host page, several settings (bnz_binarize_runs): runs = [(W, rule, k, R), ...] with rule
+    "sauvola"/"niblack" or BNZ_*; returns one {0,255} mask per setting (or fills the arrays in `out`)."""
+    img, h, w, ch = _host_img(src)
+    masks = out if out is not None else [np.empty((h, w), np.uint8) for _ in runs]
+    arr = (bnz_run * len(runs))()
+    for j, (W, rule, k, R) in enumerate(runs):
+        rid = rule if isinstance(rule, int) else (BNZ_SAUVOLA if rule == "sauvola" else BNZ_NIBLACK)
+        assert masks[j].shape == (h, w) and masks[j].dtype == np.uint8 and masks[j].flags.c_contiguous
+        arr[j] = bnz_run(int(W), rid, float(k), float(R), masks[j].ctypes.data)
+    _check(load().bnz_binarize_runs(img.ctypes.data, h, w, ch, arr, len(runs)))
+    return masks
+
 
 def alloc_pitched(height: int, row_bytes: int, device="cuda", align: int = 16):
     """uint8 CUDA tensor view of shape (height, row_bytes) whose row stride is a multiple of ``align``."""

@@ -2,6 +2,7 @@
 // messages, TMA descriptor encoding, device bookkeeping and the synchronous
 // host-pointer calls.  All pixel work happens in the CUDA kernels.
 #include <algorithm>
+#include <vector>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -201,6 +202,7 @@ struct HostCallState {
         unsigned long long *stats = nullptr, *h_stats = nullptr;
         void *src = nullptr, *dst = nullptr;
         size_t src_cap = 0, dst_cap = 0;
+        std::vector<cudaEvent_t> ev_run; // bnz_binarize_runs: one per (band, setting) kernel, grow-only
     };
     PerDevice dev[64];
     ~HostCallState()
@@ -216,6 +218,8 @@ struct HostCallState {
                 if (v.ev_k[i])
                     cudaEventDestroy(v.ev_k[i]);
             }
+            for (cudaEvent_t ev : v.ev_run)
+                cudaEventDestroy(ev);
             if (v.up)
                 cudaStreamDestroy(v.up);
             if (v.down)
@@ -423,11 +427,130 @@ static int binarize_host(const uint8_t *src, int height, int width, int channels
     return rc;
 }
 
+// One host page, several settings (bnz_binarize_runs): the page goes up once,
+// in the same row bands as binarize_host, and every band runs each setting's
+// kernel as soon as the rows its windows reach are up; each (band, setting)
+// mask comes down on the download stream as soon as its kernel is done.
+static int binarize_runs_host(const uint8_t *src, int height, int width, int channels, const bnz_run *runs,
+                              int nruns)
+{
+    if (!runs || nruns < 1 || nruns > 1024)
+        return fail(BNZ_EINVAL, "bnz_binarize_runs: 1 to 1024 settings (got %d)", nruns);
+    int Wmax = 1;
+    for (int r = 0; r < nruns; ++r) {
+        const bnz_run &u = runs[r];
+        const double R = u.rule == BNZ_NIBLACK ? 1.0 : u.R;
+        int rc = check_common(src, (size_t)width * channels, height, width, channels, u.W, u.rule, u.k, R, u.dst,
+                              (size_t)width, 0);
+        if (rc != BNZ_OK)
+            return fail(rc, "setting %d: %s", r, bnz_last_error());
+        Wmax = std::max(Wmax, u.W);
+    }
+    int dev = 0;
+    int rc = current_device(&dev);
+    if (rc != BNZ_OK)
+        return rc;
+    int sms = 0;
+    rc = device_sm_count(&sms);
+    if (rc != BNZ_OK)
+        return rc;
+    const size_t row_in = (size_t)width * channels;
+    const size_t sp = (row_in + 15) & ~size_t(15);
+    const size_t dp = ((size_t)width + 15) & ~size_t(15);
+    const size_t mask_bytes = dp * height;
+    HostCallState::PerDevice *v = nullptr;
+    rc = host_call_state(dev, sp * height, mask_bytes * nruns, &v);
+    if (rc != BNZ_OK)
+        return rc;
+    const int nb = host_bands(height, width, Wmax);
+    cudaError_t e = cudaSuccess;
+    while ((int)v->ev_run.size() < nb * nruns) {
+        cudaEvent_t ev = nullptr;
+        if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+            return cuda_fail(e, "cudaEventCreate");
+        v->ev_run.push_back(ev);
+    }
+    cudaStream_t s = v->stream;
+    std::vector<long long> strips(nruns, 1);
+    for (int r = 0; r < nruns && nb > 1; ++r) {
+        FusedPlan shape;
+        if ((rc = plan_shape(height, width, channels, runs[r].W, 0, &shape)) != BNZ_OK)
+            return rc;
+        strips[r] = shape.tiles_x;
+    }
+    do {
+        if ((e = cudaMemsetAsync(v->stats, 0, 4 * sizeof(unsigned long long), s)) != cudaSuccess) {
+            rc = cuda_fail(e, "clear statistics");
+            break;
+        }
+        int uploaded = 0;
+        for (int i = 0; i < nb && rc == BNZ_OK; ++i) {
+            const int y0 = band_start(height, i), y1 = i + 1 < nb ? band_start(height, i + 1) : height;
+            const int need = std::min(height, y1 + (Wmax - 1 - Wmax / 2));
+            if (need > uploaded) {
+                e = copy_rows(v->src, sp, src, row_in, row_in, uploaded, need, cudaMemcpyHostToDevice, v->up);
+                if (e != cudaSuccess) {
+                    rc = cuda_fail(e, "copy input to device");
+                    break;
+                }
+                uploaded = need;
+            }
+            if ((e = cudaEventRecord(v->ev_up[i], v->up)) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(s, v->ev_up[i], 0)) != cudaSuccess) {
+                rc = cuda_fail(e, "order band upload");
+                break;
+            }
+            for (int r = 0; r < nruns && rc == BNZ_OK; ++r) {
+                const bnz_run &u = runs[r];
+                uint8_t *dmask = static_cast<uint8_t *>(v->dst) + (size_t)r * mask_bytes;
+                bnz_tile tile = {0, 0, 0, 0};
+                if (nb > 1)
+                    tile.tile_h = (int)std::max<long long>(8, (strips[r] * (y1 - y0) + sms - 1) / sms);
+                rc = binarize_dev(static_cast<const uint8_t *>(v->src), sp, height, width, channels, u.W, u.rule, u.k,
+                                  u.rule == BNZ_NIBLACK ? 1.0 : u.R, dmask, dp, 0, nb > 1 ? &tile : nullptr, s,
+                                  v->stats, y0, y1);
+                if (rc != BNZ_OK)
+                    break;
+                cudaEvent_t ev = v->ev_run[(size_t)i * nruns + r];
+                if ((e = cudaEventRecord(ev, s)) != cudaSuccess || (e = cudaStreamWaitEvent(v->down, ev, 0)) != cudaSuccess) {
+                    rc = cuda_fail(e, "order mask download");
+                    break;
+                }
+                e = copy_rows(u.dst, (size_t)width, dmask, dp, (size_t)width, y0, y1, cudaMemcpyDeviceToHost, v->down);
+                if (e != cudaSuccess) {
+                    rc = cuda_fail(e, "copy result to host");
+                    break;
+                }
+            }
+        }
+        if (rc != BNZ_OK)
+            break;
+        if ((e = cudaMemcpyAsync(v->h_stats, v->stats, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                 v->down)) != cudaSuccess) {
+            rc = cuda_fail(e, "read statistics");
+            break;
+        }
+    } while (0);
+    for (cudaStream_t q : {v->up, s, v->down}) {
+        e = cudaStreamSynchronize(q);
+        if (rc == BNZ_OK && e != cudaSuccess)
+            rc = cuda_fail(e, "cudaStreamSynchronize");
+    }
+    if (rc == BNZ_OK && v->h_stats[BNZ_STATS_TIMEOUTS] != 0)
+        rc = fail(BNZ_ETIMEOUT, "a device-side wait timed out; output incomplete");
+    return rc;
+}
+
 } // namespace bnz
 
 using namespace bnz;
 
 extern "C" {
+
+int bnz_binarize_runs(const uint8_t *src, int height, int width, int channels, const bnz_run *runs, int nruns)
+{
+    return binarize_runs_host(src, height, width, channels, runs, nruns);
+}
 
 int bnz_sauvola(const uint8_t *src, int height, int width, int channels, int W, double k, double R, uint8_t *dst)
 {

@@ -1,14 +1,17 @@
 // batch.cu -- many uneven pages in one persistent launch (row a9).
 //
 // The strip-rows of all pages of a batch (strip-major within each page,
-// pages one after another) form one index range that the persistent grid
-// splits evenly, exactly as the single-page launch splits one page.  Each
-// CTA walks its range segment by segment; a segment never crosses a page, and
-// for each one the CTA reads the page's descriptor (TMA tensor map, geometry,
-// threshold constants) from device memory and runs the same producer /
-// consumer code as the single-page kernel, instantiated for the page's rule
-// and W mod 8.  Gray and RGB pages go to two launches (one per channel
-// count); with a CUDA graph the whole batch is replayed with one call.
+// pages one after another, largest window first) form one index range, a
+// work queue that the persistent CTAs take from in pieces: a device cursor
+// hands each CTA the next max(128, remaining / (2 * grid)) strip-rows (large
+// pieces first, small ones at the end, so the CTAs finish together whatever
+// the pages cost).  Each CTA walks its piece segment by segment; a segment
+// never crosses a page, and for each one the CTA reads the page's descriptor
+// (TMA tensor map, geometry, threshold constants) from device memory and runs
+// the same producer / consumer code as the single-page kernel, instantiated
+// for the page's rule and W mod 8.  Gray and RGB pages go to two launches
+// (one per channel count); with a CUDA graph the whole batch, cursor resets
+// included, is replayed with one call.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -19,6 +22,8 @@
 
 namespace bnz {
 namespace {
+
+constexpr size_t kCursorBytes = 128; // one work-queue cursor per channel group, 128-byte aligned
 
 struct alignas(128) PageDesc {
     CUtensorMap map;  // 128 bytes, 128-byte aligned (as cuda.h declares it): TMA reads it from global memory
@@ -49,22 +54,37 @@ __device__ __forceinline__ void dispatch(int sel, const CUtensorMap *map, const 
 #undef BNZ_CASE
 }
 
+constexpr long long kMinPiece = 128; // strip-rows of the smallest piece a CTA takes from the queue
+
 template <int CIN>
 __global__ void __launch_bounds__(NT, 1)
     batch_kernel(const PageDesc *__restrict__ pages, int npages, long long total, unsigned long long *stats,
-                 unsigned int *err_flag)
+                 unsigned int *err_flag, unsigned long long *cursor)
 {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ int s_abort;
     __shared__ FusedParams s_p;
+    __shared__ long long s_piece[2];
     if (threadIdx.x == 0) {
         init_barriers(smem, kEmpty);
         s_abort = 0;
     }
+    init_recip_table(smem);
     __syncthreads();
     uint64_t phase = 0, ephase = 0, eused = 0;
     uint32_t nfb = 0, nties = 0;
-    const long long L0 = total * blockIdx.x / gridDim.x, L1 = total * (blockIdx.x + 1) / gridDim.x;
+    for (;;) {
+    if (threadIdx.x == 0) { // the next piece of the queue
+        const long long seen = (long long)*reinterpret_cast<volatile unsigned long long *>(cursor);
+        const long long size = max(kMinPiece, (total - seen) / (2 * (long long)gridDim.x));
+        const long long st = (long long)atomicAdd(cursor, (unsigned long long)size);
+        s_piece[0] = st;
+        s_piece[1] = min(st + size, total);
+    }
+    __syncthreads();
+    const long long L0 = s_piece[0], L1 = s_piece[1];
+    if (L0 >= total)
+        break;
     int pi = 0;
     for (long long cur = L0; cur < L1;) {
         // the page holding strip-row cur (pages are few; ranges are sorted)
@@ -90,6 +110,9 @@ __global__ void __launch_bounds__(NT, 1)
         if (s_abort)
             break;
     }
+    if (s_abort)
+        break;
+    }
     report(stats, err_flag, nfb, nties, s_abort != 0);
 }
 
@@ -97,6 +120,7 @@ struct Group {
     int ch = 0;
     std::vector<PageDesc> host;
     PageDesc *dev = nullptr;
+    unsigned long long *cursor = nullptr; // the group's work-queue cursor (device, after the descriptors)
     bool owned = false; // dev allocated by the batch (freed with it)
     long long total = 0;
     size_t smem = 0;
@@ -129,8 +153,12 @@ int launch_group(const Group &g, unsigned long long *stats, unsigned int *err, c
     const PageDesc *pages = g.dev;
     int npages = (int)g.host.size();
     long long total = g.total;
-    void *args[] = {(void *)&pages, (void *)&npages, (void *)&total, (void *)&stats, (void *)&err};
-    cudaError_t e = cudaLaunchKernel(fn, dim3((unsigned)g.grid), dim3(NT), args, g.smem, stream);
+    unsigned long long *cursor = g.cursor;
+    cudaError_t e = cudaMemsetAsync(cursor, 0, sizeof(unsigned long long), stream);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "reset batch work queue");
+    void *args[] = {(void *)&pages, (void *)&npages, (void *)&total, (void *)&stats, (void *)&err, (void *)&cursor};
+    e = cudaLaunchKernel(fn, dim3((unsigned)g.grid), dim3(NT), args, g.smem, stream);
     if (e != cudaSuccess)
         return cuda_fail(e, "launch batch kernel");
     return BNZ_OK;
@@ -229,11 +257,14 @@ static int plan_batch(const bnz_page *pages, int n, unsigned long long *d_stats,
     for (Group &g : b->groups) {
         if (g.host.empty())
             continue;
-        // pages of the same kernel instance (rule, W mod 8) next to each other: the
-        // persistent CTAs walk contiguous ranges, so most of them then run the same
-        // code at any time instead of thrashing the instruction caches
-        std::stable_sort(g.host.begin(), g.host.end(),
-                         [](const PageDesc &a, const PageDesc &c) { return a.sel < c.sel; });
+        // largest window first (its pages cost the most per pixel: they should not be
+        // left for the end of the queue), and pages of the same kernel instance
+        // (rule, W mod 8) next to each other: the CTAs take consecutive pieces, so
+        // most of them then run the same code at any time instead of thrashing the
+        // instruction caches
+        std::stable_sort(g.host.begin(), g.host.end(), [](const PageDesc &a, const PageDesc &c) {
+            return a.p.W != c.p.W ? a.p.W > c.p.W : a.sel < c.sel;
+        });
         for (PageDesc &d : g.host) {
             const long long rows = d.t0;
             d.t0 = g.total;
@@ -263,9 +294,10 @@ int bnz_batch_create(const bnz_page *pages, int n, int use_graph, unsigned long 
         if (g.host.empty())
             continue;
         void *p = nullptr;
-        cudaError_t e = cudaMalloc(&p, g.host.size() * sizeof(PageDesc));
+        cudaError_t e = cudaMalloc(&p, g.host.size() * sizeof(PageDesc) + kCursorBytes);
         if (e == cudaSuccess) {
             g.dev = static_cast<PageDesc *>(p);
+            g.cursor = reinterpret_cast<unsigned long long *>(g.dev + g.host.size());
             g.owned = true;
             e = cudaMemcpy(g.dev, g.host.data(), g.host.size() * sizeof(PageDesc), cudaMemcpyHostToDevice);
         }
@@ -298,7 +330,7 @@ int bnz_batch_create(const bnz_page *pages, int n, int use_graph, unsigned long 
     return BNZ_OK;
 }
 
-size_t bnz_batch_desc_bytes(int n) { return n > 0 ? (size_t)n * sizeof(PageDesc) : 0; }
+size_t bnz_batch_desc_bytes(int n) { return n > 0 ? (size_t)n * sizeof(PageDesc) + 2 * kCursorBytes : 0; }
 
 int bnz_batch_create_async(const bnz_page *pages, int n, void *d_desc, size_t desc_bytes, void *stream,
                            unsigned long long *d_stats, bnz_batch **out)
@@ -310,10 +342,14 @@ int bnz_batch_create_async(const bnz_page *pages, int n, void *d_desc, size_t de
     if (rc != BNZ_OK)
         return rc;
     PageDesc *next = static_cast<PageDesc *>(d_desc);
-    for (Group &g : b->groups) {
+    unsigned long long *cursors = reinterpret_cast<unsigned long long *>(static_cast<uint8_t *>(d_desc) +
+                                                                         (size_t)n * sizeof(PageDesc));
+    for (int gi = 0; gi < 2; ++gi) {
+        Group &g = b->groups[gi];
         if (g.host.empty())
             continue;
         g.dev = next;
+        g.cursor = cursors + gi * (kCursorBytes / sizeof(unsigned long long));
         next += g.host.size();
         cudaError_t e = cudaMemcpyAsync(g.dev, g.host.data(), g.host.size() * sizeof(PageDesc),
                                         cudaMemcpyHostToDevice, static_cast<cudaStream_t>(stream));

@@ -19,6 +19,7 @@ namespace {
 // Fast decision of both rules for the lane's 16 pixels when every window of the
 // warp is W x W: the sums, V, sqrt(V), S1 and the pixel values are formed
 // once, then each rule's fp32 filter gives its own mask word and margin.
+template <bool SMALL>
 __device__ __forceinline__ void decide_lane_int_dual(const FusedParams &ps, const FusedParams &pn, uint32_t base1,
                                                      uint32_t base2, const uint32_t (&d1)[L], const uint32_t (&d2)[L],
                                                      const uint32_t (&fw)[4], uint32_t (&outs)[4], uint32_t (&outn)[4],
@@ -34,7 +35,7 @@ __device__ __forceinline__ void decide_lane_int_dual(const FusedParams &ps, cons
         float s[4], q[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e)
-            stats_int(base1, nb1, NB2, nW, d1[4 * qq + e], d2[4 * qq + e], s[e], q[e]);
+            stats_int<SMALL>(base1, nb1, NB2, nW, d1[4 * qq + e], d2[4 * qq + e], s[e], q[e]);
         const float2 s01 = make_float2(s[0], s[1]), s23 = make_float2(s[2], s[3]);
         const float2 q01 = make_float2(q[0], q[1]), q23 = make_float2(q[2], q[3]);
         const float2 a = filter2_int<BNZ_SAUVOLA>(s01, q01, nf01, ps);
@@ -81,11 +82,21 @@ __device__ __forceinline__ void consume_dual(const FusedParams &ps, const FusedP
             const bool lane_clip = g.active && g.xg0 < p.w && (yclip || g.xclip);
             uint32_t outs[4], outn[4];
             float mns = INFINITY, mnn = INFINITY;
+            const bool sm = small_window(p);
             if (!__any_sync(0xffffffffu, lane_clip)) {
-                decide_lane_int_dual(ps, pn, base1, base2, d1, d2, fw, outs, outn, mns, mnn);
+                if (sm)
+                    decide_lane_int_dual<true>(ps, pn, base1, base2, d1, d2, fw, outs, outn, mns, mnn);
+                else
+                    decide_lane_int_dual<false>(ps, pn, base1, base2, d1, d2, fw, outs, outn, mns, mnn);
             } else {
-                decide_lane_border<BNZ_SAUVOLA>(ps, y, g.xg0, base1, base2, d1, d2, fw, outs, mns);
-                decide_lane_border<BNZ_NIBLACK>(pn, y, g.xg0, base1, base2, d1, d2, fw, outn, mnn);
+                const float2 *tab = reinterpret_cast<const float2 *>(smem + kTabOffset);
+                if (sm) {
+                    decide_lane_border<BNZ_SAUVOLA, true>(ps, tab, y, g.xg0, base1, base2, d1, d2, fw, outs, mns);
+                    decide_lane_border<BNZ_NIBLACK, true>(pn, tab, y, g.xg0, base1, base2, d1, d2, fw, outn, mnn);
+                } else {
+                    decide_lane_border<BNZ_SAUVOLA, false>(ps, tab, y, g.xg0, base1, base2, d1, d2, fw, outs, mns);
+                    decide_lane_border<BNZ_NIBLACK, false>(pn, tab, y, g.xg0, base1, base2, d1, d2, fw, outn, mnn);
+                }
             }
             // rare: values inside a rule's fp32 margin take that rule's exact path
             if ((mns < ps.E || mnn < pn.E) && g.active) {
@@ -118,6 +129,7 @@ __global__ void __launch_bounds__(NT, 1)
         prefetch_tmap(&tmap);
         s_abort = 0;
     }
+    init_recip_table(smem);
     __syncthreads();
     uint64_t phase = 0, ephase = 0, eused = 0;
     uint32_t nfb = 0, nties_s = 0, nties_n = 0;

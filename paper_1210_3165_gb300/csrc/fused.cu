@@ -55,6 +55,7 @@ __global__ void __launch_bounds__(NT, 1)
         prefetch_tmap(&tmap);
         s_abort = 0;
     }
+    init_recip_table(smem);
     __syncthreads();
     uint64_t phase = 0;             // bit i: parity of the next completion of full barrier i
     uint64_t ephase = 0, eused = 0; // TMA issuer: free-signal parity, slots ever loaded
@@ -127,7 +128,7 @@ bool layout(int ch, int W, int tw, int NSS, FusedPlan *pl)
     const int nbar = std::max(pl->NS, pl->NSS);
     if (2 * nbar > kMaxBarriers)
         return false;
-    size_t off = round128((size_t)kMaxBarriers * 8); // same barrier area for every page of a batch
+    size_t off = round128((size_t)kTabOffset + kTabBytes); // barriers and reciprocal table, as in every kernel
     pl->off_ring = (uint32_t)off;
     off = round128(off + (size_t)pl->ring_rows * pl->SWP);
     pl->off_stage = (uint32_t)off;
@@ -344,11 +345,13 @@ void fill_fused_params(FusedParams *p, const FusedPlan &pl, int h, int w, int W,
     p->packed = packed ? 1 : 0;
     p->vec_ok = ((reinterpret_cast<uintptr_t>(d_dst) | dst_pitch) & 15u) == 0 ? 1 : 0;
     p->timeout_cycles = 4000000000ll; // ~2 s at 2 GHz
+    p->drain_cycles = 4000000000ll;
 }
 
 int launch_fused(const uint8_t *d_src, size_t src_pitch, int h, int w, int ch, int W, int rule, double k, double R,
                  uint8_t *d_dst, size_t dst_pitch, int packed, const bnz_tile *tile, cudaStream_t stream,
-                 unsigned long long *d_stats, unsigned int *d_err, int y_lo, int y_hi)
+                 unsigned long long *d_stats, unsigned int *d_err, int y_lo, int y_hi, bool force_wait,
+                 long long wait_cycles)
 {
     if (y_hi < 0)
         y_hi = h;
@@ -367,6 +370,8 @@ int launch_fused(const uint8_t *d_src, size_t src_pitch, int h, int w, int ch, i
     fill_fused_params(&p, pl, h, w, W, rule, k, R, d_dst, dst_pitch, packed, d_stats, d_err);
     p.y_lo = y_lo;
     p.y_hi = y_hi;
+    if (force_wait)
+        p.timeout_cycles = wait_cycles;
     const void *fn = kernel_for(ch, rule, W);
     rc = ensure_smem_optin(fn);
     if (rc != BNZ_OK)

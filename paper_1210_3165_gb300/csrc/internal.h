@@ -71,7 +71,8 @@ struct FusedParams {
     // the second stage decides by the sign of its f - t when |f - t| > Tdf =
     // 1e-9 + its own error bound + the fp64 definition's (double_float_cut)
     float Tdf;
-    long long timeout_cycles;
+    long long timeout_cycles; // limit of every wait but the final drain (<= 0: give up unless already complete)
+    long long drain_cycles;   // limit of the TMA issuer's final wait for its copies in flight
 };
 
 // Shape of the fused kernel for one page (strip width, ring, shared-memory
@@ -87,10 +88,11 @@ constexpr int kMaxBarriers = 96; // mbarriers reserved at the start of shared me
 int ensure_smem_optin(const void *fn);
 // Output rows [y_lo, y_hi) of the page (0, h: all); the kernel reads input rows
 // [y_lo - W/2, y_hi + W) at most, the ones past y_hi - 1 + (W - 1 - W/2) unused.
+// wait_cycles > 0 (or <= 0 with force_wait) overrides the waits' limit (self-test of the abort path).
 int launch_fused(const uint8_t *d_src, size_t src_pitch, int h, int w, int ch, int W, int rule, double k,
                  double R, uint8_t *d_dst, size_t dst_pitch, int packed, const bnz_tile *tile,
                  cudaStream_t stream, unsigned long long *d_stats, unsigned int *d_err, int y_lo = 0,
-                 int y_hi = -1);
+                 int y_hi = -1, bool force_wait = false, long long wait_cycles = 0);
 
 // Library-owned per-device error word (allocated on first use).
 int device_err_flag(unsigned int **flag);

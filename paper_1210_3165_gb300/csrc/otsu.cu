@@ -14,9 +14,13 @@
 // Three launches on the caller's stream, no host round trip:
 //   otsu_hist    the histogram: 8 warp-private 256-bin tables in shared memory
 //                per CTA, merged into the caller's scratch with 64-bit atomics;
-//   otsu_select  one CTA of 256 threads, thread t evaluates q(t); a block
-//                reduction takes the argmax and stores T in the scratch;
-//   otsu_mask    Eq. 2 with T read from the scratch: byte or packed mask.
+//                each thread takes 16 pixels per step (128-bit loads);
+//   otsu_select  one CTA of 256 threads: a block scan gives every thread t the
+//                exact prefixes n0, s0 of the levels below t, thread t
+//                evaluates q(t), a block reduction takes the argmax and stores
+//                T in the scratch;
+//   otsu_mask    Eq. 2 with T read from the scratch: byte or packed mask,
+//                16 pixels per thread and step.
 // Both passes over the page are HBM streams (1 or 3 B/px read each, 1 B/px or
 // 1/8 B/px written by the second).
 #include <algorithm>
@@ -31,19 +35,25 @@ constexpr int kOtsuThreads = 256;
 constexpr int kHistOffset = 0;    // uint64[256] in the scratch
 constexpr int kTOffset = 2048;    // int32 T in the scratch
 
-// Gray values of the 8 pixels starting at column x of row `row` (x + 8 <= w):
-// 8 bytes (gray) or 24 bytes (RGB) from a 16-byte aligned row start.
+// Gray values of the 16 pixels starting at column x of row `row` (x a
+// multiple of 16, x + 16 <= w): 16 bytes (gray) or 48 bytes (RGB), 128-bit
+// loads from a 16-byte aligned row start.
 template <int CIN>
-__device__ __forceinline__ void load8(const uint8_t *row, int x, uint32_t &g0, uint32_t &g1)
+__device__ __forceinline__ void load16(const uint8_t *row, int x, uint32_t (&g)[4])
 {
     if (CIN == 1) {
-        const uint2 v = *reinterpret_cast<const uint2 *>(row + x);
-        g0 = v.x;
-        g1 = v.y;
+        const uint4 v = *reinterpret_cast<const uint4 *>(row + x);
+        g[0] = v.x;
+        g[1] = v.y;
+        g[2] = v.z;
+        g[3] = v.w;
     } else {
-        const uint32_t *p = reinterpret_cast<const uint32_t *>(row + 3 * x);
-        g0 = gray4(p[0], p[1], p[2]);
-        g1 = gray4(p[3], p[4], p[5]);
+        const uint4 *p = reinterpret_cast<const uint4 *>(row + 3 * x);
+        const uint4 a = p[0], b = p[1], c = p[2];
+        g[0] = gray4(a.x, a.y, a.z);
+        g[1] = gray4(a.w, b.x, b.y);
+        g[2] = gray4(b.z, b.w, c.x);
+        g[3] = gray4(c.y, c.z, c.w);
     }
 }
 
@@ -66,21 +76,21 @@ __global__ void __launch_bounds__(kOtsuThreads)
         (&sh[0][0])[i] = 0;
     __syncthreads();
     uint32_t *mine = sh[warp];
-    const int groups = (w + 7) / 8; // 8-pixel groups per row
+    const int groups = (w + 15) / 16; // 16-pixel groups per row
     const long long total = (long long)groups * h;
     for (long long gi = (long long)blockIdx.x * kOtsuThreads + threadIdx.x; gi < total;
          gi += (long long)gridDim.x * kOtsuThreads) {
         const int y = (int)(gi / groups);
-        const int x = (int)(gi - (long long)y * groups) * 8;
+        const int x = (int)(gi - (long long)y * groups) * 16;
         const uint8_t *row = src + (long long)y * pitch;
-        if (x + 8 <= w) {
-            uint32_t g0, g1;
-            load8<CIN>(row, x, g0, g1);
+        if (x + 16 <= w) {
+            uint32_t g[4];
+            load16<CIN>(row, x, g);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                atomicAdd(&mine[(g0 >> (8 * j)) & 0xffu], 1u);
-                atomicAdd(&mine[(g1 >> (8 * j)) & 0xffu], 1u);
-            }
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    atomicAdd(&mine[(g[q] >> (8 * j)) & 0xffu], 1u);
         } else {
             for (int xx = x; xx < w; ++xx)
                 atomicAdd(&mine[gray_at<CIN>(row, xx)], 1u);
@@ -99,23 +109,42 @@ __global__ void __launch_bounds__(kOtsuThreads)
 
 __global__ void __launch_bounds__(kOtsuThreads) otsu_select(const unsigned long long *hist, int *T_out)
 {
-    __shared__ unsigned long long sn[256], ss[256];
+    __shared__ unsigned long long wn[kOtsuThreads / 32], ws[kOtsuThreads / 32], tot[2];
     __shared__ double sq[kOtsuThreads / 32];
     __shared__ int st[kOtsuThreads / 32];
-    const int t = threadIdx.x;
-    sn[t] = hist[t];
-    ss[t] = hist[t] * (unsigned long long)t;
-    __syncthreads();
-    // totals and the prefixes below t (levels 0 .. t-1), 64-bit exact (N <= 2^28)
-    unsigned long long N = 0, S = 0, n0 = 0, s0 = 0;
-    for (int i = 0; i < 256; ++i) {
-        N += sn[i];
-        S += ss[i];
-        if (i < t) {
-            n0 += sn[i];
-            s0 += ss[i];
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const unsigned long long c = hist[t], v = c * (unsigned long long)t;
+    // inclusive block scan of (count, level sum), exact 64-bit (N <= 2^28)
+    unsigned long long cn = c, cs = v;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const unsigned long long a = __shfl_up_sync(0xffffffffu, cn, off);
+        const unsigned long long b = __shfl_up_sync(0xffffffffu, cs, off);
+        if (lane >= off) {
+            cn += a;
+            cs += b;
         }
     }
+    if (lane == 31) {
+        wn[wid] = cn;
+        ws[wid] = cs;
+    }
+    __syncthreads();
+    if (t == 0) { // exclusive offsets of the 8 warps, and the totals
+        unsigned long long an = 0, as = 0;
+        for (int k = 0; k < kOtsuThreads / 32; ++k) {
+            const unsigned long long xn = wn[k], xs = ws[k];
+            wn[k] = an;
+            ws[k] = as;
+            an += xn;
+            as += xs;
+        }
+        tot[0] = an;
+        tot[1] = as;
+    }
+    __syncthreads();
+    const unsigned long long N = tot[0], S = tot[1];
+    const unsigned long long n0 = cn + wn[wid] - c, s0 = cs + ws[wid] - v; // levels 0 .. t-1
     const unsigned long long n1 = N - n0;
     double q = -1.0; // t = 0 and splits with an empty class take no part
     if (t > 0 && n0 > 0 && n1 > 0) {
@@ -157,38 +186,35 @@ __global__ void __launch_bounds__(kOtsuThreads)
               int packed, int vec_ok)
 {
     const uint32_t T = (uint32_t)*T_in;
-    const int groups = (w + 7) / 8;
+    // byte-wise f >= T for four packed gray values: __vcmpgeu4 gives 0xFF / 0x00 per byte
+    const uint32_t T4 = T > 255u ? 0u : T * 0x01010101u;
+    const int groups = (w + 15) / 16;
     const long long total = (long long)groups * h;
     for (long long gi = (long long)blockIdx.x * kOtsuThreads + threadIdx.x; gi < total;
          gi += (long long)gridDim.x * kOtsuThreads) {
         const int y = (int)(gi / groups);
-        const int x = (int)(gi - (long long)y * groups) * 8;
+        const int x = (int)(gi - (long long)y * groups) * 16;
         const uint8_t *row = src + (long long)y * pitch;
         uint8_t *drow = dst + (long long)y * dst_pitch;
-        if (x + 8 <= w) {
-            uint32_t g0, g1;
-            load8<CIN>(row, x, g0, g1);
-            uint32_t bits = 0; // bit j <-> pixel x + j, 1 <-> 255 (Eq. 2: f >= T)
+        if (x + 16 <= w) {
+            uint32_t g[4], m[4];
+            load16<CIN>(row, x, g);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                bits |= (((g0 >> (8 * j)) & 0xffu) >= T ? 1u : 0u) << j;
-                bits |= (((g1 >> (8 * j)) & 0xffu) >= T ? 1u : 0u) << (j + 4);
-            }
+            for (int q = 0; q < 4; ++q)
+                m[q] = T == 0u ? 0xffffffffu : __vcmpgeu4(g[q], T4);
             if (packed) {
-                drow[x >> 3] = (uint8_t)bits;
-            } else {
-                // bit j -> byte j of 0x00 / 0xFF
-                const uint32_t lo = ((bits & 15u) * 0x00204081u & 0x01010101u) * 0xffu;
-                const uint32_t hi = ((bits >> 4) * 0x00204081u & 0x01010101u) * 0xffu;
-                if (vec_ok) {
-                    *reinterpret_cast<uint2 *>(drow + x) = make_uint2(lo, hi);
-                } else {
+                uint32_t bits = 0; // bit j <-> pixel x + j: the msb of each byte
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        drow[x + j] = (uint8_t)(lo >> (8 * j));
-                        drow[x + 4 + j] = (uint8_t)(hi >> (8 * j));
-                    }
-                }
+                for (int q = 0; q < 4; ++q)
+                    bits |= ((((m[q] >> 7) & 0x01010101u) * 0x01020408u) >> 24) << (4 * q);
+                drow[x >> 3] = (uint8_t)bits;
+                drow[(x >> 3) + 1] = (uint8_t)(bits >> 8);
+            } else if (vec_ok) {
+                *reinterpret_cast<uint4 *>(drow + x) = make_uint4(m[0], m[1], m[2], m[3]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    drow[x + j] = (uint8_t)(m[j >> 2] >> (8 * (j & 3)));
             }
         } else {
             uint32_t bits = 0;
@@ -199,8 +225,11 @@ __global__ void __launch_bounds__(kOtsuThreads)
                 else
                     drow[xx] = f >= T ? 255 : 0;
             }
-            if (packed)
+            if (packed) {
                 drow[x >> 3] = (uint8_t)bits;
+                if (w - x > 8)
+                    drow[(x >> 3) + 1] = (uint8_t)(bits >> 8);
+            }
         }
     }
 }
@@ -219,7 +248,7 @@ int launch_otsu(const uint8_t *d_src, size_t src_pitch, int h, int w, int ch, ui
     cudaError_t e = cudaMemsetAsync(hist, 0, 256 * sizeof(unsigned long long), stream);
     if (e != cudaSuccess)
         return cuda_fail(e, "clear histogram");
-    const long long groups = (long long)((w + 7) / 8) * h;
+    const long long groups = (long long)((w + 15) / 16) * h;
     // a few CTAs per SM, grid-stride: every CTA merges one set of 256 bins
     const int grid = (int)std::max<long long>(1, std::min<long long>((long long)sms * 4,
                                                                       (groups + kOtsuThreads - 1) / kOtsuThreads));
@@ -228,7 +257,7 @@ int launch_otsu(const uint8_t *d_src, size_t src_pitch, int h, int w, int ch, ui
     else
         otsu_hist<3><<<grid, kOtsuThreads, 0, stream>>>(d_src, (long long)src_pitch, h, w, hist);
     otsu_select<<<1, kOtsuThreads, 0, stream>>>(hist, T);
-    const int vec_ok = ((reinterpret_cast<uintptr_t>(d_dst) | dst_pitch) & 7u) == 0 ? 1 : 0;
+    const int vec_ok = ((reinterpret_cast<uintptr_t>(d_dst) | dst_pitch) & 15u) == 0 ? 1 : 0;
     if (ch == 1)
         otsu_mask<1><<<grid, kOtsuThreads, 0, stream>>>(d_src, (long long)src_pitch, h, w, T, d_dst,
                                                          (long long)dst_pitch, packed, vec_ok);

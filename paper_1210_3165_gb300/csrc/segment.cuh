@@ -174,7 +174,7 @@ __device__ __forceinline__ void produce(const CUtensorMap *tmap, const FusedPara
         // the last load of each slot (earlier ones completed before its reuse)
         const int q0 = max(0, j - nbar);
         for (int q = q0, qs = q0 % nbar; q < j; ++q, qs = (qs + 1 == nbar) ? 0 : qs + 1)
-            (void)mbar_wait_bounded(&full[qs], (uint32_t)(((phase >> qs) & 1ull) ^ 1ull), p.timeout_cycles);
+            (void)mbar_wait_bounded(&full[qs], (uint32_t)(((phase >> qs) & 1ull) ^ 1ull), p.drain_cycles);
         return;
     }
 
@@ -492,17 +492,32 @@ __device__ __forceinline__ void lane_sums_again(const FusedParams &p, const Lane
 // sqrt(V) by sqrt.approx from V = n*S2 - S1^2, exact in 64 bits and rounded to
 // fp32 (hi word exact, lo word rounded, one more rounding in the fma: relative
 // error <= 2u), and S1 as fp32 (exact, S1 < 2^24).
+// With SMALL (W <= 22, so V <= n^2 * 127.5^2 < 2^32) V is exact in 32 bits
+// (modular arithmetic gives the exact value) and rounds to fp32 once.
+template <bool SMALL>
 __device__ __forceinline__ void stats_int(uint32_t base1, int nb1, long long NB2, int nW, uint32_t d1, uint32_t d2,
                                           float &s1f, float &sq)
 {
     const uint32_t S1 = base1 + d1;
-    const int nS1 = nb1 - (int)d1;                              // -S1
-    const long long P = NB2 + (long long)nW * (int)d2;          // n * S2
-    const long long V = P + (long long)(int)S1 * nS1;           // n * S2 - S1^2 >= 0
-    const float vf = __fmaf_rn(__uint2float_rn((uint32_t)((unsigned long long)V >> 32)), 4294967296.0f,
-                               __uint2float_rn((uint32_t)V));
+    float vf;
+    if (SMALL) {
+        const uint32_t V = (uint32_t)NB2 + (uint32_t)nW * d2 - S1 * S1;
+        vf = __uint2float_rn(V);
+    } else {
+        const int nS1 = nb1 - (int)d1;                              // -S1
+        const long long P = NB2 + (long long)nW * (int)d2;          // n * S2
+        const long long V = P + (long long)(int)S1 * nS1;           // n * S2 - S1^2 >= 0
+        vf = __fmaf_rn(__uint2float_rn((uint32_t)((unsigned long long)V >> 32)), 4294967296.0f,
+                       __uint2float_rn((uint32_t)V));
+    }
     sq = sqrt_approx(vf);
     s1f = __uint2float_rn(S1);
+}
+
+// W <= 22: the window variance fits 32 bits
+__device__ __forceinline__ bool small_window(const FusedParams &p)
+{
+    return p.W <= 22;
 }
 
 // Two pixels' fp32 filters, nd ~ t - f (= -d), for an unclipped window:
@@ -538,7 +553,7 @@ __device__ __forceinline__ void neg_bytes(uint32_t w, float2 &n01, float2 &n23)
 
 // Fast decision of the lane's 16 pixels when every window of the warp is W x W.
 // outw: byte t of word t/4 = 255 (white) or 0; mn: smallest |nd|.
-template <int RULE>
+template <int RULE, bool SMALL>
 __device__ __forceinline__ void decide_lane_int(const FusedParams &p, uint32_t base1, uint32_t base2,
                                                 const uint32_t (&d1)[L], const uint32_t (&d2)[L],
                                                 const uint32_t (&fw)[4], uint32_t (&outw)[4], float &mn)
@@ -553,7 +568,7 @@ __device__ __forceinline__ void decide_lane_int(const FusedParams &p, uint32_t b
         float s[4], q[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e)
-            stats_int(base1, nb1, NB2, nW, d1[4 * qq + e], d2[4 * qq + e], s[e], q[e]);
+            stats_int<SMALL>(base1, nb1, NB2, nW, d1[4 * qq + e], d2[4 * qq + e], s[e], q[e]);
         const float2 a = filter2_int<RULE>(make_float2(s[0], s[1]), make_float2(q[0], q[1]), nf01, p);
         const float2 c = filter2_int<RULE>(make_float2(s[2], s[3]), make_float2(q[2], q[3]), nf23, p);
         mn = fminf(mn, fminf(fminf(fabsf(a.x), fabsf(a.y)), fminf(fabsf(c.x), fabsf(c.y))));
@@ -586,24 +601,82 @@ __device__ __forceinline__ int clipped_rows(const FusedParams &p, int y)
     return min(y + p.r_hi, p.h - 1) - max(y - p.r_lo, 0) + 1;
 }
 
+// Table of 1/j and 1/j^2 (fp32, correctly rounded) for j = 1..BNZ_MAX_W, at
+// the start of shared memory after the barriers: the clipped windows' constants
+// come from it instead of a reciprocal per pixel.
+constexpr int kTabOffset = kMaxBarriers * 8;
+constexpr int kTabBytes = (BNZ_MAX_W + 1) * 8;
+
+__device__ __forceinline__ void init_recip_table(uint8_t *smem)
+{
+    float2 *tab = reinterpret_cast<float2 *>(smem + kTabOffset);
+    for (int j = threadIdx.x; j <= BNZ_MAX_W; j += blockDim.x)
+        tab[j] = j ? make_float2(__fdiv_rn(1.0f, (float)j), __fdiv_rn(1.0f, (float)(j * j))) : make_float2(0.f, 0.f);
+}
+
 // Fast decision of the lane's 16 pixels in a warp that touches the image
-// border: each pixel with its own clipped count.
-template <int RULE>
-__device__ __forceinline__ void decide_lane_border(const FusedParams &p, int y, int xg0, uint32_t base1,
-                                                   uint32_t base2, const uint32_t (&d1)[L], const uint32_t (&d2)[L],
-                                                   const uint32_t (&fw)[4], uint32_t (&outw)[4], float &mn)
+// border: each pixel with its own clipped count n = nr * nc, and its
+// constants from the reciprocal table:
+//   Sauvola c0 = ((1-k)/nr)(1/nc), c1 = (k/(R nr^2))(1/nc^2)   nd = S1 (c0 + c1 sqrt(V)) - f
+//   Niblack c0 = (1/nr)(1/nc),     c1 = (k/nr)(1/nc)          nd = S1 c0 + (c1 sqrt(V) - f)
+// Each constant is within 5u of its value (u = 2^-24), inside the error
+// budget decision_margin allows a clipped window.
+template <int RULE, bool SMALL>
+__device__ __forceinline__ void decide_lane_border(const FusedParams &p, const float2 *tab, int y, int xg0,
+                                                   uint32_t base1, uint32_t base2, const uint32_t (&d1)[L],
+                                                   const uint32_t (&d2)[L], const uint32_t (&fw)[4],
+                                                   uint32_t (&outw)[4], float &mn)
 {
     const int nr = clipped_rows(p, y);
+    const float2 tr = tab[nr];
+    const float r0 = RULE == BNZ_SAUVOLA ? __fmul_rn(p.omk, tr.x) : tr.x;
+    const float r1 = RULE == BNZ_SAUVOLA ? __fmul_rn(p.kR, tr.y) : __fmul_rn(p.kf, tr.x);
+    const int a = xg0 + p.r_hi, bl = xg0 - p.r_lo;
 #pragma unroll
     for (int qq = 0; qq < 4; ++qq) {
-        float nd[4];
+        float2 nf01, nf23;
+        neg_bytes(fw[qq], nf01, nf23);
+        float s[4], q[4], c0[4], c1[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const int t = 4 * qq + e;
-            const int xg = xg0 + t;
-            nd[e] = filter_general<RULE>(byte_dyn(fw[qq], e), clipped_n(p, nr, xg), base1 + d1[t], base2 + d2[t], p);
-            mn = fminf(mn, xg < p.w ? fabsf(nd[e]) : INFINITY);
+            // pixels past the image's right edge (results discarded) would give nc <= 0: keep the
+            // table index in [1, W]
+            const int nc = max(min(a + t, p.w - 1) - max(bl + t, 0) + 1, 1);
+            const uint32_t n = (uint32_t)(nr * nc);
+            const float2 tc = tab[nc];
+            c0[e] = __fmul_rn(r0, tc.x);
+            c1[e] = __fmul_rn(r1, RULE == BNZ_SAUVOLA ? tc.y : tc.x);
+            const uint32_t S1 = base1 + d1[t], S2 = base2 + d2[t];
+            float vf;
+            if (SMALL) {
+                vf = __uint2float_rn(n * S2 - S1 * S1);
+            } else {
+                const long long V = (long long)((unsigned long long)n * S2) + (long long)(int)S1 * -(int)S1;
+                vf = __fmaf_rn(__uint2float_rn((uint32_t)((unsigned long long)V >> 32)), 4294967296.0f,
+                               __uint2float_rn((uint32_t)V));
+            }
+            q[e] = sqrt_approx(vf);
+            s[e] = __uint2float_rn(S1);
         }
+        float2 nd01, nd23;
+        if (RULE == BNZ_SAUVOLA) {
+            nd01 = __ffma2_rn(make_float2(s[0], s[1]),
+                              __ffma2_rn(make_float2(c1[0], c1[1]), make_float2(q[0], q[1]), make_float2(c0[0], c0[1])),
+                              nf01);
+            nd23 = __ffma2_rn(make_float2(s[2], s[3]),
+                              __ffma2_rn(make_float2(c1[2], c1[3]), make_float2(q[2], q[3]), make_float2(c0[2], c0[3])),
+                              nf23);
+        } else {
+            nd01 = __ffma2_rn(make_float2(s[0], s[1]), make_float2(c0[0], c0[1]),
+                              __ffma2_rn(make_float2(c1[0], c1[1]), make_float2(q[0], q[1]), nf01));
+            nd23 = __ffma2_rn(make_float2(s[2], s[3]), make_float2(c0[2], c0[3]),
+                              __ffma2_rn(make_float2(c1[2], c1[3]), make_float2(q[2], q[3]), nf23));
+        }
+        const float nd[4] = {nd01.x, nd01.y, nd23.x, nd23.y};
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            mn = fminf(mn, xg0 + 4 * qq + e < p.w ? fabsf(nd[e]) : INFINITY);
         outw[qq] = sign_bytes(nd[0], nd[1], nd[2], nd[3]);
     }
 }
@@ -724,10 +797,19 @@ __device__ __forceinline__ void consume(const FusedParams &p, const Segment &sg,
             const bool lane_clip = g.active && g.xg0 < p.w && (yclip || g.xclip);
             uint32_t outw[4];
             float mn = INFINITY; // smallest |nd| of the lane's pixels inside the image
-            if (!__any_sync(0xffffffffu, lane_clip))
-                decide_lane_int<RULE>(p, base1, base2, d1, d2, fw, outw, mn);
-            else
-                decide_lane_border<RULE>(p, y, g.xg0, base1, base2, d1, d2, fw, outw, mn);
+            const bool sm = small_window(p);
+            if (!__any_sync(0xffffffffu, lane_clip)) {
+                if (sm)
+                    decide_lane_int<RULE, true>(p, base1, base2, d1, d2, fw, outw, mn);
+                else
+                    decide_lane_int<RULE, false>(p, base1, base2, d1, d2, fw, outw, mn);
+            } else {
+                const float2 *tab = reinterpret_cast<const float2 *>(smem + kTabOffset);
+                if (sm)
+                    decide_lane_border<RULE, true>(p, tab, y, g.xg0, base1, base2, d1, d2, fw, outw, mn);
+                else
+                    decide_lane_border<RULE, false>(p, tab, y, g.xg0, base1, base2, d1, d2, fw, outw, mn);
+            }
             if (mn < p.E && g.active) { // rare: a value inside the fp32 margin
                 uint32_t e1[L], e2[L];
                 lane_sums_again<KO, KI, WM8>(p, g, C1, e1, e2);
@@ -755,6 +837,7 @@ __device__ __forceinline__ void run_segment(const CUtensorMap *tmap, const Fused
 // Kernel prologue: full and empty barriers for up to `nbar` ring/staging slots.
 __device__ __forceinline__ void init_barriers(uint8_t *smem, int nbar)
 {
+    // (thread 0 only; the reciprocal table is filled by all threads, init_recip_table)
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
     for (int i = 0; i < nbar; ++i) {
         mbar_init(&bars[i], 1);

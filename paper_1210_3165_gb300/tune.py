@@ -1,12 +1,16 @@
-"""Autotuner for the fused kernel's strip width.
+"""Autotuner for the fused kernel's tile shape.
 
-For each (channels, W) it times the fused kernel with every strip width that
-fits shared memory (512, 256, 128 output columns) on a synthetic page and
-keeps the fastest.  The page is tall (4096 rows by default) so that, as in a
-batch or a stream of pages, the W rows of warm-up at the top of each strip
-segment are amortized; on short pages narrower strips win only because they
-give each CTA more rows per segment.  Results are cached as JSON keyed by GPU name, so tuning is
-done once per machine; batches take their per-page ``tile_w`` from the table.
+For each (channels, W) it times the fused kernel on a synthetic page with
+every strip width that fits shared memory (512, 256, 128 output columns) and
+several heights of the rows each CTA walks (the library's default split over
+one CTA per SM, or a fixed number of rows per CTA, which sets the grid) and
+keeps the fastest pair.  The page is tall (4096 rows by default) so that, as
+in a batch or a stream of pages, the W rows of warm-up at the top of each
+strip segment are amortized.  Results are cached as JSON keyed by GPU name,
+library version and a hash of the kernel sources, so tuning is done once per
+machine and build; single-page calls take ``bnz_tile(tile_w, tile_h)`` from
+the table (``tile_shape_for``) and batches their per-page ``tile_w``
+(``tile_for``).
 """
 from __future__ import annotations
 
@@ -17,6 +21,20 @@ from . import (BNZ_SAUVOLA, BnzError, alloc_pitched, bnz_binarize_dev, bnz_tile,
 
 DEFAULT_WINDOWS = (15, 25, 31, 45, 61, 75, 101)
 TILE_WIDTHS = (512, 256, 128)
+TILE_HEIGHTS = (0, 128, 256, 512)   # rows per CTA; 0 = the library's split over one CTA per SM
+
+
+def build_key() -> str:
+    """Library version and a hash of the kernel sources: a table tuned on another build is not reused."""
+    import hashlib
+    from . import bnz_version
+    h = hashlib.sha256()
+    csrc = os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + f.read())
+    return f"v{bnz_version()}-{h.hexdigest()[:12]}"
 
 
 def cache_path(gpu_name: str | None = None) -> str:
@@ -25,7 +43,8 @@ def cache_path(gpu_name: str | None = None) -> str:
     base = os.environ.get("BNZ_TUNE_CACHE") or os.path.join(os.path.expanduser("~"), ".cache", "bnz")
     if base.endswith(".json"):
         return base
-    return os.path.join(base, "tune-" + "".join(c if c.isalnum() else "_" for c in name) + ".json")
+    tag = "".join(c if c.isalnum() else "_" for c in name)
+    return os.path.join(base, f"tune-{tag}-{build_key()}.json")
 
 
 def _time_one(src, out, W, tile, reps):
@@ -45,13 +64,14 @@ def _time_one(src, out, W, tile, reps):
 
 
 def tune(windows=DEFAULT_WINDOWS, channels=(1, 3), shape=(4096, 4096), reps: int = 7, seed: int = 4,
-         save: bool = True) -> dict:
-    """Return {"1": {"15": 512, ...}, "3": {...}} and cache it unless save=False."""
+         save: bool = True, heights=TILE_HEIGHTS) -> dict:
+    """Return {"1": {"15": {"tile_w": 512, "tile_h": 0, "ms": ...}, ...}, "3": {...}} and cache it unless
+    save=False."""
     import torch
     import synth
     from . import to_device_pitched
     load()
-    table: dict = {"gpu": torch.cuda.get_device_name(), "shape": list(shape)}
+    table: dict = {"gpu": torch.cuda.get_device_name(), "shape": list(shape), "build": build_key()}
     for ch in channels:
         page = synth.page(shape[0], shape[1], seed, synth.STAINS if ch == 3 else synth.DOC, ch)
         src = to_device_pitched(page)
@@ -60,11 +80,13 @@ def tune(windows=DEFAULT_WINDOWS, channels=(1, 3), shape=(4096, 4096), reps: int
         for W in windows:
             timings = {}
             for tw in TILE_WIDTHS:
-                try:
-                    timings[tw] = _time_one(src, out, W, bnz_tile(tw, 0, 0, 0), reps)
-                except BnzError:
-                    continue  # does not fit shared memory
-            best[str(W)] = min(timings, key=timings.get)
+                for th in heights:
+                    try:
+                        timings[(tw, th)] = _time_one(src, out, W, bnz_tile(tw, th, 0, 0), reps)
+                    except BnzError:
+                        break  # this width does not fit shared memory
+            (tw, th) = min(timings, key=timings.get)
+            best[str(W)] = {"tile_w": tw, "tile_h": th, "ms": round(timings[(tw, th)], 5)}
         table[str(ch)] = best
     if save:
         path = cache_path()
@@ -82,10 +104,22 @@ def load_table(path: str | None = None) -> dict | None:
         return None
 
 
-def tile_for(table: dict | None, channels: int, W: int) -> int:
-    """Tuned strip width for the nearest tuned W (0 = let the library choose)."""
+def _entry(table: dict | None, channels: int, W: int) -> dict | None:
     if not table or str(channels) not in table:
-        return 0
+        return None
     entries = {int(k): v for k, v in table[str(channels)].items()}
     nearest = min(entries, key=lambda w: (abs(w - W), w))
-    return int(entries[nearest])
+    e = entries[nearest]
+    return e if isinstance(e, dict) else {"tile_w": int(e), "tile_h": 0}
+
+
+def tile_for(table: dict | None, channels: int, W: int) -> int:
+    """Tuned strip width for the nearest tuned W (0 = let the library choose)."""
+    e = _entry(table, channels, W)
+    return int(e["tile_w"]) if e else 0
+
+
+def tile_shape_for(table: dict | None, channels: int, W: int):
+    """bnz_tile(tile_w, tile_h) tuned for the nearest W, or None (library default)."""
+    e = _entry(table, channels, W)
+    return bnz_tile(int(e["tile_w"]), int(e["tile_h"]), 0, 0) if e else None

@@ -216,3 +216,61 @@ def test_bounded_wait_gives_up_and_context_stays_usable(bnz):
     assert rc == 0 and to.value == 0 and 0 <= cyc.value < limit
     img = synth.page(300, 257, 21, synth.DOC, 1)
     check(bnz, img, 15, "sauvola", 0.5)
+
+
+def test_gray_conversion_exhaustive(bnz):
+    """Eq. 1 as the fused kernel's producers compute it (byte dot products and a multiply-high by the
+    reciprocal of 1000), over every one of the 2^24 (r, g, b) triples, equals the oracle's integer rule;
+    a ragged tail of 3 pixels goes through the one-pixel form."""
+    import ctypes
+    i = np.arange(1 << 24, dtype=np.uint32)
+    rgb = np.stack([(i >> 16) & 255, (i >> 8) & 255, i & 255], axis=-1).astype(np.uint8).reshape(4096, 4096, 3)
+    ref = oracle.gray(rgb).reshape(-1)
+    d_rgb = torch.from_numpy(rgb.reshape(-1)).cuda()
+    for npix in (1 << 24, (1 << 24) - 1):
+        d_gray = torch.zeros(npix, dtype=torch.uint8, device="cuda")
+        rc = bnz.load().bnz_selftest_gray(ctypes.c_void_p(d_rgb.data_ptr()), npix, ctypes.c_void_p(d_gray.data_ptr()),
+                                          None)
+        assert rc == 0, bnz.bnz_last_error()
+        torch.cuda.synchronize()
+        got = d_gray.cpu().numpy()
+        bad = np.flatnonzero(got != ref[:npix])
+        assert bad.size == 0, f"{bad.size} triples differ, first {rgb.reshape(-1, 3)[bad[0]]}"
+
+
+@pytest.mark.parametrize("ch,W,rule", [(3, 31, "sauvola"), (1, 101, "niblack")])
+def test_fused_kernel_abort_path(bnz, ch, W, rule):
+    """The fused kernel's own waits made to give up (self-test entry: a wait gives up unless its copy has
+    already landed, while the final drain of copies in flight keeps its normal limit): the call reports
+    BNZ_ETIMEOUT and the timed-out CTAs in the counters; the context stays usable, and the next normal launch on
+    the same buffers is bit-exact.  Nothing traps, faults or waits forever."""
+    import ctypes
+    img = synth.page(1500, 2100, 41, synth.STAINS if ch == 3 else synth.DOC, ch)
+    d = bnz.to_device_pitched(img)
+    out = bnz.alloc_pitched(img.shape[0], img.shape[1])
+    stats = torch.zeros(4, dtype=torch.int64, device="cuda")
+    k = 0.5 if rule == "sauvola" else -0.2
+    rid = bnz.BNZ_SAUVOLA if rule == "sauvola" else bnz.BNZ_NIBLACK
+    s = torch.cuda.current_stream()
+    rc = bnz.load().bnz_selftest_fused_timeout(d.data_ptr(), d.stride(0), img.shape[0], img.shape[1], ch, W, rid,
+                                               k, 128.0, out.data_ptr(), out.stride(0), ctypes.c_void_p(s.cuda_stream),
+                                               stats.data_ptr())
+    assert rc == bnz.BNZ_ETIMEOUT, (rc, bnz.bnz_last_error())
+    assert int(stats[2]) > 0
+    check(bnz, img, W, rule, k)
+
+
+@pytest.mark.parametrize("h,w,ch", [(2050, 1100, 3), (700, 900, 1)])
+def test_host_one_page_several_settings(bnz, h, w, ch):
+    """bnz_binarize_runs: one upload of the page, every setting's mask equal to the oracle's (and to the
+    one-setting host calls); the larger page goes in row bands."""
+    img = synth.page(h, w, 61, synth.STAINS if ch == 3 else synth.DOC, ch)
+    runs = [(15, "sauvola", 0.5, 128.0), (101, "niblack", -0.2, 128.0), (31, "sauvola", 0.3, 64.0),
+            (4, "niblack", 0.1, 1.0)]
+    masks = bnz.binarize_runs(img, runs)
+    for (W, rule, k, R), got in zip(runs, masks):
+        rid = oracle.SAUVOLA if rule == "sauvola" else oracle.NIBLACK
+        ref, _ = oracle.binarize(img, W, rid, k, R, threads=NTHREADS)
+        assert not np.any(got != ref), f"{rule} W={W}: {int(np.sum(got != ref))} mismatches"
+    again = bnz.binarize_runs(img, runs[:1])
+    np.testing.assert_array_equal(again[0], masks[0])

@@ -198,6 +198,25 @@ def test_worked_example_golden():
         assert ms[y, x] == p["g_sauvola"] and mn[y, x] == p["g_niblack"]
 
 
+def test_worked_example_derivation_matches_fixture():
+    """Every number of the worked example is re-derived from the definitions with exact arithmetic
+    (tests/golden/derive_worked_3x3.py: rationals and a 60-digit square root, no oracle call)."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("derive_worked_3x3", os.path.join(GOLDEN, "derive_worked_3x3.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    g = json.load(open(os.path.join(GOLDEN, "worked_3x3.json")))
+    assert g["image"] == mod.IMAGE and g["W"] == mod.W
+    derived = mod.derive()
+    assert len(derived) == len(g["pixels"])
+    for p, q in zip(g["pixels"], derived):
+        for key, v in p.items():
+            if isinstance(v, float):
+                assert v == pytest.approx(q[key], abs=1e-12), key
+            else:
+                assert v == q[key], key
+
+
 # ---------------------------------------------------------------------------
 # closed forms and special cases
 # ---------------------------------------------------------------------------
