@@ -15,7 +15,15 @@ is a single IEEE-rounded step in the order the C source states:
 * the global rule of Eq. 2 with Otsu's threshold (cited in Sec. 1; Otsu's
   published definition: the T maximising the between-class variance of the
   gray histogram, exact 128-bit class difference, fp64 criterion, smallest T
-  among equal values).
+  among equal values);
+* the reduced-set rule of Eq. 5 (Sec. 2): m', s' over a structure S' of O(W)
+  window pixels.  Fig. 1, which draws the paper's six structures, is not
+  available; the structures GS1..GS6 here are proposed by this project (cross,
+  diagonals, star, frame, frame + cross, frame + diagonals; GS0 = the whole
+  window).  Their agreement with the paper's accuracy figures is therefore
+  unpinned; the oracle itself is pinned to brute-force set enumeration,
+  closed forms and to Eq. 4 (GS0);
+* the confusion counts behind the F-measure of Eq. 6.
 
 Pins (tests/test_oracle_*.py) tie it to things other than itself: brute force
 on tiny images, a library box filter, exact rational arithmetic, closed forms
@@ -85,6 +93,11 @@ def _load():
         lib.bnzref_histogram.argtypes = [P, i, i, i, ll, P]
         lib.bnzref_otsu_threshold.argtypes = [P, P]
         lib.bnzref_otsu.argtypes = [P, i, i, i, ll, P, ll, ctypes.POINTER(i)]
+        lib.bnzref_gs_member.argtypes = [i, i, i, i]
+        lib.bnzref_gs_offsets.argtypes = [i, i, P, P, i]
+        lib.bnzref_gs_sums.argtypes = [P, i, i, i, i, P, P, P]
+        lib.bnzref_gs_binarize.argtypes = [P, i, i, i, ll, i, i, i, d, d, P, ll, i64p]
+        lib.bnzref_confusion.argtypes = [P, ll, i, P, ll, i, i, i, P]
         _lib = lib
         return lib
 
@@ -236,3 +249,73 @@ def otsu(src: np.ndarray, packed: bool = False):
     if packed:
         out = pack(out)
     return out, int(T.value)
+
+
+# ---- reduced sets S' (Sec. 2, Eq. 5) and the F-measure (Eq. 6) ----------------
+
+GS_FULL, GS_CROSS, GS_DIAGONALS, GS_STAR, GS_FRAME, GS_FRAME_CROSS, GS_FRAME_DIAGONALS = range(7)
+GS_NAMES = {GS_FULL: "full", GS_CROSS: "cross", GS_DIAGONALS: "diagonals", GS_STAR: "star",
+            GS_FRAME: "frame", GS_FRAME_CROSS: "frame+cross", GS_FRAME_DIAGONALS: "frame+diagonals"}
+
+
+def gs_offsets(gs: int, W: int):
+    """(dy, dx) offsets of the structure S' in the W x W window, row-major."""
+    lib = _load()
+    n = lib.bnzref_gs_offsets(int(gs), int(W), None, None, 0)
+    if n < 0:
+        raise ValueError("bad structure or window")
+    dy = np.empty(n, np.int32)
+    dx = np.empty(n, np.int32)
+    lib.bnzref_gs_offsets(int(gs), int(W), _ptr(dy), _ptr(dx), n)
+    return list(zip(dy.tolist(), dx.tolist()))
+
+
+def gs_sums(f: np.ndarray, W: int, gs: int):
+    """Exact (n', S1', S2') of every pixel over the in-image samples of S'."""
+    f = np.ascontiguousarray(f, dtype=np.uint8)
+    h, w = f.shape
+    n = np.empty((h, w), np.int64)
+    a = np.empty((h, w), np.int64)
+    b = np.empty((h, w), np.int64)
+    _check(_load().bnzref_gs_sums(_ptr(f), h, w, int(W), int(gs), _ptr(n), _ptr(a), _ptr(b)))
+    return n, a, b
+
+
+def gs_binarize(src: np.ndarray, W: int, gs: int, rule: int, k: float, R: float = 128.0):
+    """Eq. 5 (Sauvola on m', s' with R' = R) or Niblack on m', s'; returns (mask, ties)."""
+    src, h, w, ch = _img(src)
+    out = np.empty((h, w), np.uint8)
+    ties = ctypes.c_int64(0)
+    _check(_load().bnzref_gs_binarize(_ptr(src), h, w, ch, w * ch, int(W), int(gs), int(rule), float(k),
+                                      float(R), _ptr(out), w, ctypes.byref(ties)))
+    return out, int(ties.value)
+
+
+def gs_binarize_rows(src: np.ndarray, W: int, gs: int, rule: int, k: float, R: float, y0: int, y1: int):
+    """Rows [y0, y1) of gs_binarize, computed on the band that holds their windows (same values:
+    a pixel's samples lie within its window, and the band keeps every in-image row of it)."""
+    h = src.shape[0]
+    lo, hi = max(0, y0 - W // 2), min(h, y1 + (W - 1 - W // 2))
+    out, _ = gs_binarize(np.ascontiguousarray(src[lo:hi]), W, gs, rule, k, R)
+    return out[y0 - lo:y1 - lo]
+
+
+def confusion(mask: np.ndarray, ref: np.ndarray, mask_ink: int = 0, ref_ink: int = 1):
+    """(TP, FP, FN, TN) of mask against ref; a pixel is text where it equals the array's ink value."""
+    mask = np.ascontiguousarray(mask, dtype=np.uint8)
+    ref = np.ascontiguousarray(ref, dtype=np.uint8)
+    if mask.shape != ref.shape or mask.ndim != 2:
+        raise ValueError("mask and reference must be equal-shaped 2-D arrays")
+    h, w = mask.shape
+    c = np.zeros(4, np.int64)
+    _check(_load().bnzref_confusion(_ptr(mask), w, int(mask_ink), _ptr(ref), w, int(ref_ink), h, w, _ptr(c)))
+    return tuple(int(v) for v in c)
+
+
+def fmeasure(counts):
+    """Eq. 6: FM = 2 R P / (R + P), R = TP/(TP+FN), P = TP/(TP+FP); returns (FM, R, P), 0 where undefined."""
+    tp, fp, fn = counts[0], counts[1], counts[2]
+    rec = tp / (tp + fn) if tp + fn else 0.0
+    prec = tp / (tp + fp) if tp + fp else 0.0
+    fm = 2.0 * rec * prec / (rec + prec) if rec + prec else 0.0
+    return fm, rec, prec

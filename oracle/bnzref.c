@@ -486,3 +486,162 @@ int bnzref_otsu(const uint8_t *src, int h, int w, int ch, long long pitch, uint8
         *T_out = T;
     return BNZREF_OK;
 }
+
+/* ---- reduced sets S' (Sec. 2, Eq. 5) ----------------------------------------
+ *
+ * Sec. 2 replaces the window set S by a reduced set S' of pixels sampled from
+ * the window in a geometric order, and Eq. 5 evaluates Sauvola's rule on the
+ * mean m' and standard deviation s' of S' with a dynamic range R'.  The
+ * structures themselves are drawn in Fig. 1, which is not available, so the
+ * six below are proposed here (they are not the paper's drawings).  Each has
+ * O(W) samples, as the O(W N^2) bound of Sec. 3.2 requires.  Offsets (dy, dx)
+ * run over the window [-r_lo, r_hi]^2 (bnzref_radii); with lo = -r_lo and
+ * hi = r_hi:
+ *   0  the whole window (S' = S: Eq. 5 is Eq. 4)
+ *   1  cross        dy == 0 or dx == 0
+ *   2  diagonals    dy == dx or dy == -dx
+ *   3  star         cross or diagonals
+ *   4  frame        dy in {lo, hi} or dx in {lo, hi}
+ *   5  frame or cross
+ *   6  frame or diagonals
+ * As for S, samples outside the image are dropped and n' counts the others;
+ * m' = S1'/n' and s' = sqrt(n' S2' - S1'^2)/n' (population deviation), and the
+ * decision is Eq. 3 on t' with the fp64 order of bnzref_threshold_value
+ * (Niblack's rule on m', s' likewise).  Every sum is exact. */
+int bnzref_gs_member(int gs, int W, int dy, int dx)
+{
+    int r_lo, r_hi;
+    bnzref_radii(W, &r_lo, &r_hi);
+    if (dy < -r_lo || dy > r_hi || dx < -r_lo || dx > r_hi)
+        return 0;
+    const int cross = dy == 0 || dx == 0;
+    const int diag = dy == dx || dy == -dx;
+    const int frame = dy == -r_lo || dy == r_hi || dx == -r_lo || dx == r_hi;
+    switch (gs) {
+    case 0: return 1;
+    case 1: return cross;
+    case 2: return diag;
+    case 3: return cross || diag;
+    case 4: return frame;
+    case 5: return frame || cross;
+    case 6: return frame || diag;
+    default: return 0;
+    }
+}
+
+/* The offsets of S' in row-major order; returns their number (-1: bad args).
+ * dy, dx may be NULL to count only; otherwise they hold at least cap entries. */
+int bnzref_gs_offsets(int gs, int W, int *dy, int *dx, int cap)
+{
+    if (W < 1 || gs < 0 || gs > 6)
+        return -1;
+    int r_lo, r_hi, n = 0;
+    bnzref_radii(W, &r_lo, &r_hi);
+    for (int a = -r_lo; a <= r_hi; ++a)
+        for (int b = -r_lo; b <= r_hi; ++b) {
+            if (!bnzref_gs_member(gs, W, a, b))
+                continue;
+            if (dy && dx) {
+                if (n >= cap)
+                    return -1;
+                dy[n] = a;
+                dx[n] = b;
+            }
+            ++n;
+        }
+    return n;
+}
+
+/* n', S1', S2' of every pixel: the in-image samples of S' summed one by one
+ * (O(|S'|) = O(W) per pixel, the evaluation Sec. 3.2 counts). */
+int bnzref_gs_sums(const uint8_t *f, int h, int w, int W, int gs, int64_t *n, int64_t *s1, int64_t *s2)
+{
+    if (!f || !n || !s1 || !s2 || h < 1 || w < 1)
+        return BNZREF_EINVAL;
+    const int cnt = bnzref_gs_offsets(gs, W, NULL, NULL, 0);
+    if (cnt < 1)
+        return BNZREF_EINVAL;
+    int *dy = (int *)malloc(sizeof(int) * (size_t)cnt);
+    int *dx = (int *)malloc(sizeof(int) * (size_t)cnt);
+    if (!dy || !dx) {
+        free(dy);
+        free(dx);
+        return BNZREF_ENOMEM;
+    }
+    bnzref_gs_offsets(gs, W, dy, dx, cnt);
+    for (int y = 0; y < h; ++y)
+        for (int x = 0; x < w; ++x) {
+            int64_t c = 0, a = 0, b = 0;
+            for (int i = 0; i < cnt; ++i) {
+                const int yy = y + dy[i], xx = x + dx[i];
+                if (yy < 0 || yy >= h || xx < 0 || xx >= w)
+                    continue;
+                const int64_t v = f[(long long)yy * w + xx];
+                ++c;
+                a += v;
+                b += v * v;
+            }
+            const long long i = (long long)y * w + x;
+            n[i] = c;
+            s1[i] = a;
+            s2[i] = b;
+        }
+    free(dy);
+    free(dx);
+    return BNZREF_OK;
+}
+
+/* Eq. 1 gray, the reduced-set sums and the Eq. 3 decision on t' (Eq. 5 for
+ * Sauvola with R' = R); ties |f - t'| < 1e-9 counted. */
+int bnzref_gs_binarize(const uint8_t *src, int h, int w, int ch, long long src_pitch, int W, int gs, int rule,
+                       double k, double R, uint8_t *dst, long long dst_pitch, int64_t *ties)
+{
+    if (!src || !dst || h < 1 || w < 1 || (ch != 1 && ch != 3) || W < 1 || gs < 0 || gs > 6 ||
+        src_pitch < (long long)w * ch || dst_pitch < w || (rule != BNZREF_SAUVOLA && rule != BNZREF_NIBLACK))
+        return BNZREF_EINVAL;
+    if (rule == BNZREF_SAUVOLA && !(R > 0.0))
+        return BNZREF_EINVAL;
+    const size_t np = (size_t)h * (size_t)w;
+    uint8_t *f = (uint8_t *)malloc(np);
+    int64_t *n = (int64_t *)malloc(np * sizeof(int64_t));
+    int64_t *a = (int64_t *)malloc(np * sizeof(int64_t));
+    int64_t *b = (int64_t *)malloc(np * sizeof(int64_t));
+    uint8_t *out = (uint8_t *)malloc(np);
+    int rc = BNZREF_ENOMEM;
+    if (f && n && a && b && out) {
+        bnzref_gray(src, h, w, ch, src_pitch, f);
+        rc = bnzref_gs_sums(f, h, w, W, gs, n, a, b);
+        if (rc == BNZREF_OK)
+            rc = bnzref_threshold(f, n, a, b, h, w, rule, k, R, out, ties);
+        if (rc == BNZREF_OK)
+            for (int y = 0; y < h; ++y)
+                memcpy(dst + (long long)y * dst_pitch, out + (long long)y * w, (size_t)w);
+    }
+    free(f);
+    free(n);
+    free(a);
+    free(b);
+    free(out);
+    return rc;
+}
+
+/* ---- F-measure, Eq. 6 ---------------------------------------------------------
+ * Confusion counts of a binarized mask against a reference mask, the text
+ * (foreground) of each being the pixels equal to its ink value: counts[0] =
+ * TP (ink in both), [1] = FP (ink in the mask only), [2] = FN (ink in the
+ * reference only), [3] = TN.  Eq. 6 then needs R = TP/(TP+FN), P = TP/(TP+FP). */
+int bnzref_confusion(const uint8_t *mask, long long mask_pitch, int mask_ink, const uint8_t *ref, long long ref_pitch,
+                     int ref_ink, int h, int w, int64_t *counts)
+{
+    if (!mask || !ref || !counts || h < 0 || w < 0 || mask_pitch < w || ref_pitch < w)
+        return BNZREF_EINVAL;
+    int64_t c[4] = {0, 0, 0, 0};
+    for (int y = 0; y < h; ++y)
+        for (int x = 0; x < w; ++x) {
+            const int a = mask[(long long)y * mask_pitch + x] == mask_ink;
+            const int b = ref[(long long)y * ref_pitch + x] == ref_ink;
+            c[a ? (b ? 0 : 1) : (b ? 2 : 3)]++;
+        }
+    memcpy(counts, c, sizeof c);
+    return BNZREF_OK;
+}

@@ -33,6 +33,15 @@ int bnzref_otsu_threshold(const uint64_t *hist, double *q_out);
 int bnzref_otsu(const uint8_t *src, int h, int w, int ch, long long pitch, uint8_t *dst, long long dst_pitch,
                 int *T_out);
 
+/* Reduced sets S' of Sec. 2 (Eq. 5; structures proposed here, see bnzref.c) and Eq. 6 confusion counts. */
+int bnzref_gs_member(int gs, int W, int dy, int dx);
+int bnzref_gs_offsets(int gs, int W, int *dy, int *dx, int cap);
+int bnzref_gs_sums(const uint8_t *f, int h, int w, int W, int gs, int64_t *n, int64_t *s1, int64_t *s2);
+int bnzref_gs_binarize(const uint8_t *src, int h, int w, int ch, long long src_pitch, int W, int gs, int rule,
+                       double k, double R, uint8_t *dst, long long dst_pitch, int64_t *ties);
+int bnzref_confusion(const uint8_t *mask, long long mask_pitch, int mask_ink, const uint8_t *ref, long long ref_pitch,
+                     int ref_ink, int h, int w, int64_t *counts);
+
 #ifdef __cplusplus
 }
 #endif
