@@ -393,6 +393,7 @@ def run_ours(args):
     if not args.case:
         result["dual"] = dual_runs(bnz, srcs, outs, stream, dev, args.steps, max(args.warmup, 3))
         result["otsu"] = otsu_runs(bnz, srcs, outs, stream, dev, args.steps, max(args.warmup, 3))
+        result["gs"] = gs_runs(bnz, srcs, outs, stream, dev)
     if not args.case and not args.no_extra and rank == 0:
         del srcs, outs
         torch.cuda.empty_cache()
@@ -697,6 +698,49 @@ def otsu_runs(bnz, srcs, outs, stream, dev, steps, warmup):
             "GB/s": round(gbs, 1), "frac": round(gbs / peak, 4), "T": T}
 
 
+def gs_runs(bnz, srcs, outs, stream, dev):
+    """Reduced-set rule of Sec. 2 (Eq. 5, Sauvola k=0.5 R'=128) on the same page for the six structures
+    proposed by this library (the paper's Fig. 1 is not available, so the structures and their accuracy are not
+    the paper's): time per launch (blocks of 20 launches, each on its own input copy), algorithmic bytes 4 B/px,
+    and the F-measure of Eq. 6 against the page's ground-truth stroke mask and against the exact Sauvola mask
+    of the same W (counts from the confusion kernel)."""
+    import torch
+    import synth
+    _, gt = synth.page(H, W_IMG, SEED, synth.STAINS, CH, ground_truth=True)
+    d_gt = bnz.to_device_pitched(gt, dev)
+    exact = bnz.alloc_pitched(H, W_IMG, dev)
+    peak, _ = measured_peak()
+    bytes_launch = H * W_IMG * BYTES_PER_PX
+    rot = [0]
+    res = {"kernel": "gs_kernel", "rule": "Sauvola k=0.5 R'=128", "algorithmic_bytes_per_launch": bytes_launch,
+           "structures": {}, "exact_sauvola_fm_vs_ground_truth": {},
+           "note": "structures proposed here (cross, diagonals, star, frame, frame+cross, frame+diagonals); "
+                   "the paper's Fig. 1 is unavailable, so its accuracy figures are not comparable"}
+    Ws = (15, 31, 61, 101)
+    for W in Ws:
+        bnz.bnz_binarize_dev(srcs[0], W, bnz.BNZ_SAUVOLA, 0.5, 128.0, exact, stream=stream)
+        stream.synchronize()
+        res["exact_sauvola_fm_vs_ground_truth"][f"W{W}"] = round(bnz.fmeasure(exact, d_gt, 0, 1)[0], 5)
+        for gs, name in bnz.GS_NAMES.items():
+            def call(gs=gs, W=W):
+                c = rot[0] % NCOPY
+                rot[0] += 1
+                bnz.bnz_gs_binarize_dev(srcs[c], W, gs, bnz.BNZ_SAUVOLA, 0.5, 128.0, outs[c], stream=stream)
+            with torch.cuda.stream(stream):
+                for _ in range(3):
+                    call()
+            ms = _block_ms(call, stream, 20)
+            bnz.bnz_gs_binarize_dev(srcs[0], W, gs, bnz.BNZ_SAUVOLA, 0.5, 128.0, outs[0], stream=stream)
+            stream.synchronize()
+            gbs = bytes_launch / (ms / 1e3) / 1e9
+            res["structures"].setdefault(name, {})[f"W{W}"] = {
+                "us": round(ms * 1e3, 2), "Mpixel/s": round(H * W_IMG / (ms / 1e3) / 1e6, 1),
+                "GB/s": round(gbs, 1), "frac": round(gbs / peak, 4),
+                "fm_vs_ground_truth": round(bnz.fmeasure(outs[0], d_gt, 0, 1)[0], 5),
+                "fm_vs_exact_sauvola": round(bnz.fmeasure(outs[0], exact, 0, 0)[0], 5)}
+    return res
+
+
 def e2e_host_api(bnz, page, steps):
     """Same metric through the host-pointer C ABI, copies inside the timed region: a step uploads the pinned
     page once and brings back its 8 masks with bnz_binarize_runs (one page, eight settings; uploads, kernels and
@@ -956,6 +1000,29 @@ def run_integral(args):
     return 0
 
 
+def run_gs(args):
+    """The reduced-set kernel alone (Sec. 2, Eq. 5, Sauvola k=0.5 R'=128) on the 4096x4096 RGB page for one
+    structure and W (--gs-case GS,W): --warmup calls, then --steps timed calls (for profiler captures)."""
+    import torch
+    import paper_1210_3165_gb300 as bnz
+    torch.cuda.set_device(0)
+    bnz.load()
+    gs, W = (int(v) for v in args.gs_case.split(","))
+    src = bnz.to_device_pitched(host_page())
+    out = bnz.alloc_pitched(H, W_IMG)
+    stream = torch.cuda.Stream()
+
+    def call():
+        bnz.bnz_gs_binarize_dev(src, W, gs, bnz.BNZ_SAUVOLA, 0.5, 128.0, out, stream=stream)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            call()
+    ms = _block_ms(call, stream, max(args.steps, 1), 1)
+    print(json.dumps({"workload": f"reduced set {bnz.GS_NAMES[gs]}, W={W}, {WORKLOAD.split(',')[0]}",
+                      "ms_per_call": ms, "Mpixel/s": H * W_IMG / (ms / 1e3) / 1e6, "kernels_per_call": 1}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -967,13 +1034,14 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the other configurations' keys")
     ap.add_argument("--min-seconds", type=float, default=1.0,
                     help="repeat the K-step timed pass until this much time has passed (median pass reported)")
-    ap.add_argument("--workload", default="page", choices=["page", "batch", "serve", "integral"],
+    ap.add_argument("--workload", default="page", choices=["page", "batch", "serve", "integral", "gs"],
                     help="page: the 4096x4096 RGB page (default); batch: 256 uneven gray pages; "
                          "serve: Poisson stream of RGB pages through the serving loop")
     ap.add_argument("--case", default=None,
                     help="page workload restricted to one configuration CH,W,RULE (e.g. 3,15,sauvola): "
                          "one launch per step, for profiler captures")
     ap.add_argument("--integral-size", type=int, default=8192, help="page side of --workload integral")
+    ap.add_argument("--gs-case", default="1,31", help="structure and W of --workload gs (e.g. 5,101)")
     ap.add_argument("--serve-requests", type=int, default=10000)
     ap.add_argument("--serve-capacity", type=int, default=2000, help="requests of the closed-loop capacity run")
     ap.add_argument("--serve-loads", default="0.5,0.8,0.95", help="offered loads, fractions of batched capacity")
@@ -989,6 +1057,8 @@ def main():
         return run_batch(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "gs":
+        return run_gs(args)
     if args.workload == "integral":
         return run_integral(args)
     if args.case:

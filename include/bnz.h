@@ -106,7 +106,9 @@ typedef struct {
  * Page-locked host buffers copy fastest.  Pages of a megapixel or more are
  * processed in up to 4 row bands whose uploads, kernels and downloads overlap
  * on the calling thread's library streams; the result is the same as in one
- * piece.  Thread-safe: every calling thread has its own streams and buffers. */
+ * piece.  A page whose input and mask would take more than half of the free
+ * device memory streams through bnz_binarize_window with that half as the
+ * window.  Thread-safe: every calling thread has its own streams and buffers. */
 BNZ_API int bnz_sauvola(const uint8_t *src, int height, int width, int channels, int W, double k, double R,
                 uint8_t *dst);
 
@@ -129,6 +131,20 @@ typedef struct {
 } bnz_run;
 BNZ_API int bnz_binarize_runs(const uint8_t *src, int height, int width, int channels, const bnz_run *runs,
                               int nruns);
+
+/* Out-of-core form of bnz_sauvola / bnz_niblack (rule BNZ_SAUVOLA or
+ * BNZ_NIBLACK, R ignored for Niblack): a host page of any height streams
+ * through a device window of at most window_bytes (input and mask slots; the
+ * calling thread's buffers grow to that size and are kept for later calls).
+ * The page is cut into bands of B output rows, B as large as 3 slots of
+ * (B + W - 1) input rows and (B + W/2) mask rows (16-byte padded) allow; each
+ * band is uploaded with its read-only halo (the W/2 rows above and W - 1 - W/2
+ * below that its windows reach), binarized and downloaded on the calling
+ * thread's three library streams, overlapping the other bands.  dst equals
+ * what bnz_sauvola / bnz_niblack writes.  BNZ_EINVAL if window_bytes holds no
+ * 3 slots of 8 rows; otherwise errors as bnz_sauvola.  Blocks until done. */
+BNZ_API int bnz_binarize_window(const uint8_t *src, int height, int width, int channels, int W, int rule, double k,
+                                double R, uint8_t *dst, size_t window_bytes);
 
 /* The row bands bnz_sauvola and bnz_niblack use for a page (host logic only, no
  * device needed): returns the band count nb (>= 1) and, if starts is not NULL,
@@ -186,6 +202,52 @@ BNZ_API int bnz_dual_dev(const uint8_t *d_src, size_t src_pitch, int height, int
 #define BNZ_OTSU_SCRATCH_BYTES 4096
 BNZ_API int bnz_otsu_dev(const uint8_t *d_src, size_t src_pitch, int height, int width, int channels,
                  uint8_t *d_dst, size_t dst_pitch, int packed, void *d_scratch, void *stream);
+
+/* ---- reduced sets S' (Sec. 2, Eq. 5) --------------------------------------
+ * Sec. 2 thresholds with Eq. 5, t' = m' (1 + k (s'/R' - 1)), where m' and s'
+ * are the mean and population deviation of a reduced set S' of O(W) window
+ * pixels laid out along a geometric structure (Fig. 1).  The paper's drawings
+ * are not available; the structures below are this library's proposals.  With
+ * window offsets (dy, dx) in [-W/2, W - 1 - W/2]^2 (the same window as the
+ * exact calls), S' holds the offsets on
+ *   BNZ_GS_CROSS               dy == 0 or dx == 0                (2W - 1)
+ *   BNZ_GS_DIAGONALS           dy == dx or dy == -dx             (2W - 1, odd W)
+ *   BNZ_GS_STAR                cross or diagonals                (4W - 3)
+ *   BNZ_GS_FRAME               dy or dx on the window's edge     (4W - 4)
+ *   BNZ_GS_FRAME_CROSS         frame or cross                    (6W - 9, W >= 5)
+ *   BNZ_GS_FRAME_DIAGONALS     frame or diagonals                (6W - 9, W >= 5)
+ * Samples outside the image are dropped and n' counts the others. */
+#define BNZ_GS_CROSS 1
+#define BNZ_GS_DIAGONALS 2
+#define BNZ_GS_STAR 3
+#define BNZ_GS_FRAME 4
+#define BNZ_GS_FRAME_CROSS 5
+#define BNZ_GS_FRAME_DIAGONALS 6
+
+/* Reduced-set binarization: g = 0 if f < t', else 255 (Eq. 3 on t').  For
+ * BNZ_SAUVOLA t' is Eq. 5 with R' = R; for BNZ_NIBLACK t' = m' + k s' (R
+ * ignored).  Every output equals the fp64 evaluation of t' on the exact
+ * integer sums of S' (same order and tie rule as the exact calls).
+ * d_src: gray or RGB (channels 1 or 3), any alignment, src_pitch >= width *
+ * channels.  d_dst: byte mask (0 / 255), dst_pitch >= width.  W in [3,
+ * BNZ_MAX_W]; k and R within the limits of bnz_sauvola_dev.  d_stats
+ * (nullable, 4 counters, accumulated): [0] pixels re-decided past the fp32
+ * filter, [1] ties |f - t'| < 1e-9.  One kernel on `stream`, no host
+ * synchronization.  Errors: BNZ_EINVAL for bad arguments or an unknown
+ * structure, BNZ_ECUDA for a failed launch. */
+BNZ_API int bnz_gs_binarize_dev(const void *d_src, size_t src_pitch, int height, int width, int channels, int W,
+                                int gs, int rule, double k, double R, void *d_dst, size_t dst_pitch,
+                                unsigned long long *d_stats, void *stream);
+
+/* Confusion counts for the F-measure of Eq. 6, FM = 2 R P / (R + P) with
+ * R = TP / (TP + FN) and P = TP / (TP + FP): a pixel is text in d_mask where
+ * it equals mask_ink and text in d_ref where it equals ref_ink (bytes).
+ * Adds TP, FP, FN to d_counts[0..2] (device, caller-zeroed; TN = height *
+ * width - the three).  Byte masks of height x width, any alignment.  One
+ * kernel on `stream`.  Errors: BNZ_EINVAL, BNZ_ECUDA. */
+BNZ_API int bnz_confusion_dev(const void *d_mask, size_t mask_pitch, int mask_ink, const void *d_ref,
+                              size_t ref_pitch, int ref_ink, int height, int width, unsigned long long *d_counts,
+                              void *stream);
 
 /* Generic form of the two calls above with an explicit rule and optional
  * tile shape (tile may be NULL).  R is ignored for BNZ_NIBLACK. */

@@ -133,6 +133,9 @@ def _optional_symbols(lib):
         "bnz_binarize_integral_dev": ([P, sz, i, i, i, i, i, d, d, P, sz, i, P, sz, P, P], ctypes.c_int),
         "bnz_binarize_integral_static_dev": ([P, sz, i, i, i, i, i, d, d, P, sz, i, P, P], ctypes.c_int),
         "bnz_integral_images_dev": ([P, sz, i, i, i, P, sz, ctypes.POINTER(ctypes.c_longlong), P], ctypes.c_int),
+        "bnz_binarize_window": ([P, i, i, i, i, i, d, d, P, sz], ctypes.c_int),
+        "bnz_gs_binarize_dev": ([P, sz, i, i, i, i, i, i, d, d, P, sz, P, P], ctypes.c_int),
+        "bnz_confusion_dev": ([P, sz, i, P, sz, i, i, i, P, P], ctypes.c_int),
     }
     for name, (args, res) in table.items():
         if hasattr(lib, name):
@@ -185,6 +188,23 @@ def bnz_niblack(src, W: int, k: float = -0.2) -> np.ndarray:
 # ---------------------------------------------------------------------------
 # device-pointer calls (torch CUDA tensors)
 # ---------------------------------------------------------------------------
+
+def binarize_window(src, W: int, rule: str | int = "sauvola", k: float | None = None, R: float = 128.0,
+                    window_bytes: int = 256 << 20, out: np.ndarray | None = None) -> np.ndarray:
+    """Host page -> host mask through a device window of at most window_bytes (bnz_binarize_window)."""
+    if isinstance(rule, str):
+        rule = {"sauvola": BNZ_SAUVOLA, "niblack": BNZ_NIBLACK}[rule.lower()]
+    if k is None:
+        k = 0.5 if rule == BNZ_SAUVOLA else -0.2
+    a, h, w, ch = _host_img(src)
+    if out is None:
+        out = np.empty((h, w), np.uint8)
+    if out.shape != (h, w) or out.dtype != np.uint8 or not out.flags.c_contiguous:
+        raise ValueError("out must be a C-contiguous HxW uint8 array")
+    _check(load().bnz_binarize_window(a.ctypes.data, h, w, ch, int(W), int(rule), float(k), float(R),
+                                      out.ctypes.data, int(window_bytes)))
+    return out
+
 
 def binarize_runs(src, runs, out=None) -> list:
     """One host page, several settings (bnz_binarize_runs): runs = [(W, rule, k, R), ...] with rule
@@ -492,6 +512,61 @@ class Pool:
             self.close()
         except Exception:
             pass
+
+
+# reduced sets S' of Sec. 2 (Eq. 5): structures proposed by this library (see bnz.h)
+BNZ_GS_CROSS, BNZ_GS_DIAGONALS, BNZ_GS_STAR, BNZ_GS_FRAME, BNZ_GS_FRAME_CROSS, BNZ_GS_FRAME_DIAGONALS = range(1, 7)
+GS_NAMES = {BNZ_GS_CROSS: "cross", BNZ_GS_DIAGONALS: "diagonals", BNZ_GS_STAR: "star", BNZ_GS_FRAME: "frame",
+            BNZ_GS_FRAME_CROSS: "frame+cross", BNZ_GS_FRAME_DIAGONALS: "frame+diagonals"}
+
+
+def bnz_gs_binarize_dev(d_src, W: int, gs: int, rule: int, k: float, R: float, d_dst, stream=None,
+                        d_stats=None) -> None:
+    """Enqueue the reduced-set binarization (Eq. 5 on structure ``gs``) of a uint8 CUDA image."""
+    ptr, pitch, h, w, ch = _dev_img(d_src)
+    _check(load().bnz_gs_binarize_dev(ptr, pitch, h, w, ch, int(W), int(gs), int(rule), float(k), float(R),
+                                      d_dst.data_ptr(), _out_pitch(d_dst, w, False),
+                                      d_stats.data_ptr() if d_stats is not None else None,
+                                      _stream_ptr(stream)))
+
+
+def gs_binarize(d_src, W: int, gs: int, rule: str | int = "sauvola", k: float | None = None, R: float = 128.0,
+                out=None, stream=None, d_stats=None):
+    """Reduced-set mask of a uint8 CUDA image; returns the (pitched) output tensor view."""
+    if isinstance(rule, str):
+        rule = {"sauvola": BNZ_SAUVOLA, "niblack": BNZ_NIBLACK}[rule.lower()]
+    if k is None:
+        k = 0.5 if rule == BNZ_SAUVOLA else -0.2
+    _, _, h, w, _ = _dev_img(d_src)
+    if out is None:
+        out = alloc_pitched(h, w, d_src.device)
+    bnz_gs_binarize_dev(d_src, W, gs, rule, k, R, out, stream, d_stats)
+    return out
+
+
+def bnz_confusion_dev(d_mask, d_ref, d_counts, mask_ink: int = 0, ref_ink: int = 1, stream=None) -> None:
+    """Add TP, FP, FN of d_mask against d_ref (text = the ink byte of each) to d_counts[0:3] (uint64/int64)."""
+    mp, mpitch, h, w, mch = _dev_img(d_mask)
+    rp, rpitch, rh, rw, rch = _dev_img(d_ref)
+    if (h, w) != (rh, rw) or mch != 1 or rch != 1:
+        raise BnzError(BNZ_EINVAL, "mask and reference must be equal-sized byte images")
+    _check(load().bnz_confusion_dev(mp, mpitch, int(mask_ink), rp, rpitch, int(ref_ink), h, w, d_counts.data_ptr(),
+                                    _stream_ptr(stream)))
+
+
+def fmeasure(d_mask, d_ref, mask_ink: int = 0, ref_ink: int = 1, stream=None):
+    """Eq. 6 from the device counts: returns (FM, recall, precision, (TP, FP, FN, TN))."""
+    import torch
+    counts = torch.zeros(4, dtype=torch.int64, device=d_mask.device)
+    bnz_confusion_dev(d_mask, d_ref, counts, mask_ink, ref_ink, stream)
+    if stream is not None:
+        stream.synchronize()
+    tp, fp, fn, _ = (int(v) for v in counts.cpu())
+    tn = d_mask.shape[0] * d_mask.shape[1] - tp - fp - fn
+    rec = tp / (tp + fn) if tp + fn else 0.0
+    prec = tp / (tp + fp) if tp + fp else 0.0
+    fm = 2.0 * rec * prec / (rec + prec) if rec + prec else 0.0
+    return fm, rec, prec, (tp, fp, fn, tn)
 
 
 def bnz_fused_plan(h: int, w: int, ch: int, W: int, tile: bnz_tile | None = None) -> dict:

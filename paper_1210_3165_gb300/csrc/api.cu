@@ -198,7 +198,7 @@ constexpr int kMaxBands = 4;
 struct HostCallState {
     struct PerDevice {
         cudaStream_t stream = nullptr, up = nullptr, down = nullptr;
-        cudaEvent_t ev_up[kMaxBands] = {}, ev_k[kMaxBands] = {};
+        cudaEvent_t ev_up[kMaxBands] = {}, ev_k[kMaxBands] = {}, ev_dn[kMaxBands] = {};
         unsigned long long *stats = nullptr, *h_stats = nullptr;
         void *src = nullptr, *dst = nullptr;
         size_t src_cap = 0, dst_cap = 0;
@@ -217,6 +217,8 @@ struct HostCallState {
                     cudaEventDestroy(v.ev_up[i]);
                 if (v.ev_k[i])
                     cudaEventDestroy(v.ev_k[i]);
+                if (v.ev_dn[i])
+                    cudaEventDestroy(v.ev_dn[i]);
             }
             for (cudaEvent_t ev : v.ev_run)
                 cudaEventDestroy(ev);
@@ -250,9 +252,23 @@ static int grow(void **buf, size_t *cap, size_t need, const char *what)
     return BNZ_OK;
 }
 
-static int host_call_state(int d, size_t src_bytes, size_t dst_bytes, HostCallState::PerDevice **out)
+static HostCallState &host_calls()
 {
     static thread_local HostCallState st;
+    return st;
+}
+
+static size_t host_call_held(int d)
+{
+    if (d < 0 || d >= 64)
+        return 0;
+    const HostCallState::PerDevice &v = host_calls().dev[d];
+    return v.src_cap + v.dst_cap;
+}
+
+static int host_call_state(int d, size_t src_bytes, size_t dst_bytes, HostCallState::PerDevice **out)
+{
+    HostCallState &st = host_calls();
     if (d < 0 || d >= 64)
         return fail(BNZ_ENODEV, "device ordinal %d out of range", d);
     HostCallState::PerDevice &v = st.dev[d];
@@ -263,7 +279,7 @@ static int host_call_state(int d, size_t src_bytes, size_t dst_bytes, HostCallSt
             return cuda_fail(e, "cudaStreamCreate");
         }
     for (int i = 0; i < kMaxBands; ++i)
-        for (cudaEvent_t *pe : {&v.ev_up[i], &v.ev_k[i]})
+        for (cudaEvent_t *pe : {&v.ev_up[i], &v.ev_k[i], &v.ev_dn[i]})
             if (!*pe && (e = cudaEventCreateWithFlags(pe, cudaEventDisableTiming)) != cudaSuccess) {
                 *pe = nullptr;
                 return cuda_fail(e, "cudaEventCreate");
@@ -284,6 +300,9 @@ static int host_call_state(int d, size_t src_bytes, size_t dst_bytes, HostCallSt
     *out = &v;
     return BNZ_OK;
 }
+
+// Device bytes the calling thread's host-call buffers hold on device d.
+static size_t host_call_held(int d);
 
 // Both rules from one pass over the window sums (dual.cu).
 int launch_dual(const uint8_t *d_src, size_t src_pitch, int h, int w, int ch, int W, double ks, double R, double kn,
@@ -329,6 +348,127 @@ static cudaError_t copy_rows(void *dst_base, size_t dst_pitch, const void *src_b
     return cudaMemcpy2DAsync(d, dst_pitch, sp, src_pitch, row, n, kind, s);
 }
 
+// ---- pages larger than the device: a bounded window of row bands ----------
+// The page streams through kSlots band slots in device memory.  Band i holds
+// output rows [y0, y1) = [i B, i B + B) and its read-only halo: input rows
+// [y0 - r_lo, y1 + r_hi) within the page, the rows its windows reach.  It is
+// binarized as a sub-page of those rows with outputs [y0, y1) only: a window
+// of an output row never reaches the sub-page's cut edges (it clips only
+// where the page itself ends), so every mask row is the whole page's.  Three
+// streams: the upload of band i waits until the kernel of band i - kSlots has
+// read its slot; the kernel waits for its upload and for the download of
+// band i - kSlots (its output slot); the download waits for the kernel.  The
+// halo rows are uploaded again with each band ((W - 1) / B more input bytes).
+constexpr int kSlots = 3;
+
+static size_t window_slot_bytes(int B, int W, size_t sp, size_t dp)
+{
+    return (size_t)(B + W - 1) * sp + (size_t)(B + W / 2) * dp;
+}
+
+static int window_band_rows(int height, int W, size_t sp, size_t dp, size_t window_bytes, int *B_out)
+{
+    const size_t per = window_bytes / kSlots;
+    const size_t fixed = (size_t)(W - 1) * sp + (size_t)(W / 2) * dp;
+    const size_t B = per > fixed ? (per - fixed) / (sp + dp) : 0;
+    if (B < 8)
+        return fail(BNZ_EINVAL, "window_bytes %zu too small: %d slots of at least 8 rows and a %d-row halo need %zu",
+                    window_bytes, kSlots, W - 1, (size_t)kSlots * window_slot_bytes(8, W, sp, dp));
+    *B_out = (int)std::min<size_t>(B, (size_t)height);
+    return BNZ_OK;
+}
+
+static int binarize_window_host(const uint8_t *src, int height, int width, int channels, int W, int rule, double k,
+                                double R, uint8_t *dst, size_t window_bytes)
+{
+    int rc = check_common(src, (size_t)width * channels, height, width, channels, W, rule, k, R, dst,
+                          (size_t)width, 0);
+    if (rc != BNZ_OK)
+        return rc;
+    const size_t row_in = (size_t)width * channels;
+    const size_t sp = (row_in + 15) & ~size_t(15);
+    const size_t dp = ((size_t)width + 15) & ~size_t(15);
+    int B = 0;
+    if ((rc = window_band_rows(height, W, sp, dp, window_bytes, &B)) != BNZ_OK)
+        return rc;
+    int dev = 0, sms = 0;
+    if ((rc = current_device(&dev)) != BNZ_OK || (rc = device_sm_count(&sms)) != BNZ_OK)
+        return rc;
+    const int r_lo = W / 2, r_hi = W - 1 - W / 2;
+    const size_t in_slot = (size_t)(B + W - 1) * sp, out_slot = (size_t)(B + r_lo) * dp;
+    HostCallState::PerDevice *v = nullptr;
+    if ((rc = host_call_state(dev, kSlots * in_slot, kSlots * out_slot, &v)) != BNZ_OK)
+        return rc;
+    FusedPlan shape;
+    if ((rc = plan_shape(std::min(height, B + W - 1), width, channels, W, 0, &shape)) != BNZ_OK)
+        return rc;
+    cudaStream_t s = v->stream;
+    const int nb = (height + B - 1) / B;
+    cudaError_t e;
+    do {
+        if ((e = cudaMemsetAsync(v->stats, 0, 4 * sizeof(unsigned long long), s)) != cudaSuccess) {
+            rc = cuda_fail(e, "clear statistics");
+            break;
+        }
+        for (int i = 0; i < nb && rc == BNZ_OK; ++i) {
+            const int j = i % kSlots;
+            const int y0 = i * B, y1 = std::min(height, y0 + B);
+            const int in0 = std::max(0, y0 - r_lo), in1 = std::min(height, y1 + r_hi);
+            uint8_t *sin = static_cast<uint8_t *>(v->src) + (size_t)j * in_slot;
+            uint8_t *sout = static_cast<uint8_t *>(v->dst) + (size_t)j * out_slot;
+            if (i >= kSlots && (e = cudaStreamWaitEvent(v->up, v->ev_k[j], 0)) != cudaSuccess) {
+                rc = cuda_fail(e, "order slot reuse");
+                break;
+            }
+            if ((e = copy_rows(sin, sp, src + (size_t)in0 * row_in, row_in, row_in, 0, in1 - in0,
+                               cudaMemcpyHostToDevice, v->up)) != cudaSuccess) {
+                rc = cuda_fail(e, "copy band to device");
+                break;
+            }
+            if ((e = cudaEventRecord(v->ev_up[j], v->up)) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(s, v->ev_up[j], 0)) != cudaSuccess ||
+                (i >= kSlots && (e = cudaStreamWaitEvent(s, v->ev_dn[j], 0)) != cudaSuccess)) {
+                rc = cuda_fail(e, "order band kernel");
+                break;
+            }
+            bnz_tile tile = {0, 0, 0, 0};
+            tile.tile_h = (int)std::max<long long>(8, ((long long)shape.tiles_x * (y1 - y0) + sms - 1) / sms);
+            rc = binarize_dev(sin, sp, in1 - in0, width, channels, W, rule, k, R, sout, dp, 0, &tile, s, v->stats,
+                              y0 - in0, y1 - in0);
+            if (rc != BNZ_OK)
+                break;
+            if ((e = cudaEventRecord(v->ev_k[j], s)) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(v->down, v->ev_k[j], 0)) != cudaSuccess) {
+                rc = cuda_fail(e, "order band download");
+                break;
+            }
+            if ((e = cudaMemcpy2DAsync(dst + (size_t)y0 * width, (size_t)width, sout + (size_t)(y0 - in0) * dp, dp,
+                                       (size_t)width, (size_t)(y1 - y0), cudaMemcpyDeviceToHost, v->down)) !=
+                    cudaSuccess ||
+                (e = cudaEventRecord(v->ev_dn[j], v->down)) != cudaSuccess) {
+                rc = cuda_fail(e, "copy band result to host");
+                break;
+            }
+        }
+        if (rc != BNZ_OK)
+            break;
+        if ((e = cudaStreamWaitEvent(v->down, v->ev_k[(nb - 1) % kSlots], 0)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(v->h_stats, v->stats, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                 v->down)) != cudaSuccess) {
+            rc = cuda_fail(e, "read statistics");
+            break;
+        }
+    } while (0);
+    for (cudaStream_t q : {v->up, s, v->down}) {
+        e = cudaStreamSynchronize(q);
+        if (rc == BNZ_OK && e != cudaSuccess)
+            rc = cuda_fail(e, "cudaStreamSynchronize");
+    }
+    if (rc == BNZ_OK && v->h_stats[BNZ_STATS_TIMEOUTS] != 0)
+        rc = fail(BNZ_ETIMEOUT, "a device-side wait timed out; output incomplete");
+    return rc;
+}
+
 static int binarize_host(const uint8_t *src, int height, int width, int channels, int W, int rule, double k,
                          double R, uint8_t *dst)
 {
@@ -347,6 +487,14 @@ static int binarize_host(const uint8_t *src, int height, int width, int channels
     const size_t row_in = (size_t)width * channels;
     const size_t sp = (row_in + 15) & ~size_t(15);
     const size_t dp = ((size_t)width + 15) & ~size_t(15);
+    // a page (and its mask) that would take more than half of the free device
+    // memory streams through a window of that half instead
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+        const size_t avail = (free_b + host_call_held(dev)) / 2;
+        if ((sp + dp) * (size_t)height > avail)
+            return binarize_window_host(src, height, width, channels, W, rule, k, R, dst, avail);
+    }
     HostCallState::PerDevice *v = nullptr;
     rc = host_call_state(dev, sp * height, dp * height, &v);
     if (rc != BNZ_OK)
@@ -550,6 +698,13 @@ extern "C" {
 int bnz_binarize_runs(const uint8_t *src, int height, int width, int channels, const bnz_run *runs, int nruns)
 {
     return binarize_runs_host(src, height, width, channels, runs, nruns);
+}
+
+int bnz_binarize_window(const uint8_t *src, int height, int width, int channels, int W, int rule, double k, double R,
+                        uint8_t *dst, size_t window_bytes)
+{
+    return binarize_window_host(src, height, width, channels, W, rule, k, rule == BNZ_NIBLACK ? 1.0 : R, dst,
+                                window_bytes);
 }
 
 int bnz_sauvola(const uint8_t *src, int height, int width, int channels, int W, double k, double R, uint8_t *dst)

@@ -123,4 +123,10 @@ int launch_integral(const uint8_t *d_src, size_t src_pitch, int h, int w, int ch
                     double R, uint8_t *d_dst, size_t dst_pitch, int packed, void *scratch, cudaStream_t stream,
                     unsigned long long *d_stats);
 
+// ---- reduced-set rule of Sec. 2 and the Eq. 6 counts (gs.cu) ---------------
+int launch_gs(const uint8_t *d_src, size_t src_pitch, int h, int w, int ch, int W, int gs, int rule, double k,
+              double R, uint8_t *d_dst, size_t dst_pitch, unsigned long long *d_stats, cudaStream_t stream);
+int launch_confusion(const uint8_t *d_mask, size_t mask_pitch, int mask_ink, const uint8_t *d_ref, size_t ref_pitch,
+                     int ref_ink, int h, int w, unsigned long long *d_counts, cudaStream_t stream);
+
 } // namespace bnz

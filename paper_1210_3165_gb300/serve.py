@@ -341,10 +341,13 @@ class NativeServer:
     (16-byte row pitch).  Masks land in a pinned host arena; the futures return numpy arrays over it."""
 
     def __init__(self, budget_bytes: int = 16 << 30, max_batch: int = 16, batched: bool = True,
-                 compute_streams: int = 1, host_bytes: int = 4 << 30, inject_timeout_every: int = 0):
+                 compute_streams: int = 1, host_bytes: int = 4 << 30, inject_timeout_every: int = 0,
+                 host_arena: HostArena | None = None):
         import ctypes
         from . import _check, bnz_server_config, load
-        self.host = HostArena(host_bytes)
+        # host_arena: a caller-owned arena shared by several servers (one pinned reservation; submit waits
+        # while it is full, so it should hold the masks of every request in flight)
+        self.host = host_arena if host_arena is not None else HostArena(host_bytes)
         self._ct = ctypes
         self._lib = load()
         self.budget = int(budget_bytes)

@@ -175,3 +175,51 @@ def test_host_bands_rejects_bad_arguments():
         bnz.host_bands(0, 10, 3)
     with pytest.raises(bnz.BnzError):
         bnz.host_bands(10, 10, 256)
+
+
+def test_reduced_set_and_confusion_argument_checks(lib):
+    buf = np.zeros(8192, np.uint8)
+    a = _aligned(buf)
+    rc = lib.bnz_gs_binarize_dev(a, 16, 8, 16, 1, 2, bnz.BNZ_GS_CROSS, bnz.BNZ_SAUVOLA, 0.5, 128.0, a + 1024, 16,
+                                 None, None)
+    assert rc == bnz.BNZ_EINVAL and "W >= 3" in bnz.bnz_last_error()
+    for gs in (0, 7):
+        rc = lib.bnz_gs_binarize_dev(a, 16, 8, 16, 1, 5, gs, bnz.BNZ_SAUVOLA, 0.5, 128.0, a + 1024, 16, None, None)
+        assert rc == bnz.BNZ_EINVAL and "unknown structure" in bnz.bnz_last_error()
+    rc = lib.bnz_gs_binarize_dev(a, 16, 8, 16, 1, 5, 1, bnz.BNZ_SAUVOLA, 0.5, 0.0, a + 1024, 16, None, None)
+    assert rc == bnz.BNZ_EINVAL and "R must be" in bnz.bnz_last_error()
+    rc = lib.bnz_gs_binarize_dev(a, 16, 8, 16, 1, 256, 1, bnz.BNZ_SAUVOLA, 0.5, 128.0, a + 1024, 16, None, None)
+    assert rc == bnz.BNZ_EINVAL and "window size" in bnz.bnz_last_error()
+    rc = lib.bnz_confusion_dev(a, 8, 0, a + 1024, 16, 1, 4, 16, a + 4096, None)
+    assert rc == bnz.BNZ_EINVAL and "pitch" in bnz.bnz_last_error()
+    rc = lib.bnz_confusion_dev(a, 16, 256, a + 1024, 16, 1, 4, 16, a + 4096, None)
+    assert rc == bnz.BNZ_EINVAL and "ink" in bnz.bnz_last_error()
+    assert lib.bnz_confusion_dev(a, 16, 0, a + 1024, 16, 1, 0, 16, a + 4096, None) == bnz.BNZ_OK  # empty: no work
+    assert (buf == 0).all()
+
+
+def test_reduced_set_needs_a_device():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    lib = bnz.load()
+    buf = np.zeros(8192, np.uint8)
+    a = _aligned(buf)
+    assert lib.bnz_gs_binarize_dev(a, 16, 8, 16, 1, 5, 1, bnz.BNZ_SAUVOLA, 0.5, 128.0, a + 1024, 16, None,
+                                   None) == bnz.BNZ_ENODEV
+    assert lib.bnz_confusion_dev(a, 16, 0, a + 1024, 16, 1, 4, 16, a + 4096, None) == bnz.BNZ_ENODEV
+    assert (buf == 0).all()
+
+
+def test_window_call_checks(lib):
+    src = np.zeros((64, 64), np.uint8)
+    dst = np.zeros((64, 64), np.uint8)
+    rc = lib.bnz_binarize_window(src.ctypes.data, 64, 64, 1, 15, bnz.BNZ_SAUVOLA, 0.5, 128.0, dst.ctypes.data, 1000)
+    assert rc == bnz.BNZ_EINVAL and "too small" in bnz.bnz_last_error()
+    rc = lib.bnz_binarize_window(src.ctypes.data, 64, 64, 1, 0, bnz.BNZ_SAUVOLA, 0.5, 128.0, dst.ctypes.data, 1 << 20)
+    assert rc == bnz.BNZ_EINVAL and "window size" in bnz.bnz_last_error()
+    import torch
+    if not torch.cuda.is_available():
+        rc = lib.bnz_binarize_window(src.ctypes.data, 64, 64, 1, 15, bnz.BNZ_SAUVOLA, 0.5, 128.0, dst.ctypes.data,
+                                     1 << 20)
+        assert rc == bnz.BNZ_ENODEV
