@@ -89,12 +89,15 @@ typedef enum { BNZ_SAUVOLA = 0, BNZ_NIBLACK = 1 } bnz_rule;
 /* Optional tile shape for the fused kernel (autotuner hook).  Zero fields
  * mean "library default".  tile_w: output columns per strip, 128, 256 or 512.
  * tile_h: approximate rows of work per CTA (sets the grid size).
- * chunk: rows per TMA load (8). */
+ * chunk: rows per TMA load (8).  edge_weight: cost of a row of the page's
+ * first or last strip (whose windows are clipped at the page's sides) against
+ * a row of an inner strip, in sixteenths (16: equal); the CTAs are dealt out
+ * per strip in that proportion. */
 typedef struct {
     int tile_w;
     int tile_h;
     int chunk;
-    int reserved;
+    int edge_weight;
 } bnz_tile;
 
 /* ---- synchronous host-pointer API (Eq. 3 with Eq. 4 / Niblack) ---------- */

@@ -57,7 +57,7 @@ class bnz_run(ctypes.Structure):
 
 class bnz_tile(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int), ("chunk", ctypes.c_int),
-                ("reserved", ctypes.c_int)]
+                ("edge_weight", ctypes.c_int)]
 
 
 _lib = None

@@ -133,8 +133,8 @@ __global__ void __launch_bounds__(NT, 1)
     __syncthreads();
     uint64_t phase = 0, ephase = 0, eused = 0;
     uint32_t nfb = 0, nties_s = 0, nties_n = 0;
-    const long long T = (long long)ps.tiles_x * (ps.y_hi - ps.y_lo);
-    const long long L0 = T * blockIdx.x / gridDim.x, L1 = T * (blockIdx.x + 1) / gridDim.x;
+    long long L0, L1;
+    cta_range(ps, L0, L1);
     for (long long cur = L0; cur < L1;) {
         const Segment sg = make_segment(ps, cur, L1);
         cur += sg.th_eff;

@@ -60,8 +60,8 @@ __global__ void __launch_bounds__(NT, 1)
     uint64_t phase = 0;             // bit i: parity of the next completion of full barrier i
     uint64_t ephase = 0, eused = 0; // TMA issuer: free-signal parity, slots ever loaded
     uint32_t nfb = 0, nties = 0;
-    const long long T = (long long)p.tiles_x * (p.y_hi - p.y_lo);
-    const long long L0 = T * blockIdx.x / gridDim.x, L1 = T * (blockIdx.x + 1) / gridDim.x;
+    long long L0, L1;
+    cta_range(p, L0, L1);
     for (long long cur = L0; cur < L1;) {
         const Segment sg = make_segment(p, cur, L1);
         cur += sg.th_eff;
@@ -315,6 +315,21 @@ int plan_fused(int h, int w, int ch, int W, const bnz_tile *tile, FusedPlan *pl,
     if (tile && tile->tile_h > 0)
         G = (T + tile->tile_h - 1) / tile->tile_h;
     G = std::max<long long>(1, std::min<long long>(G, 1 << 30));
+    // whole CTAs per strip when every strip gets at least two: the first and
+    // last strips get edge_weight/16 times an inner strip's share
+    const int S = pl->tiles_x;
+    pl->n_edge = 0;
+    if (S >= 2 && G >= 2 * S && rows >= 2) {
+        const int ew = (tile && tile->edge_weight > 0) ? tile->edge_weight : kEdgeWeight;
+        if (S == 2) {
+            G &= ~1ll;
+            pl->n_edge = (int)(G / 2);
+        } else {
+            const double tot = 2.0 * ew + 16.0 * (S - 2);
+            long long ne = std::llround((double)G * ew / tot);
+            pl->n_edge = (int)std::max<long long>(1, std::min<long long>(ne, (G - (S - 2)) / 2));
+        }
+    }
     pl->grid = (int)G;
     pl->rows_per_cta = (int)((T + G - 1) / G);
     return BNZ_OK;
@@ -339,6 +354,7 @@ void fill_fused_params(FusedParams *p, const FusedPlan &pl, int h, int w, int W,
     p->ngo = pl.ngo;
     p->ring_rows = pl.ring_rows;
     p->tiles_x = pl.tiles_x;
+    p->n_edge = pl.n_edge;
     p->off_ring = pl.off_ring;
     p->off_stage = pl.off_stage;
     p->off_cb = pl.off_cb;

@@ -47,12 +47,33 @@
 namespace bnz {
 namespace {
 
-constexpr int GT = 256;      // threads of a CTA = output columns of a strip
-constexpr int kMaxCorr = 12; // crossing points of the structures (at most 9 for W >= 3)
-constexpr int kPRow = 512;   // entries of a prefix row (the span is at most GT + BNZ_MAX_W + 1)
-constexpr int kPF = 8;       // entering rows loaded ahead
+constexpr int GT = 256;    // threads of a CTA = output columns of a strip
+constexpr int kPRow = 512; // entries of a prefix row (the span is at most GT + BNZ_MAX_W + 1 <= 512)
+constexpr int kPF = 8;     // entering rows loaded ahead
 
-enum : uint32_t { L_HC = 1u, L_VC = 2u, L_DP = 4u, L_DM = 8u, L_FRAME = 16u };
+// The lines of a structure, as disjoint pieces where possible (frame sides
+// and, with the frame, the centre row and column stop short of the frame):
+//   HC     centre row: offsets [a, b] (cross, star) or (a, b) (frame + cross)
+//   VFULL  centre column, rows [a, b] (cross, star)
+//   DIAG   dy = dx over [a, b] and dy = -dx over [-mm, mm]
+//   FRAME  rows a and b over [a, b]; columns a and b over rows (a, b)
+//   VCUT   column sums over rows (a, b): the frame's sides, and the centre
+//          column of frame + cross
+// CENTRE: extra counts of the centre pixel (lines through it beyond the first).
+// Frame + diagonals also counts the diagonals' four end points twice (they
+// lie on the frame).
+template <int GS>
+struct Shape {
+    static constexpr bool HC = GS == BNZ_GS_CROSS || GS == BNZ_GS_STAR || GS == BNZ_GS_FRAME_CROSS;
+    static constexpr bool HC_CUT = GS == BNZ_GS_FRAME_CROSS;
+    static constexpr bool VFULL = GS == BNZ_GS_CROSS || GS == BNZ_GS_STAR;
+    static constexpr bool DIAG = GS == BNZ_GS_DIAGONALS || GS == BNZ_GS_STAR || GS == BNZ_GS_FRAME_DIAGONALS;
+    static constexpr bool FRAME = GS >= BNZ_GS_FRAME;
+    static constexpr bool VCUT = FRAME;
+    static constexpr bool ENDS = GS == BNZ_GS_FRAME_DIAGONALS;
+    static constexpr int NH = (HC ? 1 : 0) + (FRAME ? 2 : 0); // prefix rows per output row
+    static constexpr int CENTRE = GS == BNZ_GS_STAR ? 3 : (GS == BNZ_GS_FRAME ? 0 : 1);
+};
 
 struct GsParams {
     const uint8_t *src;
@@ -60,17 +81,18 @@ struct GsParams {
     int a, b, mm;     // window offsets [a, b]; anti-diagonal offsets |d| <= mm
     int span, sp, nr; // span columns (GT + W + 1), their padded bytes, ring rows (W + 1)
     int seg_rows;     // output rows per CTA
-    uint32_t lines;   // L_* bits of the structure
-    int nh;           // prefix rows per step: centre row, frame top, frame bottom (in that order)
-    int ncorr;
-    int cdy[kMaxCorr], cdx[kMaxCorr], cex[kMaxCorr]; // crossing points and their extra counts
-    uint32_t off_v, off_d, off_p;                    // shared-memory offsets
-    FusedParams d;                                   // h, w, W, output, statistics, decision constants
+    uint32_t off_v, off_d, off_p; // shared-memory offsets
+    FusedParams d;    // h, w, W, output, statistics, decision constants (nW = |S'|)
 };
 
 __device__ __forceinline__ int back(int s, int k, int nr) // ring slot k rows above slot s (0 <= k < nr)
 {
     return s >= k ? s - k : s - k + nr;
+}
+
+__device__ __forceinline__ int clip_len(int lo, int hi, int n) // |[lo, hi] within [0, n)|
+{
+    return max(0, min(hi, n - 1) - max(lo, 0) + 1);
 }
 
 template <int CIN>
@@ -93,22 +115,19 @@ __device__ __forceinline__ uint32_t to_gray(uint32_t v)
     return (299u * (v & 0xffu) + 587u * ((v >> 8) & 0xffu) + 114u * (v >> 16) + 500u) / 1000u;
 }
 
-// Inclusive prefix sums of f and f^2 along one ring row: lane l covers span
-// columns [16 l, 16 l + 16); P[i] = sums over columns 0..i.
-__device__ __forceinline__ void prefix_row(const uint8_t *row, int sp, uint2 *P, int lane)
+// Inclusive prefix sums of f and f^2 over one half (256 span columns) of a
+// ring row: lane l covers columns [256 hf + 8 l, +8).  Each half is summed on
+// its own: a reader adds the first half's total P[255] to entries >= 256.
+__device__ __forceinline__ void prefix_half(const uint8_t *row, int sp, uint2 *P, int hf, int lane)
 {
-    uint32_t q[4] = {0u, 0u, 0u, 0u};
-    if (16 * lane < sp) {
-        const uint4 v = *reinterpret_cast<const uint4 *>(row + 16 * lane);
-        q[0] = v.x;
-        q[1] = v.y;
-        q[2] = v.z;
-        q[3] = v.w;
-    }
-    uint32_t s1[16], s2[16], a1 = 0u, a2 = 0u;
+    const int c0 = 256 * hf + 8 * lane;
+    uint2 q = make_uint2(0u, 0u);
+    if (c0 < sp)
+        q = *reinterpret_cast<const uint2 *>(row + c0);
+    uint32_t s1[8], s2[8], a1 = 0u, a2 = 0u;
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-        const uint32_t f = (q[i >> 2] >> (8 * (i & 3))) & 0xffu;
+    for (int i = 0; i < 8; ++i) {
+        const uint32_t f = ((i < 4 ? q.x : q.y) >> (8 * (i & 3))) & 0xffu;
         a1 += f;
         a2 += f * f;
         s1[i] = a1;
@@ -126,15 +145,29 @@ __device__ __forceinline__ void prefix_row(const uint8_t *row, int sp, uint2 *P,
     }
     e1 -= a1; // exclusive
     e2 -= a2;
-    uint4 *dst = reinterpret_cast<uint4 *>(P + 16 * lane);
+    uint4 *dst = reinterpret_cast<uint4 *>(P + c0);
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < 4; ++i)
         dst[i] = make_uint4(e1 + s1[2 * i], e2 + s2[2 * i], e1 + s1[2 * i + 1], e2 + s2[2 * i + 1]);
 }
 
-template <int CIN, int RULE>
+// Sums over span columns (i0, i1] of a prefix row written in two halves.
+__device__ __forceinline__ uint2 seg(const uint2 *P, int i0, int i1)
+{
+    const uint2 hi = P[i1], lo = P[i0];
+    uint2 r = make_uint2(hi.x - lo.x, hi.y - lo.y);
+    if (i1 >= 256 && i0 < 256) {
+        const uint2 t = P[255];
+        r.x += t.x;
+        r.y += t.y;
+    }
+    return r;
+}
+
+template <int CIN, int RULE, int GS>
 __global__ void __launch_bounds__(GT) gs_kernel(const __grid_constant__ GsParams g)
 {
+    using S = Shape<GS>;
     extern __shared__ __align__(16) uint8_t smem[];
     const FusedParams &p = g.d;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -143,9 +176,8 @@ __global__ void __launch_bounds__(GT) gs_kernel(const __grid_constant__ GsParams
     const int yb = min(p.h, ya + g.seg_rows);
     const int a = g.a, b = g.b, mm = g.mm, W = p.W, nr = g.nr, span = g.span, sp = g.sp;
     const int cs = x0 + a - 1; // first span column
-    const uint32_t lines = g.lines;
     uint8_t *ring = smem;
-    uint2 *V = reinterpret_cast<uint2 *>(smem + g.off_v);
+    uint2 *V = reinterpret_cast<uint2 *>(smem + g.off_v); // column sums of every span column (W or W - 2 rows)
     uint2 *Dp = reinterpret_cast<uint2 *>(smem + g.off_d);
     uint2 *Dm = Dp + GT;
     uint2 *P = reinterpret_cast<uint2 *>(smem + g.off_p);
@@ -154,12 +186,13 @@ __global__ void __launch_bounds__(GT) gs_kernel(const __grid_constant__ GsParams
         reinterpret_cast<uint4 *>(ring)[i] = make_uint4(0u, 0u, 0u, 0u);
     Dp[t] = make_uint2(0u, 0u);
     Dm[t] = make_uint2(0u, 0u);
-    uint2 va = make_uint2(0u, 0u), vb = make_uint2(0u, 0u); // vertical sums of span columns t, t + GT
+    uint2 va = make_uint2(0u, 0u), vb = make_uint2(0u, 0u); // column sums of span columns t, t + GT
 
-    // per-column constants of the output pixel (clipped line lengths)
+    // per-column constants of the output pixel
     const bool xin = x < p.w;
-    const int cnt_h = min(x + b, p.w - 1) - max(x + a, 0) + 1;
-    const int cin_a = (unsigned)(x + a) < (unsigned)p.w, cin_b = (unsigned)(x + b) < (unsigned)p.w;
+    const bool x_inner = x + a >= 0 && x + b < p.w;
+    const int cnt_h = clip_len(x + a, x + b, p.w), cnt_hc = clip_len(x + a + 1, x + b - 1, p.w);
+    const bool cin_a = (unsigned)(x + a) < (unsigned)p.w, cin_b = (unsigned)(x + b) < (unsigned)p.w;
 
     const int y_first = ya - (W - 1); // entering row ya + a: the first row of the first output's window
     int es = (y_first + b) % nr;
@@ -194,21 +227,22 @@ __global__ void __launch_bounds__(GT) gs_kernel(const __grid_constant__ GsParams
         }
         __syncthreads();
 
-        const int ls = back(es, W, nr); // leaving row e - W
-        const uint8_t *rl = ring + ls * sp;
-        if (lines & (L_VC | L_FRAME)) {
-            const uint32_t u = re[t], v = rl[t];
+        if (S::VFULL || S::VCUT) { // rows [y + a, y + b] (entering e, leaving e - W) or (y + a, y + b)
+            const uint8_t *ri = S::VFULL ? re : ring + back(es, 1, nr) * sp;
+            const uint8_t *ro = ring + back(es, S::VFULL ? W : W - 1, nr) * sp;
+            const uint32_t u = ri[t], v = ro[t];
             va.x += u - v;
             va.y += u * u - v * v;
             V[t] = va;
             if (t + GT < span) {
-                const uint32_t u2 = re[t + GT], v2 = rl[t + GT];
+                const uint32_t u2 = ri[t + GT], v2 = ro[t + GT];
                 vb.x += u2 - v2;
                 vb.y += u2 * u2 - v2 * v2;
                 V[t + GT] = vb;
             }
         }
-        if (lines & L_DP) {
+        if (S::DIAG) {
+            const uint8_t *rl = ring + back(es, W, nr) * sp; // row y + a - 1
             const int s = (t - y) & (GT - 1);
             if (t != 0) { // continue the diagonal of (y - 1, x - 1)
                 const uint32_t u = re[t + W], v = rl[t];
@@ -229,16 +263,14 @@ __global__ void __launch_bounds__(GT) gs_kernel(const __grid_constant__ GsParams
                 if (t == 0) // the slot of that column
                     Dp[s] = make_uint2(s1, s2);
             }
-        }
-        if (lines & L_DM) {
-            const int s = (t + y) & (GT - 1);
+            const int sm = (t + y) & (GT - 1);
             if (t != GT - 1) { // continue the anti-diagonal of (y - 1, x + 1)
                 const uint8_t *rdl = ring + back(es, b + mm + 1, nr) * sp;
                 const uint32_t u = re[t - mm - a + 1], v = rdl[t + W + 1];
-                uint2 d = Dm[s];
+                uint2 d = Dm[sm];
                 d.x += u - v;
                 d.y += u * u - v * v;
-                Dm[s] = d;
+                Dm[sm] = d;
             }
             if (warp == GT / 32 - 1) { // the anti-diagonal entering at the strip's last column
                 uint32_t s1 = 0u, s2 = 0u;
@@ -251,65 +283,91 @@ __global__ void __launch_bounds__(GT) gs_kernel(const __grid_constant__ GsParams
                 s1 = __reduce_add_sync(0xffffffffu, s1);
                 s2 = __reduce_add_sync(0xffffffffu, s2);
                 if (t == GT - 1) // the slot of that column
-                    Dm[s] = make_uint2(s1, s2);
+                    Dm[sm] = make_uint2(s1, s2);
             }
         }
         const bool out_row = y >= ya;
-        if (out_row && warp < g.nh) { // row sums: prefix of row y (centre), y + a (frame top) or e (frame bottom)
-            const int kb = (lines & L_HC) ? (warp == 0 ? b : (warp == 1 ? W - 1 : 0)) : (warp == 0 ? W - 1 : 0);
-            prefix_row(ring + back(es, kb, nr) * sp, sp, P + warp * kPRow, lane);
+        if (S::NH > 0 && out_row && warp < 2 * S::NH) {
+            // prefix rows, two warps each: centre row y (back b), frame top y + a (back W - 1), bottom e (back 0)
+            const int j = warp >> 1;
+            const int kb = S::HC ? (j == 0 ? b : (j == 1 ? W - 1 : 0)) : (j == 0 ? W - 1 : 0);
+            prefix_half(ring + back(es, kb, nr) * sp, sp, P + j * kPRow, warp & 1, lane);
         }
         __syncthreads();
 
         if (out_row && xin) {
-            const int ys = back(es, b, nr); // row y
-            const uint32_t f = ring[ys * sp + t - a + 1];
-            uint32_t n = 0u, S1 = 0u, S2 = 0u;
-            const int cnt_v = min(y + b, p.h - 1) - max(y + a, 0) + 1;
+            const uint32_t f = ring[back(es, b, nr) * sp + t - a + 1];
+            uint32_t S1 = 0u, S2 = 0u;
             int pr = 0;
-            if (lines & L_HC) {
-                const uint2 hi = P[t + W], lo = P[t];
-                S1 += hi.x - lo.x;
-                S2 += hi.y - lo.y;
-                n += cnt_h;
+            if (S::HC) { // span columns of x + a .. x + b are t + 1 .. t + W
+                const uint2 h = S::HC_CUT ? seg(P, t + 1, t + W - 1) : seg(P, t, t + W);
+                S1 += h.x;
+                S2 += h.y;
                 pr = 1;
             }
-            if (lines & L_VC) {
+            if (S::VFULL || S::HC_CUT) { // centre column
                 const uint2 v = V[t - a + 1];
                 S1 += v.x;
                 S2 += v.y;
-                n += cnt_v;
             }
-            if (lines & L_FRAME) {
-                const uint2 th = P[pr * kPRow + t + W], tl = P[pr * kPRow + t];
-                const uint2 bh = P[(pr + 1) * kPRow + t + W], bl = P[(pr + 1) * kPRow + t];
+            if (S::FRAME) {
+                const uint2 top = seg(P + pr * kPRow, t, t + W), bot = seg(P + (pr + 1) * kPRow, t, t + W);
                 const uint2 vl = V[t + 1], vr = V[t + W];
-                S1 += (th.x - tl.x) + (bh.x - bl.x) + vl.x + vr.x;
-                S2 += (th.y - tl.y) + (bh.y - bl.y) + vl.y + vr.y;
-                n += ((unsigned)(y + a) < (unsigned)p.h ? cnt_h : 0) + ((unsigned)(y + b) < (unsigned)p.h ? cnt_h : 0) +
-                     (cin_a ? cnt_v : 0) + (cin_b ? cnt_v : 0);
+                S1 += top.x + bot.x + vl.x + vr.x;
+                S2 += top.y + bot.y + vl.y + vr.y;
             }
-            if (lines & L_DP) {
-                const uint2 d = Dp[(t - y) & (GT - 1)];
-                S1 += d.x;
-                S2 += d.y;
-                const int lo = max(a, max(-y, -x)), hi = min(b, min(p.h - 1 - y, p.w - 1 - x));
-                n += max(0, hi - lo + 1);
+            if (S::DIAG) {
+                const uint2 d = Dp[(t - y) & (GT - 1)], m = Dm[(t + y) & (GT - 1)];
+                S1 += d.x + m.x;
+                S2 += d.y + m.y;
             }
-            if (lines & L_DM) {
-                const uint2 d = Dm[(t + y) & (GT - 1)];
-                S1 += d.x;
-                S2 += d.y;
-                const int lo = max(-mm, max(-y, x - (p.w - 1))), hi = min(mm, min(p.h - 1 - y, x));
-                n += max(0, hi - lo + 1);
+            S1 -= S::CENTRE * f;
+            S2 -= S::CENTRE * f * f;
+            uint2 ends = make_uint2(0u, 0u);
+            int nends = 0;
+            if (S::ENDS) { // the diagonals' end points, also on the frame
+                const uint2 *Pt = P + pr * kPRow, *Pb = P + (pr + 1) * kPRow;
+                const uint2 e0 = seg(Pt, t, t + 1);          // (a, a)
+                const uint2 e1 = seg(Pb, t + W - 1, t + W);  // (b, b)
+                uint2 e2, e3;
+                if (mm == b && a == -b) {                    // odd W: (a, b) and (b, a)
+                    e2 = seg(Pt, t + W - 1, t + W);
+                    e3 = seg(Pb, t, t + 1);
+                } else {                                     // even W: (-b, b) on column b, (b, -b) on row b
+                    const uint32_t v = ring[back(es, 2 * b, nr) * sp + t + W];
+                    e2 = make_uint2(v, v * v);
+                    e3 = seg(Pb, t + 1, t + 2);
+                }
+                ends = make_uint2(e0.x + e1.x + e2.x + e3.x, e0.y + e1.y + e2.y + e3.y);
+                S1 -= ends.x;
+                S2 -= ends.y;
+                if (!(x_inner && y + a >= 0 && y + b < p.h)) {
+                    const int ye = mm == b && a == -b ? a : -b, xe = -ye; // the anti-diagonal's upper end
+                    nends = ((unsigned)(y + a) < (unsigned)p.h && cin_a) + ((unsigned)(y + b) < (unsigned)p.h && cin_b) +
+                            ((unsigned)(y + ye) < (unsigned)p.h && (unsigned)(x + xe) < (unsigned)p.w) +
+                            ((unsigned)(y - ye) < (unsigned)p.h && (unsigned)(x - xe) < (unsigned)p.w);
+                }
             }
-            for (int c = 0; c < g.ncorr; ++c) { // crossing points counted more than once
-                const int dy = g.cdy[c], dx = g.cdx[c], ex = g.cex[c];
-                const uint32_t v = ring[back(es, b - dy, nr) * sp + t + dx - a + 1];
-                S1 -= ex * v;
-                S2 -= ex * v * v;
-                if ((unsigned)(y + dy) < (unsigned)p.h && (unsigned)(x + dx) < (unsigned)p.w)
-                    n -= ex;
+            uint32_t n;
+            if (x_inner && y + a >= 0 && y + b < p.h) {
+                n = p.nW; // the whole structure inside the page: |S'|
+            } else {
+                const int cnt_v = clip_len(y + a, y + b, p.h), cnt_vc = clip_len(y + a + 1, y + b - 1, p.h);
+                int c = 0;
+                if (S::HC)
+                    c += S::HC_CUT ? cnt_hc : cnt_h;
+                if (S::VFULL)
+                    c += cnt_v;
+                if (S::HC_CUT)
+                    c += cnt_vc;
+                if (S::FRAME)
+                    c += ((unsigned)(y + a) < (unsigned)p.h ? cnt_h : 0) + ((unsigned)(y + b) < (unsigned)p.h ? cnt_h : 0) +
+                         (cin_a ? cnt_vc : 0) + (cin_b ? cnt_vc : 0);
+                if (S::DIAG) {
+                    c += max(0, min(b, min(p.h - 1 - y, p.w - 1 - x)) - max(a, max(-y, -x)) + 1);
+                    c += max(0, min(mm, min(p.h - 1 - y, x)) - max(-mm, max(-y, x - (p.w - 1))) + 1);
+                }
+                n = (uint32_t)(c - S::CENTRE - nends);
             }
             const uint32_t r = decide_pixel<RULE>(f, n, S1, S2, p, nfb, nties);
             p.dst[(long long)y * p.dst_pitch + x] = (uint8_t)r;
@@ -360,75 +418,50 @@ __global__ void __launch_bounds__(256) confusion_kernel(const uint8_t *mask, lon
         atomicAdd(counts + threadIdx.x, s[threadIdx.x]);
 }
 
-struct Line {
-    int kind; // 0 row dy = v, 1 column dx = v, 2 diagonal, 3 anti-diagonal
-    int v;
-};
-
-// Lines of a structure, its L_* bits, and the crossing points with their extra counts.
-int structure(int gs, int W, GsParams *g)
+// |S'|: the structure's offsets in the W x W window (the definition, counted).
+int structure_size(int gs, int W)
 {
-    const int a = -(W / 2), b = W - 1 - W / 2, mm = std::min(W / 2, W - 1 - W / 2);
-    Line ls[8];
-    int nl = 0;
-    uint32_t bits = 0;
-    const bool cross = gs == BNZ_GS_CROSS || gs == BNZ_GS_STAR || gs == BNZ_GS_FRAME_CROSS;
-    const bool diag = gs == BNZ_GS_DIAGONALS || gs == BNZ_GS_STAR || gs == BNZ_GS_FRAME_DIAGONALS;
-    const bool frame = gs == BNZ_GS_FRAME || gs == BNZ_GS_FRAME_CROSS || gs == BNZ_GS_FRAME_DIAGONALS;
-    if (cross) {
-        ls[nl++] = {0, 0};
-        ls[nl++] = {1, 0};
-        bits |= L_HC | L_VC;
-    }
-    if (diag) {
-        ls[nl++] = {2, 0};
-        ls[nl++] = {3, 0};
-        bits |= L_DP | L_DM;
-    }
-    if (frame) {
-        ls[nl++] = {0, a};
-        ls[nl++] = {0, b};
-        ls[nl++] = {1, a};
-        ls[nl++] = {1, b};
-        bits |= L_FRAME;
-    }
-    auto on = [&](const Line &l, int dy, int dx) {
-        switch (l.kind) {
-        case 0: return dy == l.v;
-        case 1: return dx == l.v;
-        case 2: return dy == dx;
-        default: return dy == -dx && dy >= -mm && dy <= mm;
-        }
-    };
-    g->a = a;
-    g->b = b;
-    g->mm = mm;
-    g->lines = bits;
-    g->nh = ((bits & L_HC) ? 1 : 0) + ((bits & L_FRAME) ? 2 : 0);
-    g->ncorr = 0;
+    const int a = -(W / 2), b = W - 1 - W / 2;
+    int n = 0;
     for (int dy = a; dy <= b; ++dy)
         for (int dx = a; dx <= b; ++dx) {
-            int c = 0;
-            for (int i = 0; i < nl; ++i)
-                c += on(ls[i], dy, dx) ? 1 : 0;
-            if (c > 1) {
-                if (g->ncorr == kMaxCorr)
-                    return fail(BNZ_EINVAL, "structure %d: too many crossing points for W = %d", gs, W);
-                g->cdy[g->ncorr] = dy;
-                g->cdx[g->ncorr] = dx;
-                g->cex[g->ncorr] = c - 1;
-                ++g->ncorr;
+            const bool cross = dy == 0 || dx == 0;
+            const bool diag = dy == dx || dy == -dx;
+            const bool frame = dy == a || dy == b || dx == a || dx == b;
+            bool in = false;
+            switch (gs) {
+            case BNZ_GS_CROSS: in = cross; break;
+            case BNZ_GS_DIAGONALS: in = diag; break;
+            case BNZ_GS_STAR: in = cross || diag; break;
+            case BNZ_GS_FRAME: in = frame; break;
+            case BNZ_GS_FRAME_CROSS: in = frame || cross; break;
+            default: in = frame || diag; break;
             }
+            n += in ? 1 : 0;
         }
-    return BNZ_OK;
+    return n;
 }
 
 size_t round16(size_t v) { return (v + 15) / 16 * 16; }
 
 template <int CIN, int RULE>
-const void *kernel_fn()
+const void *kernel_fn(int gs)
 {
-    return reinterpret_cast<const void *>(&gs_kernel<CIN, RULE>);
+    switch (gs) {
+    case BNZ_GS_CROSS: return reinterpret_cast<const void *>(&gs_kernel<CIN, RULE, BNZ_GS_CROSS>);
+    case BNZ_GS_DIAGONALS: return reinterpret_cast<const void *>(&gs_kernel<CIN, RULE, BNZ_GS_DIAGONALS>);
+    case BNZ_GS_STAR: return reinterpret_cast<const void *>(&gs_kernel<CIN, RULE, BNZ_GS_STAR>);
+    case BNZ_GS_FRAME: return reinterpret_cast<const void *>(&gs_kernel<CIN, RULE, BNZ_GS_FRAME>);
+    case BNZ_GS_FRAME_CROSS: return reinterpret_cast<const void *>(&gs_kernel<CIN, RULE, BNZ_GS_FRAME_CROSS>);
+    default: return reinterpret_cast<const void *>(&gs_kernel<CIN, RULE, BNZ_GS_FRAME_DIAGONALS>);
+    }
+}
+
+const void *kernel_for(int ch, int rule, int gs)
+{
+    if (ch == 1)
+        return rule == BNZ_SAUVOLA ? kernel_fn<1, BNZ_SAUVOLA>(gs) : kernel_fn<1, BNZ_NIBLACK>(gs);
+    return rule == BNZ_SAUVOLA ? kernel_fn<3, BNZ_SAUVOLA>(gs) : kernel_fn<3, BNZ_NIBLACK>(gs);
 }
 
 std::once_flag g_attr_once[64];
@@ -440,15 +473,14 @@ int set_attributes(int dev)
         return fail(BNZ_ENODEV, "device ordinal %d out of range", dev);
     std::call_once(g_attr_once[dev], [dev] {
         int rc = BNZ_OK;
-        const void *fns[4] = {kernel_fn<1, BNZ_SAUVOLA>(), kernel_fn<1, BNZ_NIBLACK>(), kernel_fn<3, BNZ_SAUVOLA>(),
-                              kernel_fn<3, BNZ_NIBLACK>()};
-        for (const void *fn : fns) {
-            cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-            if (e != cudaSuccess) {
-                rc = cuda_fail(e, "cudaFuncSetAttribute(gs kernel)");
-                break;
-            }
-        }
+        for (int ch : {1, 3})
+            for (int rule : {BNZ_SAUVOLA, BNZ_NIBLACK})
+                for (int gs = BNZ_GS_CROSS; gs <= BNZ_GS_FRAME_DIAGONALS && rc == BNZ_OK; ++gs) {
+                    cudaError_t e = cudaFuncSetAttribute(kernel_for(ch, rule, gs),
+                                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+                    if (e != cudaSuccess)
+                        rc = cuda_fail(e, "cudaFuncSetAttribute(gs kernel)");
+                }
         g_attr_rc[dev] = rc;
     });
     return g_attr_rc[dev];
@@ -461,10 +493,19 @@ int launch_gs(const uint8_t *d_src, size_t src_pitch, int h, int w, int ch, int 
 {
     GsParams g;
     memset(&g, 0, sizeof g);
-    int rc = structure(gs, W, &g);
-    if (rc != BNZ_OK)
-        return rc;
+    g.a = -(W / 2);
+    g.b = W - 1 - W / 2;
+    g.mm = std::min(W / 2, W - 1 - W / 2);
+    const bool hc = gs == BNZ_GS_CROSS || gs == BNZ_GS_STAR || gs == BNZ_GS_FRAME_CROSS;
+    const int nh = (hc ? 1 : 0) + (gs >= BNZ_GS_FRAME ? 2 : 0);
     fill_decision_params(&g.d, h, w, W, rule, k, R);
+    // the fp32 filter's constants for the unclipped structure, n = |S'|
+    const double n = (double)structure_size(gs, W);
+    g.d.nW = (uint32_t)n;
+    g.d.omkn = (float)((1.0 - k) / n);
+    g.d.kRn2 = (float)(k / (R * n * n));
+    g.d.invn = (float)(1.0 / n);
+    g.d.kn = (float)(k / n);
     g.d.dst = d_dst;
     g.d.dst_pitch = (long long)dst_pitch;
     g.d.stats = d_stats;
@@ -479,9 +520,9 @@ int launch_gs(const uint8_t *d_src, size_t src_pitch, int h, int w, int ch, int 
     g.off_d = (uint32_t)off;
     off += 2 * GT * sizeof(uint2);
     g.off_p = (uint32_t)off;
-    off += (size_t)std::max(g.nh, 1) * kPRow * sizeof(uint2);
+    off += (size_t)std::max(nh, 1) * kPRow * sizeof(uint2);
     const size_t smem = off;
-    int dev = 0, occ = 0, sms = 0;
+    int dev = 0, occ = 0, sms = 0, rc = BNZ_OK;
     rc = device_sm_count(&sms);
     if (rc != BNZ_OK)
         return rc;
@@ -491,8 +532,7 @@ int launch_gs(const uint8_t *d_src, size_t src_pitch, int h, int w, int ch, int 
     rc = set_attributes(dev);
     if (rc != BNZ_OK)
         return rc;
-    const void *fn = ch == 1 ? (rule == BNZ_SAUVOLA ? kernel_fn<1, BNZ_SAUVOLA>() : kernel_fn<1, BNZ_NIBLACK>())
-                             : (rule == BNZ_SAUVOLA ? kernel_fn<3, BNZ_SAUVOLA>() : kernel_fn<3, BNZ_NIBLACK>());
+    const void *fn = kernel_for(ch, rule, gs);
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, GT, smem);
     if (e != cudaSuccess)
         return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(gs kernel)");

@@ -41,6 +41,7 @@ struct FusedPlan {
     int ngo;        // 4-column groups whose column sums the consumers read (from group o4 on)
     int tiles_x;    // strips across the image
     int grid;       // persistent CTAs
+    int n_edge;     // CTAs on each of the first and last strips (0: one even split of all strip-rows)
     int rows_per_cta;
     uint32_t off_ring, off_stage, off_cb; // column sums: 2 buffers x {c1, c2} x CH rows x RS words
     size_t smem;
@@ -55,6 +56,7 @@ struct FusedParams {
     int y_lo, y_hi;  // output rows [y_lo, y_hi) of this launch (the window clips at 0 and h)
     int TW, CH, NS, NSS, SWP, ring_rows, tiles_x;
     int o4, wq, ngo; // column-sum groups: origin, entering-stream offset, count (see FusedPlan)
+    int n_edge;      // CTAs per edge strip, the rest dealt evenly over the inner strips (0: even split)
     uint32_t off_ring, off_stage, off_cb;
     int packed;     // 1: one bit per pixel
     int vec_ok;     // dst and dst_pitch 16-byte aligned
@@ -84,6 +86,8 @@ void fill_fused_params(FusedParams *p, const FusedPlan &pl, int h, int w, int W,
                        uint8_t *d_dst, size_t dst_pitch, int packed, unsigned long long *d_stats,
                        unsigned int *d_err);
 constexpr int kMaxBarriers = 96; // mbarriers reserved at the start of shared memory: full + empty per slot
+// Default cost of an edge strip's row against an inner strip's, in sixteenths (bnz_tile.edge_weight).
+constexpr int kEdgeWeight = 20; // measured best of 16..32 on 4096^2 RGB pages, W 15..101, both rules
 // Raise the kernel's dynamic shared-memory limit to the largest plan, once per device.
 int ensure_smem_optin(const void *fn);
 // Output rows [y_lo, y_hi) of the page (0, h: all); the kernel reads input rows

@@ -124,6 +124,40 @@ __device__ __forceinline__ Segment make_segment(const FusedParams &p, long long 
     return sg;
 }
 
+// The strip-rows [L0, L1) of this CTA.  n_edge > 0: whole CTAs per strip, so
+// that no CTA starts a second segment (each segment first sums its window's
+// rows): n_edge CTAs on the first and on the last strip (their windows clip
+// at the page's sides, the slower path), the others dealt evenly over the
+// inner strips; each CTA takes an even share of its strip's rows.
+__device__ __forceinline__ void cta_range(const FusedParams &p, long long &L0, long long &L1)
+{
+    const int nr = p.y_hi - p.y_lo;
+    const int G = (int)gridDim.x, i = (int)blockIdx.x;
+    if (p.n_edge <= 0) {
+        const long long T = (long long)p.tiles_x * nr;
+        L0 = T * i / G;
+        L1 = T * (i + 1) / G;
+        return;
+    }
+    const int S = p.tiles_x, ne = p.n_edge;
+    int s, j, n;
+    if (i < ne) {
+        s = 0, j = i, n = ne;
+    } else if (i >= G - ne) {
+        s = S - 1, j = i - (G - ne), n = ne;
+    } else {
+        const int m = S - 2, R = G - 2 * ne, q = R / m, rem = R % m, k = i - ne;
+        if (k < rem * (q + 1)) {
+            s = 1 + k / (q + 1), j = k % (q + 1), n = q + 1;
+        } else {
+            const int k2 = k - rem * (q + 1);
+            s = 1 + rem + k2 / q, j = k2 % q, n = q;
+        }
+    }
+    L0 = (long long)s * nr + (long long)nr * j / n;
+    L1 = (long long)s * nr + (long long)nr * (j + 1) / n;
+}
+
 // ---------------------------------------------------------------------------
 // producers: TMA ring, RGB->gray, column sums (a1-a3)
 // ---------------------------------------------------------------------------

@@ -4,7 +4,9 @@ For each (channels, W) it times the fused kernel on a synthetic page with
 every strip width that fits shared memory (512, 256, 128 output columns) and
 several heights of the rows each CTA walks (the library's default split over
 one CTA per SM, or a fixed number of rows per CTA, which sets the grid) and
-keeps the fastest pair.  The page is tall (4096 rows by default) so that, as
+keeps the fastest pair, then the fastest edge weight for it (the share of CTAs
+given to the page's first and last strips, whose clipped windows take the
+slower path).  The page is tall (4096 rows by default) so that, as
 in a batch or a stream of pages, the W rows of warm-up at the top of each
 strip segment are amortized.  Results are cached as JSON keyed by GPU name,
 library version and a hash of the kernel sources, so tuning is done once per
@@ -22,6 +24,7 @@ from . import (BNZ_SAUVOLA, BnzError, alloc_pitched, bnz_binarize_dev, bnz_tile,
 DEFAULT_WINDOWS = (15, 25, 31, 45, 61, 75, 101)
 TILE_WIDTHS = (512, 256, 128)
 TILE_HEIGHTS = (0, 128, 256, 512)   # rows per CTA; 0 = the library's split over one CTA per SM
+EDGE_WEIGHTS = (16, 18, 20, 22, 24)  # an edge strip's row cost in sixteenths of an inner strip's
 
 
 def build_key() -> str:
@@ -65,8 +68,8 @@ def _time_one(src, out, W, tile, reps):
 
 def tune(windows=DEFAULT_WINDOWS, channels=(1, 3), shape=(4096, 4096), reps: int = 7, seed: int = 4,
          save: bool = True, heights=TILE_HEIGHTS) -> dict:
-    """Return {"1": {"15": {"tile_w": 512, "tile_h": 0, "ms": ...}, ...}, "3": {...}} and cache it unless
-    save=False."""
+    """Return {"1": {"15": {"tile_w": 512, "tile_h": 0, "edge_weight": 20, "ms": ...}, ...}, "3": {...}} and
+    cache it unless save=False."""
     import torch
     import synth
     from . import to_device_pitched
@@ -86,7 +89,9 @@ def tune(windows=DEFAULT_WINDOWS, channels=(1, 3), shape=(4096, 4096), reps: int
                     except BnzError:
                         break  # this width does not fit shared memory
             (tw, th) = min(timings, key=timings.get)
-            best[str(W)] = {"tile_w": tw, "tile_h": th, "ms": round(timings[(tw, th)], 5)}
+            edge = {ew: _time_one(src, out, W, bnz_tile(tw, th, 0, ew), reps) for ew in EDGE_WEIGHTS}
+            ew = min(edge, key=edge.get)
+            best[str(W)] = {"tile_w": tw, "tile_h": th, "edge_weight": ew, "ms": round(edge[ew], 5)}
         table[str(ch)] = best
     if save:
         path = cache_path()
@@ -120,6 +125,6 @@ def tile_for(table: dict | None, channels: int, W: int) -> int:
 
 
 def tile_shape_for(table: dict | None, channels: int, W: int):
-    """bnz_tile(tile_w, tile_h) tuned for the nearest W, or None (library default)."""
+    """bnz_tile(tile_w, tile_h, 0, edge_weight) tuned for the nearest W, or None (library default)."""
     e = _entry(table, channels, W)
-    return bnz_tile(int(e["tile_w"]), int(e["tile_h"]), 0, 0) if e else None
+    return bnz_tile(int(e["tile_w"]), int(e["tile_h"]), 0, int(e.get("edge_weight", 0))) if e else None

@@ -108,12 +108,14 @@ def test_autotuner_table_and_lookup(bnz, tmp_path, monkeypatch):
     monkeypatch.setenv("BNZ_TUNE_CACHE", str(tmp_path / "t.json"))
     table = tune.tune(windows=(15, 101), channels=(1,), shape=(512, 1024), reps=3)
     assert set(table["1"]) == {"15", "101"}
-    assert all(v["tile_w"] in (128, 256, 512) and v["tile_h"] in tune.TILE_HEIGHTS for v in table["1"].values())
+    assert all(v["tile_w"] in (128, 256, 512) and v["tile_h"] in tune.TILE_HEIGHTS and
+               v["edge_weight"] in tune.EDGE_WEIGHTS for v in table["1"].values())
     assert table["build"] == tune.build_key()
     assert tune.load_table() == table
     assert tune.tile_for(table, 1, 17) == table["1"]["15"]["tile_w"]
     t = tune.tile_shape_for(table, 1, 17)
-    assert (t.tile_w, t.tile_h) == (table["1"]["15"]["tile_w"], table["1"]["15"]["tile_h"])
+    e = table["1"]["15"]
+    assert (t.tile_w, t.tile_h, t.edge_weight) == (e["tile_w"], e["tile_h"], e["edge_weight"])
     assert tune.tile_for(None, 1, 17) == 0 and tune.tile_shape_for(None, 1, 17) is None
     # the tuned shape gives the oracle's mask
     img = synth.page(700, 1100, 5, synth.DOC, 1)

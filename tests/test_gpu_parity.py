@@ -274,3 +274,14 @@ def test_host_one_page_several_settings(bnz, h, w, ch):
         assert not np.any(got != ref), f"{rule} W={W}: {int(np.sum(got != ref))} mismatches"
     again = bnz.binarize_runs(img, runs[:1])
     np.testing.assert_array_equal(again[0], masks[0])
+
+
+@pytest.mark.parametrize("ew", [16, 24, 40])
+@pytest.mark.parametrize("w", [1100, 1500, 2200])
+def test_edge_weight_split(bnz, ew, w):
+    """Whole CTAs per strip, the edge strips weighted: every split covers every row once (oracle-exact)."""
+    img = synth.page(700, w, ew + w, synth.STAINS, 3)
+    ref, _ = oracle.binarize(img, 31, oracle.SAUVOLA, 0.5, 128.0, threads=os.cpu_count() or 4)
+    for tile in (bnz.bnz_tile(0, 0, 0, ew), bnz.bnz_tile(256, 40, 0, ew)):
+        got = bnz.binarize(bnz.to_device_pitched(img), 31, "sauvola", 0.5, 128.0, tile=tile).cpu().numpy()
+        assert np.array_equal(got, ref)
