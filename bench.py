@@ -631,8 +631,9 @@ def batch_summary(bnz, dev):
 
 def serve_summary(bnz, args):
     """Config 5 on a reduced request count: the native serving engine, batched steps vs one plain launch per
-    page, pages from pinned host memory ("host") and already on the device ("resident"): closed-loop capacity,
-    then the Poisson trace at 0.8 of the batched arm's capacity with p50/p99 latency."""
+    page, pages from pinned host memory ("host") and already on the device ("resident"): closed-loop capacity
+    (median of three runs, all three listed), then the Poisson trace at 0.8 of the batched arm's capacity with
+    p50/p99 latency."""
     import torch
     import synth
     from paper_1210_3165_gb300.serve import NativeServer
@@ -650,8 +651,8 @@ def serve_summary(bnz, args):
         res = {}
         for name, mk in arms.items():
             serve_once(mk, reqs[:32], None)
-            cap = serve_once(mk, reqs, None)
-            res[name] = {"capacity_pages_per_s": round(cap["pages_per_s"], 1)}
+            caps = sorted(serve_once(mk, reqs, None)["pages_per_s"] for _ in range(3))
+            res[name] = {"capacity_pages_per_s": round(caps[1], 1), "capacity_runs": [round(c, 1) for c in caps]}
         load = 0.8 * res["batched"]["capacity_pages_per_s"]
         for name, mk in arms.items():
             st = serve_once(mk, reqs, load)
@@ -1023,6 +1024,38 @@ def run_gs(args):
     return 0
 
 
+def run_edge_sweep(args):
+    """Fused kernel time per launch against bnz_tile.edge_weight on the page workload (blocks of 20 launches,
+    median of 7, each launch on its own input copy): the sweep behind the library's default edge weight."""
+    import torch
+    import paper_1210_3165_gb300 as bnz
+    torch.cuda.set_device(0)
+    bnz.load()
+    page = host_page()
+    srcs = [bnz.to_device_pitched(page) for _ in range(NCOPY)]
+    outs = [bnz.alloc_pitched(H, W_IMG) for _ in range(NCOPY)]
+    stream = torch.cuda.Stream()
+    rot = [0]
+    res = {}
+    for W, rule, k, R in RUNS:
+        row = {}
+        rid = bnz.BNZ_SAUVOLA if rule == "sauvola" else bnz.BNZ_NIBLACK
+        for ew in (16, 18, 20, 22, 24, 28, 32):
+            tile = bnz.bnz_tile(0, 0, 0, ew)
+
+            def call():
+                c = rot[0] % NCOPY
+                rot[0] += 1
+                bnz.bnz_binarize_dev(srcs[c], W, rid, k, R, outs[c], tile=tile, stream=stream)
+            with torch.cuda.stream(stream):
+                for _ in range(max(args.warmup, 3)):
+                    call()
+            row[ew] = round(_block_ms(call, stream, 20, 7) * 1e3, 2)
+        res[f"{rule}_W{W}"] = row
+    print(json.dumps({"workload": WORKLOAD, "us_per_launch_by_edge_weight": res}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1034,7 +1067,7 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the other configurations' keys")
     ap.add_argument("--min-seconds", type=float, default=1.0,
                     help="repeat the K-step timed pass until this much time has passed (median pass reported)")
-    ap.add_argument("--workload", default="page", choices=["page", "batch", "serve", "integral", "gs"],
+    ap.add_argument("--workload", default="page", choices=["page", "batch", "serve", "integral", "gs", "edge-sweep"],
                     help="page: the 4096x4096 RGB page (default); batch: 256 uneven gray pages; "
                          "serve: Poisson stream of RGB pages through the serving loop")
     ap.add_argument("--case", default=None,
@@ -1059,6 +1092,8 @@ def main():
         return run_serve(args)
     if args.workload == "gs":
         return run_gs(args)
+    if args.workload == "edge-sweep":
+        return run_edge_sweep(args)
     if args.workload == "integral":
         return run_integral(args)
     if args.case:

@@ -290,9 +290,10 @@ BNZ_API int bnz_batch_create(const bnz_page *pages, int n, int use_graph, unsign
 BNZ_API size_t bnz_batch_desc_bytes(int n);
 /* Like bnz_batch_create without a graph and without allocating: the page
  * descriptors go to caller-provided device memory d_desc (128-byte aligned,
- * bnz_batch_desc_bytes(n) bytes) by a copy ordered on `stream`; run the batch
- * on the same stream (or after it).  The batch keeps the host copy until it
- * is destroyed; d_desc must outlive the batch's runs. */
+ * bnz_batch_desc_bytes(n) bytes), written by small kernels on `stream` that
+ * carry them as launch parameters (the call never waits for the stream); run
+ * the batch on the same stream (or after it).  d_desc must outlive the
+ * batch's runs; destroying the batch does not synchronize. */
 BNZ_API int bnz_batch_create_async(const bnz_page *pages, int n, void *d_desc, size_t desc_bytes, void *stream,
                                    unsigned long long *d_stats, bnz_batch **out);
 /* Enqueue the whole batch on `stream` (one graph launch, or one kernel per channel count). */

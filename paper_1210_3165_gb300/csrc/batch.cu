@@ -33,6 +33,24 @@ struct alignas(128) PageDesc {
     int pad;
 };
 
+// Descriptors of an asynchronous batch reach the device as kernel parameters
+// (the launch copies them), not through a copy from pageable host memory: the
+// driver may order such a copy after the stream's earlier work, which would
+// block the calling thread (a serving loop) until the previous step is done.
+constexpr int kDescWords = (int)(sizeof(PageDesc) / 16);
+constexpr int kDescPerPut = 3968 / (int)sizeof(PageDesc); // 4 KB of kernel parameters at most
+static_assert(sizeof(PageDesc) % 16 == 0 && kDescPerPut >= 1, "descriptor upload chunk");
+
+struct DescPut {
+    uint4 w[kDescPerPut * kDescWords];
+};
+
+__global__ void __launch_bounds__(256) put_descs(const __grid_constant__ DescPut src, int words, uint4 *dst)
+{
+    for (int i = threadIdx.x; i < words; i += blockDim.x)
+        dst[i] = src.w[i];
+}
+
 template <int CIN>
 __device__ __forceinline__ void dispatch(int sel, const CUtensorMap *map, const FusedParams &p, const Segment &sg,
                                          uint8_t *smem, uint64_t &phase, uint64_t &ephase, uint64_t &eused,
@@ -138,7 +156,6 @@ struct bnz_batch {
     unsigned long long *stats = nullptr;
     unsigned int *err = nullptr;
     int device = 0;
-    cudaStream_t pending = nullptr; // stream of a stream-ordered descriptor upload
 };
 
 namespace bnz {
@@ -182,8 +199,6 @@ void free_batch(bnz_batch *b)
         cudaGraphExecDestroy(b->exec);
     if (b->graph)
         cudaGraphDestroy(b->graph);
-    if (b->pending) // the host copies may still be the source of a stream-ordered upload
-        cudaStreamSynchronize(b->pending);
     for (Group &g : b->groups)
         if (g.dev && g.owned)
             cudaFree(g.dev);
@@ -351,14 +366,19 @@ int bnz_batch_create_async(const bnz_page *pages, int n, void *d_desc, size_t de
         g.dev = next;
         g.cursor = cursors + gi * (kCursorBytes / sizeof(unsigned long long));
         next += g.host.size();
-        cudaError_t e = cudaMemcpyAsync(g.dev, g.host.data(), g.host.size() * sizeof(PageDesc),
-                                        cudaMemcpyHostToDevice, static_cast<cudaStream_t>(stream));
+        for (size_t i0 = 0; i0 < g.host.size(); i0 += kDescPerPut) {
+            const int m = (int)std::min<size_t>(kDescPerPut, g.host.size() - i0);
+            DescPut put;
+            memcpy(put.w, &g.host[i0], (size_t)m * sizeof(PageDesc));
+            put_descs<<<1, 256, 0, static_cast<cudaStream_t>(stream)>>>(put, m * kDescWords,
+                                                                         reinterpret_cast<uint4 *>(g.dev + i0));
+        }
+        cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) {
             free_batch(b);
             return cuda_fail(e, "batch descriptors");
         }
     }
-    b->pending = static_cast<cudaStream_t>(stream);
     *out = b;
     return BNZ_OK;
 }

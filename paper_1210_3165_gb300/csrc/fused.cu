@@ -318,9 +318,10 @@ int plan_fused(int h, int w, int ch, int W, const bnz_tile *tile, FusedPlan *pl,
     // whole CTAs per strip when every strip gets at least two: the first and
     // last strips get edge_weight/16 times an inner strip's share
     const int S = pl->tiles_x;
+    const int ew = (tile && tile->edge_weight > 0) ? tile->edge_weight : kEdgeWeight;
     pl->n_edge = 0;
+    pl->edge_w = ew;
     if (S >= 2 && G >= 2 * S && rows >= 2) {
-        const int ew = (tile && tile->edge_weight > 0) ? tile->edge_weight : kEdgeWeight;
         if (S == 2) {
             G &= ~1ll;
             pl->n_edge = (int)(G / 2);
@@ -355,6 +356,7 @@ void fill_fused_params(FusedParams *p, const FusedPlan &pl, int h, int w, int W,
     p->ring_rows = pl.ring_rows;
     p->tiles_x = pl.tiles_x;
     p->n_edge = pl.n_edge;
+    p->edge_w = pl.edge_w;
     p->off_ring = pl.off_ring;
     p->off_stage = pl.off_stage;
     p->off_cb = pl.off_cb;

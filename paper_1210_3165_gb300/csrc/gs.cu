@@ -49,7 +49,7 @@ namespace {
 
 constexpr int GT = 256;    // threads of a CTA = output columns of a strip
 constexpr int kPRow = 512; // entries of a prefix row (the span is at most GT + BNZ_MAX_W + 1 <= 512)
-constexpr int kPF = 8;     // entering rows loaded ahead
+constexpr int kPF = 4;     // entering rows loaded ahead
 
 // The lines of a structure, as disjoint pieces where possible (frame sides
 // and, with the frame, the centre row and column stop short of the frame):
@@ -165,7 +165,7 @@ __device__ __forceinline__ uint2 seg(const uint2 *P, int i0, int i1)
 }
 
 template <int CIN, int RULE, int GS>
-__global__ void __launch_bounds__(GT) gs_kernel(const __grid_constant__ GsParams g)
+__global__ void __launch_bounds__(GT, 4) gs_kernel(const __grid_constant__ GsParams g)
 {
     using S = Shape<GS>;
     extern __shared__ __align__(16) uint8_t smem[];
@@ -538,11 +538,12 @@ int launch_gs(const uint8_t *d_src, size_t src_pitch, int h, int w, int ch, int 
         return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(gs kernel)");
     if (occ < 1)
         return fail(BNZ_EINVAL, "reduced-set kernel does not fit an SM (W = %d, %zu bytes of shared memory)", W, smem);
-    // segments: enough CTAs for every SM's resident slots, each at least 64 rows tall
-    // (a segment's W - 1 rows of warm-up only add rows: no row sums, no decisions)
+    // segments: as many CTAs as the SMs hold at once (one wave: a second,
+    // partial wave would double the time), each at least 64 rows tall (a
+    // segment's W - 1 rows of warm-up only add rows: no row sums, no decisions)
     const int strips = (w + GT - 1) / GT;
     const long long target = (long long)sms * occ;
-    int segs = (int)std::min<long long>((target + strips - 1) / strips, (h + 63) / 64);
+    int segs = (int)std::min<long long>(target / strips, (h + 63) / 64);
     segs = std::max(segs, 1);
     g.seg_rows = (h + segs - 1) / segs;
     segs = (h + g.seg_rows - 1) / g.seg_rows;

@@ -42,6 +42,7 @@ struct FusedPlan {
     int tiles_x;    // strips across the image
     int grid;       // persistent CTAs
     int n_edge;     // CTAs on each of the first and last strips (0: one even split of all strip-rows)
+    int edge_w;     // the edge weight used (sixteenths)
     int rows_per_cta;
     uint32_t off_ring, off_stage, off_cb; // column sums: 2 buffers x {c1, c2} x CH rows x RS words
     size_t smem;
@@ -57,6 +58,7 @@ struct FusedParams {
     int TW, CH, NS, NSS, SWP, ring_rows, tiles_x;
     int o4, wq, ngo; // column-sum groups: origin, entering-stream offset, count (see FusedPlan)
     int n_edge;      // CTAs per edge strip, the rest dealt evenly over the inner strips (0: even split)
+    int edge_w;      // cost of a row taking the border path, in sixteenths of an inner row's
     uint32_t off_ring, off_stage, off_cb;
     int packed;     // 1: one bit per pixel
     int vec_ok;     // dst and dst_pitch 16-byte aligned

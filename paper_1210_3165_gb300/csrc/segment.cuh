@@ -154,8 +154,28 @@ __device__ __forceinline__ void cta_range(const FusedParams &p, long long &L0, l
             s = 1 + rem + k2 / q, j = k2 % q, n = q;
         }
     }
-    L0 = (long long)s * nr + (long long)nr * j / n;
-    L1 = (long long)s * nr + (long long)nr * (j + 1) / n;
+    if (s == 0 || s == S - 1 || p.edge_w <= 16) { // every row of an edge strip takes the border path
+        L0 = (long long)s * nr + (long long)nr * j / n;
+        L1 = (long long)s * nr + (long long)nr * (j + 1) / n;
+        return;
+    }
+    // inner strip: the rows whose windows clip at the page's top or bottom also
+    // take the border path and weigh edge_w / 16 as much
+    const int top = min(max(p.r_lo - p.y_lo, 0), nr);
+    const int bot = min(max(p.y_hi - (p.h - p.r_hi), 0), nr - top);
+    const long long ew = p.edge_w, mid = nr - top - bot;
+    const long long tot = (top + bot) * ew + mid * 16;
+    auto row_at = [&](long long c) -> long long { // first row whose cost prefix reaches c
+        if (c <= top * ew)
+            return (c + ew - 1) / ew;
+        c -= top * ew;
+        if (c <= mid * 16)
+            return top + (c + 15) / 16;
+        c -= mid * 16;
+        return top + mid + (c + ew - 1) / ew;
+    };
+    L0 = (long long)s * nr + row_at(tot * j / n);
+    L1 = (long long)s * nr + row_at(tot * (j + 1) / n);
 }
 
 // ---------------------------------------------------------------------------
