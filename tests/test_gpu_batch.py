@@ -121,3 +121,20 @@ def test_autotuner_table_and_lookup(bnz, tmp_path, monkeypatch):
     img = synth.page(700, 1100, 5, synth.DOC, 1)
     got = bnz.binarize(bnz.to_device_pitched(img), 15, "sauvola", 0.5, 128.0, tile=t).cpu().numpy()
     np.testing.assert_array_equal(got, oracle.sauvola(img, 15, 0.5, 128.0)[0])
+
+
+def test_async_batch_many_descriptors(bnz):
+    """More descriptors than one upload kernel carries in its parameters: every page still gets its own."""
+    specs = [(40 + 7 * i, 50 + 11 * i, 1 + 2 * (i % 2), 3 + 2 * (i % 9), "sauvola" if i % 3 else "niblack", False, 0)
+             for i in range(29)]
+    pages, hosts = make_pages(bnz, specs)
+    stream = torch.cuda.Stream()
+    desc = bnz.alloc_scratch(bnz.Batch.desc_bytes(len(pages)))
+    b = bnz.Batch(pages, desc_buffer=desc, stream=stream)
+    b.run(stream)
+    stream.synchronize()
+    for pg, img, (h, w, ch, W, rule, packed, _) in zip(pages, hosts, specs):
+        rid = oracle.SAUVOLA if rule == "sauvola" else oracle.NIBLACK
+        ref, _ = oracle.binarize(img, W, rid, pg["k"], 128.0, threads=NTHREADS, packed=packed)
+        np.testing.assert_array_equal(pg["dst"].cpu().numpy(), ref)
+    b.close()
