@@ -48,8 +48,8 @@ namespace bnz {
 namespace {
 
 constexpr int GT = 256;    // threads of a CTA = output columns of a strip
-constexpr int kPRow = 512; // entries of a prefix row (the span is at most GT + BNZ_MAX_W + 1 <= 512)
-constexpr int kPF = 4;     // entering rows loaded ahead
+constexpr int kPRow = 768; // entries of a prefix row: up to three 256-column parts (span <= 512 + 256)
+constexpr int kPF = 2;     // entering rows loaded ahead
 
 // The lines of a structure, as disjoint pieces where possible (frame sides
 // and, with the frame, the centre row and column stop short of the frame):
@@ -95,24 +95,26 @@ __device__ __forceinline__ int clip_len(int lo, int hi, int n) // |[lo, hi] with
     return max(0, min(hi, n - 1) - max(lo, 0) + 1);
 }
 
+// The raw bytes of one span column of a row (zero outside the page), each in
+// its own register: they are combined only when the row is used, kPF steps
+// later, so the loads stay in flight meanwhile.
 template <int CIN>
-__device__ __forceinline__ uint32_t fetch(const GsParams &g, int row, int col)
+__device__ __forceinline__ void fetch(const GsParams &g, int row, int col, uint32_t (&v)[CIN])
 {
-    if ((unsigned)row >= (unsigned)g.d.h || (unsigned)col >= (unsigned)g.d.w)
-        return 0u;
+    const bool in = (unsigned)row < (unsigned)g.d.h && (unsigned)col < (unsigned)g.d.w;
     const uint8_t *px = g.src + (long long)row * g.src_pitch + (long long)col * CIN;
-    if (CIN == 1)
-        return __ldg(px);
-    return (uint32_t)__ldg(px) | ((uint32_t)__ldg(px + 1) << 8) | ((uint32_t)__ldg(px + 2) << 16);
+#pragma unroll
+    for (int c = 0; c < CIN; ++c)
+        v[c] = in ? (uint32_t)__ldg(px + c) : 0u;
 }
 
+// Eq. 1, integer round-half-up (the same rule as every other kernel)
 template <int CIN>
-__device__ __forceinline__ uint32_t to_gray(uint32_t v)
+__device__ __forceinline__ uint32_t to_gray(const uint32_t (&v)[CIN])
 {
     if (CIN == 1)
-        return v;
-    // Eq. 1, integer round-half-up (the same rule as every other kernel)
-    return (299u * (v & 0xffu) + 587u * ((v >> 8) & 0xffu) + 114u * (v >> 16) + 500u) / 1000u;
+        return v[0];
+    return (299u * v[0] + 587u * v[1 % CIN] + 114u * v[2 % CIN] + 500u) / 1000u;
 }
 
 // Inclusive prefix sums of f and f^2 over one half (256 span columns) of a
@@ -151,7 +153,8 @@ __device__ __forceinline__ void prefix_half(const uint8_t *row, int sp, uint2 *P
         dst[i] = make_uint4(e1 + s1[2 * i], e2 + s2[2 * i], e1 + s1[2 * i + 1], e2 + s2[2 * i + 1]);
 }
 
-// Sums over span columns (i0, i1] of a prefix row written in two halves.
+// Sums over span columns (i0, i1] of a prefix row written in 256-column
+// parts, each summed on its own: the totals of the parts between are added.
 __device__ __forceinline__ uint2 seg(const uint2 *P, int i0, int i1)
 {
     const uint2 hi = P[i1], lo = P[i0];
@@ -161,17 +164,27 @@ __device__ __forceinline__ uint2 seg(const uint2 *P, int i0, int i1)
         r.x += t.x;
         r.y += t.y;
     }
+    if (i1 >= 512 && i0 < 512) {
+        const uint2 t = P[511];
+        r.x += t.x;
+        r.y += t.y;
+    }
     return r;
 }
 
-template <int CIN, int RULE, int GS>
-__global__ void __launch_bounds__(GT, 4) gs_kernel(const __grid_constant__ GsParams g)
+// CPT output columns per thread (strip = CPT x 256 columns): column c of the
+// strip is handled by thread c mod 256.
+template <int CIN, int RULE, int GS, int CPT>
+__global__ void __launch_bounds__(GT, CPT == 1 ? 4 : 3) gs_kernel(const __grid_constant__ GsParams g)
 {
     using S = Shape<GS>;
+    constexpr int TWS = CPT * GT;  // strip width
+    constexpr int NQ = CPT + 1;    // span columns per thread (the span is at most TWS + 256)
+    constexpr int NPART = CPT + 1; // 256-column parts of a prefix row
     extern __shared__ __align__(16) uint8_t smem[];
     const FusedParams &p = g.d;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int x0 = blockIdx.x * GT, x = x0 + t;
+    const int x0 = blockIdx.x * TWS;
     const int ya = blockIdx.y * g.seg_rows;
     const int yb = min(p.h, ya + g.seg_rows);
     const int a = g.a, b = g.b, mm = g.mm, W = p.W, nr = g.nr, span = g.span, sp = g.sp;
@@ -179,20 +192,20 @@ __global__ void __launch_bounds__(GT, 4) gs_kernel(const __grid_constant__ GsPar
     uint8_t *ring = smem;
     uint2 *V = reinterpret_cast<uint2 *>(smem + g.off_v); // column sums of every span column (W or W - 2 rows)
     uint2 *Dp = reinterpret_cast<uint2 *>(smem + g.off_d);
-    uint2 *Dm = Dp + GT;
+    uint2 *Dm = Dp + TWS;
     uint2 *P = reinterpret_cast<uint2 *>(smem + g.off_p);
 
     for (int i = t; i < nr * sp / 16; i += GT)
         reinterpret_cast<uint4 *>(ring)[i] = make_uint4(0u, 0u, 0u, 0u);
-    Dp[t] = make_uint2(0u, 0u);
-    Dm[t] = make_uint2(0u, 0u);
-    uint2 va = make_uint2(0u, 0u), vb = make_uint2(0u, 0u); // column sums of span columns t, t + GT
-
-    // per-column constants of the output pixel
-    const bool xin = x < p.w;
-    const bool x_inner = x + a >= 0 && x + b < p.w;
-    const int cnt_h = clip_len(x + a, x + b, p.w), cnt_hc = clip_len(x + a + 1, x + b - 1, p.w);
-    const bool cin_a = (unsigned)(x + a) < (unsigned)p.w, cin_b = (unsigned)(x + b) < (unsigned)p.w;
+#pragma unroll
+    for (int h = 0; h < CPT; ++h) {
+        Dp[t + h * GT] = make_uint2(0u, 0u);
+        Dm[t + h * GT] = make_uint2(0u, 0u);
+    }
+    uint2 vs[NQ]; // column sums of span columns t + q * 256
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+        vs[q] = make_uint2(0u, 0u);
 
     const int y_first = ya - (W - 1); // entering row ya + a: the first row of the first output's window
     int es = (y_first + b) % nr;
@@ -200,12 +213,12 @@ __global__ void __launch_bounds__(GT, 4) gs_kernel(const __grid_constant__ GsPar
         es += nr;
     // the entering rows of the next kPF steps are in flight in registers (a
     // step is far shorter than a DRAM round trip)
-    uint32_t r0[kPF], r1[kPF];
+    uint32_t rr[kPF][NQ][CIN];
 #pragma unroll
-    for (int i = 0; i < kPF; ++i) {
-        r0[i] = fetch<CIN>(g, y_first + b + i, cs + t);
-        r1[i] = (t + GT < span) ? fetch<CIN>(g, y_first + b + i, cs + t + GT) : 0u;
-    }
+    for (int i = 0; i < kPF; ++i)
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+            fetch<CIN>(g, y_first + b + i, t + q * GT < span ? cs + t + q * GT : -1, rr[i][q]);
     uint32_t nfb = 0, nties = 0;
     __syncthreads();
 
@@ -217,39 +230,49 @@ __global__ void __launch_bounds__(GT, 4) gs_kernel(const __grid_constant__ GsPar
             break;
         const int e = y + b; // entering row
         uint8_t *re = ring + es * sp;
-        re[t] = (uint8_t)to_gray<CIN>(r0[i]);
-        if (t + GT < span)
-            re[t + GT] = (uint8_t)to_gray<CIN>(r1[i]);
-        if (y + kPF < yb) { // the entering row of step y + kPF
-            r0[i] = fetch<CIN>(g, e + kPF, cs + t);
-            if (t + GT < span)
-                r1[i] = fetch<CIN>(g, e + kPF, cs + t + GT);
-        }
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+            if (t + q * GT < span) {
+                re[t + q * GT] = (uint8_t)to_gray<CIN>(rr[i][q]);
+                if (y + kPF < yb) // the entering row of step y + kPF
+                    fetch<CIN>(g, e + kPF, cs + t + q * GT, rr[i][q]);
+            }
         __syncthreads();
 
         if (S::VFULL || S::VCUT) { // rows [y + a, y + b] (entering e, leaving e - W) or (y + a, y + b)
             const uint8_t *ri = S::VFULL ? re : ring + back(es, 1, nr) * sp;
             const uint8_t *ro = ring + back(es, S::VFULL ? W : W - 1, nr) * sp;
-            const uint32_t u = ri[t], v = ro[t];
-            va.x += u - v;
-            va.y += u * u - v * v;
-            V[t] = va;
-            if (t + GT < span) {
-                const uint32_t u2 = ri[t + GT], v2 = ro[t + GT];
-                vb.x += u2 - v2;
-                vb.y += u2 * u2 - v2 * v2;
-                V[t + GT] = vb;
-            }
+#pragma unroll
+            for (int q = 0; q < NQ; ++q)
+                if (t + q * GT < span) {
+                    const uint32_t u = ri[t + q * GT], v = ro[t + q * GT];
+                    vs[q].x += u - v;
+                    vs[q].y += u * u - v * v;
+                    V[t + q * GT] = vs[q];
+                }
         }
         if (S::DIAG) {
             const uint8_t *rl = ring + back(es, W, nr) * sp; // row y + a - 1
-            const int s = (t - y) & (GT - 1);
-            if (t != 0) { // continue the diagonal of (y - 1, x - 1)
-                const uint32_t u = re[t + W], v = rl[t];
-                uint2 d = Dp[s];
-                d.x += u - v;
-                d.y += u * u - v * v;
-                Dp[s] = d;
+            const uint8_t *rdl = ring + back(es, b + mm + 1, nr) * sp;
+#pragma unroll
+            for (int h = 0; h < CPT; ++h) {
+                const int c = t + h * GT;
+                if (c != 0) { // continue the diagonal of (y - 1, x - 1)
+                    const int s = (c - y) & (TWS - 1);
+                    const uint32_t u = re[c + W], v = rl[c];
+                    uint2 d = Dp[s];
+                    d.x += u - v;
+                    d.y += u * u - v * v;
+                    Dp[s] = d;
+                }
+                if (c != TWS - 1) { // continue the anti-diagonal of (y - 1, x + 1)
+                    const int sm = (c + y) & (TWS - 1);
+                    const uint32_t u = re[c - mm - a + 1], v = rdl[c + W + 1];
+                    uint2 d = Dm[sm];
+                    d.x += u - v;
+                    d.y += u * u - v * v;
+                    Dm[sm] = d;
+                }
             }
             if (warp == 0) { // the diagonal entering at the strip's first column: sum it afresh
                 uint32_t s1 = 0u, s2 = 0u;
@@ -261,116 +284,119 @@ __global__ void __launch_bounds__(GT, 4) gs_kernel(const __grid_constant__ GsPar
                 s1 = __reduce_add_sync(0xffffffffu, s1);
                 s2 = __reduce_add_sync(0xffffffffu, s2);
                 if (t == 0) // the slot of that column
-                    Dp[s] = make_uint2(s1, s2);
-            }
-            const int sm = (t + y) & (GT - 1);
-            if (t != GT - 1) { // continue the anti-diagonal of (y - 1, x + 1)
-                const uint8_t *rdl = ring + back(es, b + mm + 1, nr) * sp;
-                const uint32_t u = re[t - mm - a + 1], v = rdl[t + W + 1];
-                uint2 d = Dm[sm];
-                d.x += u - v;
-                d.y += u * u - v * v;
-                Dm[sm] = d;
+                    Dp[(0 - y) & (TWS - 1)] = make_uint2(s1, s2);
             }
             if (warp == GT / 32 - 1) { // the anti-diagonal entering at the strip's last column
                 uint32_t s1 = 0u, s2 = 0u;
-                for (int j = lane; j <= 2 * mm; j += 32) { // d = j - mm: row y + d, span column GT - d - a
+                for (int j = lane; j <= 2 * mm; j += 32) { // d = j - mm: row y + d, span column TWS - d - a
                     const int d = j - mm;
-                    const uint32_t f = ring[back(es, b - d, nr) * sp + GT - d - a];
+                    const uint32_t f = ring[back(es, b - d, nr) * sp + TWS - d - a];
                     s1 += f;
                     s2 += f * f;
                 }
                 s1 = __reduce_add_sync(0xffffffffu, s1);
                 s2 = __reduce_add_sync(0xffffffffu, s2);
                 if (t == GT - 1) // the slot of that column
-                    Dm[sm] = make_uint2(s1, s2);
+                    Dm[(TWS - 1 + y) & (TWS - 1)] = make_uint2(s1, s2);
             }
         }
         const bool out_row = y >= ya;
-        if (S::NH > 0 && out_row && warp < 2 * S::NH) {
-            // prefix rows, two warps each: centre row y (back b), frame top y + a (back W - 1), bottom e (back 0)
-            const int j = warp >> 1;
-            const int kb = S::HC ? (j == 0 ? b : (j == 1 ? W - 1 : 0)) : (j == 0 ? W - 1 : 0);
-            prefix_half(ring + back(es, kb, nr) * sp, sp, P + j * kPRow, warp & 1, lane);
+        if (S::NH > 0 && out_row) {
+            // prefix rows in 256-column parts, one warp per part: centre row y (back b), frame top y + a
+            // (back W - 1), frame bottom e (back 0)
+            for (int task = warp; task < S::NH * NPART; task += GT / 32) {
+                const int j = task / NPART;
+                const int kb = S::HC ? (j == 0 ? b : (j == 1 ? W - 1 : 0)) : (j == 0 ? W - 1 : 0);
+                prefix_half(ring + back(es, kb, nr) * sp, sp, P + j * kPRow, task - j * NPART, lane);
+            }
         }
         __syncthreads();
 
-        if (out_row && xin) {
-            const uint32_t f = ring[back(es, b, nr) * sp + t - a + 1];
-            uint32_t S1 = 0u, S2 = 0u;
-            int pr = 0;
-            if (S::HC) { // span columns of x + a .. x + b are t + 1 .. t + W
-                const uint2 h = S::HC_CUT ? seg(P, t + 1, t + W - 1) : seg(P, t, t + W);
-                S1 += h.x;
-                S2 += h.y;
-                pr = 1;
-            }
-            if (S::VFULL || S::HC_CUT) { // centre column
-                const uint2 v = V[t - a + 1];
-                S1 += v.x;
-                S2 += v.y;
-            }
-            if (S::FRAME) {
-                const uint2 top = seg(P + pr * kPRow, t, t + W), bot = seg(P + (pr + 1) * kPRow, t, t + W);
-                const uint2 vl = V[t + 1], vr = V[t + W];
-                S1 += top.x + bot.x + vl.x + vr.x;
-                S2 += top.y + bot.y + vl.y + vr.y;
-            }
-            if (S::DIAG) {
-                const uint2 d = Dp[(t - y) & (GT - 1)], m = Dm[(t + y) & (GT - 1)];
-                S1 += d.x + m.x;
-                S2 += d.y + m.y;
-            }
-            S1 -= S::CENTRE * f;
-            S2 -= S::CENTRE * f * f;
-            uint2 ends = make_uint2(0u, 0u);
-            int nends = 0;
-            if (S::ENDS) { // the diagonals' end points, also on the frame
-                const uint2 *Pt = P + pr * kPRow, *Pb = P + (pr + 1) * kPRow;
-                const uint2 e0 = seg(Pt, t, t + 1);          // (a, a)
-                const uint2 e1 = seg(Pb, t + W - 1, t + W);  // (b, b)
-                uint2 e2, e3;
-                if (mm == b && a == -b) {                    // odd W: (a, b) and (b, a)
-                    e2 = seg(Pt, t + W - 1, t + W);
-                    e3 = seg(Pb, t, t + 1);
-                } else {                                     // even W: (-b, b) on column b, (b, -b) on row b
-                    const uint32_t v = ring[back(es, 2 * b, nr) * sp + t + W];
-                    e2 = make_uint2(v, v * v);
-                    e3 = seg(Pb, t + 1, t + 2);
+        if (out_row) {
+            const uint8_t *rc = ring + back(es, b, nr) * sp; // row y
+            const bool y_inner = y + a >= 0 && y + b < p.h;
+            const bool ra = (unsigned)(y + a) < (unsigned)p.h, rb = (unsigned)(y + b) < (unsigned)p.h;
+            const int cnt_v = clip_len(y + a, y + b, p.h), cnt_vc = clip_len(y + a + 1, y + b - 1, p.h);
+#pragma unroll
+            for (int h = 0; h < CPT; ++h) {
+                const int c = t + h * GT, x = x0 + c;
+                if (x >= p.w)
+                    break;
+                const uint32_t f = rc[c - a + 1];
+                uint32_t S1 = 0u, S2 = 0u;
+                int pr = 0;
+                if (S::HC) { // span columns of x + a .. x + b are c + 1 .. c + W
+                    const uint2 hs = S::HC_CUT ? seg(P, c + 1, c + W - 1) : seg(P, c, c + W);
+                    S1 += hs.x;
+                    S2 += hs.y;
+                    pr = 1;
                 }
-                ends = make_uint2(e0.x + e1.x + e2.x + e3.x, e0.y + e1.y + e2.y + e3.y);
-                S1 -= ends.x;
-                S2 -= ends.y;
-                if (!(x_inner && y + a >= 0 && y + b < p.h)) {
-                    const int ye = mm == b && a == -b ? a : -b, xe = -ye; // the anti-diagonal's upper end
-                    nends = ((unsigned)(y + a) < (unsigned)p.h && cin_a) + ((unsigned)(y + b) < (unsigned)p.h && cin_b) +
-                            ((unsigned)(y + ye) < (unsigned)p.h && (unsigned)(x + xe) < (unsigned)p.w) +
-                            ((unsigned)(y - ye) < (unsigned)p.h && (unsigned)(x - xe) < (unsigned)p.w);
+                if (S::VFULL || S::HC_CUT) { // centre column
+                    const uint2 v = V[c - a + 1];
+                    S1 += v.x;
+                    S2 += v.y;
                 }
-            }
-            uint32_t n;
-            if (x_inner && y + a >= 0 && y + b < p.h) {
-                n = p.nW; // the whole structure inside the page: |S'|
-            } else {
-                const int cnt_v = clip_len(y + a, y + b, p.h), cnt_vc = clip_len(y + a + 1, y + b - 1, p.h);
-                int c = 0;
-                if (S::HC)
-                    c += S::HC_CUT ? cnt_hc : cnt_h;
-                if (S::VFULL)
-                    c += cnt_v;
-                if (S::HC_CUT)
-                    c += cnt_vc;
-                if (S::FRAME)
-                    c += ((unsigned)(y + a) < (unsigned)p.h ? cnt_h : 0) + ((unsigned)(y + b) < (unsigned)p.h ? cnt_h : 0) +
-                         (cin_a ? cnt_vc : 0) + (cin_b ? cnt_vc : 0);
+                if (S::FRAME) {
+                    const uint2 top = seg(P + pr * kPRow, c, c + W), bot = seg(P + (pr + 1) * kPRow, c, c + W);
+                    const uint2 vl = V[c + 1], vr = V[c + W];
+                    S1 += top.x + bot.x + vl.x + vr.x;
+                    S2 += top.y + bot.y + vl.y + vr.y;
+                }
                 if (S::DIAG) {
-                    c += max(0, min(b, min(p.h - 1 - y, p.w - 1 - x)) - max(a, max(-y, -x)) + 1);
-                    c += max(0, min(mm, min(p.h - 1 - y, x)) - max(-mm, max(-y, x - (p.w - 1))) + 1);
+                    const uint2 d = Dp[(c - y) & (TWS - 1)], m = Dm[(c + y) & (TWS - 1)];
+                    S1 += d.x + m.x;
+                    S2 += d.y + m.y;
                 }
-                n = (uint32_t)(c - S::CENTRE - nends);
+                S1 -= S::CENTRE * f;
+                S2 -= S::CENTRE * f * f;
+                const bool x_inner = x + a >= 0 && x + b < p.w;
+                const bool cin_a = (unsigned)(x + a) < (unsigned)p.w, cin_b = (unsigned)(x + b) < (unsigned)p.w;
+                int nends = 0;
+                if (S::ENDS) { // the diagonals' end points, also on the frame
+                    const uint2 *Pt = P + pr * kPRow, *Pb = P + (pr + 1) * kPRow;
+                    const uint2 e0 = seg(Pt, c, c + 1);          // (a, a)
+                    const uint2 e1 = seg(Pb, c + W - 1, c + W);  // (b, b)
+                    uint2 e2, e3;
+                    if (mm == b && a == -b) {                    // odd W: (a, b) and (b, a)
+                        e2 = seg(Pt, c + W - 1, c + W);
+                        e3 = seg(Pb, c, c + 1);
+                    } else {                                     // even W: (-b, b) on column b, (b, -b) on row b
+                        const uint32_t v = ring[back(es, 2 * b, nr) * sp + c + W];
+                        e2 = make_uint2(v, v * v);
+                        e3 = seg(Pb, c + 1, c + 2);
+                    }
+                    S1 -= e0.x + e1.x + e2.x + e3.x;
+                    S2 -= e0.y + e1.y + e2.y + e3.y;
+                    if (!(x_inner && y_inner)) {
+                        const int ye = mm == b && a == -b ? a : -b, xe = -ye; // the anti-diagonal's upper end
+                        nends = (ra && cin_a) + (rb && cin_b) +
+                                ((unsigned)(y + ye) < (unsigned)p.h && (unsigned)(x + xe) < (unsigned)p.w) +
+                                ((unsigned)(y - ye) < (unsigned)p.h && (unsigned)(x - xe) < (unsigned)p.w);
+                    }
+                }
+                uint32_t n;
+                if (x_inner && y_inner) {
+                    n = p.nW; // the whole structure inside the page: |S'|
+                } else {
+                    const int cnt_h = clip_len(x + a, x + b, p.w), cnt_hc = clip_len(x + a + 1, x + b - 1, p.w);
+                    int cnt = 0;
+                    if (S::HC)
+                        cnt += S::HC_CUT ? cnt_hc : cnt_h;
+                    if (S::VFULL)
+                        cnt += cnt_v;
+                    if (S::HC_CUT)
+                        cnt += cnt_vc;
+                    if (S::FRAME)
+                        cnt += (ra ? cnt_h : 0) + (rb ? cnt_h : 0) + (cin_a ? cnt_vc : 0) + (cin_b ? cnt_vc : 0);
+                    if (S::DIAG) {
+                        cnt += max(0, min(b, min(p.h - 1 - y, p.w - 1 - x)) - max(a, max(-y, -x)) + 1);
+                        cnt += max(0, min(mm, min(p.h - 1 - y, x)) - max(-mm, max(-y, x - (p.w - 1))) + 1);
+                    }
+                    n = (uint32_t)(cnt - S::CENTRE - nends);
+                }
+                const uint32_t r = decide_pixel<RULE>(f, n, S1, S2, p, nfb, nties);
+                p.dst[(long long)y * p.dst_pitch + x] = (uint8_t)r;
             }
-            const uint32_t r = decide_pixel<RULE>(f, n, S1, S2, p, nfb, nties);
-            p.dst[(long long)y * p.dst_pitch + x] = (uint8_t)r;
         }
         es = es + 1 == nr ? 0 : es + 1;
     }
@@ -444,24 +470,44 @@ int structure_size(int gs, int W)
 
 size_t round16(size_t v) { return (v + 15) / 16 * 16; }
 
-template <int CIN, int RULE>
+template <int CIN, int RULE, int CPT>
 const void *kernel_fn(int gs)
 {
     switch (gs) {
-    case BNZ_GS_CROSS: return reinterpret_cast<const void *>(&gs_kernel<CIN, RULE, BNZ_GS_CROSS>);
-    case BNZ_GS_DIAGONALS: return reinterpret_cast<const void *>(&gs_kernel<CIN, RULE, BNZ_GS_DIAGONALS>);
-    case BNZ_GS_STAR: return reinterpret_cast<const void *>(&gs_kernel<CIN, RULE, BNZ_GS_STAR>);
-    case BNZ_GS_FRAME: return reinterpret_cast<const void *>(&gs_kernel<CIN, RULE, BNZ_GS_FRAME>);
-    case BNZ_GS_FRAME_CROSS: return reinterpret_cast<const void *>(&gs_kernel<CIN, RULE, BNZ_GS_FRAME_CROSS>);
-    default: return reinterpret_cast<const void *>(&gs_kernel<CIN, RULE, BNZ_GS_FRAME_DIAGONALS>);
+    case BNZ_GS_CROSS: return reinterpret_cast<const void *>(&gs_kernel<CIN, RULE, BNZ_GS_CROSS, CPT>);
+    case BNZ_GS_DIAGONALS: return reinterpret_cast<const void *>(&gs_kernel<CIN, RULE, BNZ_GS_DIAGONALS, CPT>);
+    case BNZ_GS_STAR: return reinterpret_cast<const void *>(&gs_kernel<CIN, RULE, BNZ_GS_STAR, CPT>);
+    case BNZ_GS_FRAME: return reinterpret_cast<const void *>(&gs_kernel<CIN, RULE, BNZ_GS_FRAME, CPT>);
+    case BNZ_GS_FRAME_CROSS: return reinterpret_cast<const void *>(&gs_kernel<CIN, RULE, BNZ_GS_FRAME_CROSS, CPT>);
+    default: return reinterpret_cast<const void *>(&gs_kernel<CIN, RULE, BNZ_GS_FRAME_DIAGONALS, CPT>);
     }
 }
 
-const void *kernel_for(int ch, int rule, int gs)
+template <int CPT>
+const void *kernel_cpt(int ch, int rule, int gs)
 {
     if (ch == 1)
-        return rule == BNZ_SAUVOLA ? kernel_fn<1, BNZ_SAUVOLA>(gs) : kernel_fn<1, BNZ_NIBLACK>(gs);
-    return rule == BNZ_SAUVOLA ? kernel_fn<3, BNZ_SAUVOLA>(gs) : kernel_fn<3, BNZ_NIBLACK>(gs);
+        return rule == BNZ_SAUVOLA ? kernel_fn<1, BNZ_SAUVOLA, CPT>(gs) : kernel_fn<1, BNZ_NIBLACK, CPT>(gs);
+    return rule == BNZ_SAUVOLA ? kernel_fn<3, BNZ_SAUVOLA, CPT>(gs) : kernel_fn<3, BNZ_NIBLACK, CPT>(gs);
+}
+
+const void *kernel_for(int ch, int rule, int gs, int cpt)
+{
+    return cpt == 2 ? kernel_cpt<2>(ch, rule, gs) : kernel_cpt<1>(ch, rule, gs);
+}
+
+// Two output columns per thread (512-column strips) halve the per-step work
+// that does not depend on the column (the barriers, the ring and slot
+// bookkeeping, the warp sums of the diagonals entering the strip); measured on
+// 4096^2 RGB pages it pays for the structures with diagonals up to W = 128
+// (15-25 % faster) and not for the others (0-4 % slower), whose wider span
+// costs shared memory that 256-column strips keep for more CTAs.
+constexpr int kCpt2MaxW = 128;
+
+int columns_per_thread(int gs, int W)
+{
+    const bool diag = gs == BNZ_GS_DIAGONALS || gs == BNZ_GS_STAR || gs == BNZ_GS_FRAME_DIAGONALS;
+    return diag && W <= kCpt2MaxW ? 2 : 1;
 }
 
 std::once_flag g_attr_once[64];
@@ -475,12 +521,13 @@ int set_attributes(int dev)
         int rc = BNZ_OK;
         for (int ch : {1, 3})
             for (int rule : {BNZ_SAUVOLA, BNZ_NIBLACK})
-                for (int gs = BNZ_GS_CROSS; gs <= BNZ_GS_FRAME_DIAGONALS && rc == BNZ_OK; ++gs) {
-                    cudaError_t e = cudaFuncSetAttribute(kernel_for(ch, rule, gs),
-                                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-                    if (e != cudaSuccess)
-                        rc = cuda_fail(e, "cudaFuncSetAttribute(gs kernel)");
-                }
+                for (int gs = BNZ_GS_CROSS; gs <= BNZ_GS_FRAME_DIAGONALS; ++gs)
+                    for (int cpt = 1; cpt <= 2 && rc == BNZ_OK; ++cpt) {
+                        cudaError_t e = cudaFuncSetAttribute(kernel_for(ch, rule, gs, cpt),
+                                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+                        if (e != cudaSuccess)
+                            rc = cuda_fail(e, "cudaFuncSetAttribute(gs kernel)");
+                    }
         g_attr_rc[dev] = rc;
     });
     return g_attr_rc[dev];
@@ -511,14 +558,16 @@ int launch_gs(const uint8_t *d_src, size_t src_pitch, int h, int w, int ch, int 
     g.d.stats = d_stats;
     g.src = d_src;
     g.src_pitch = (long long)src_pitch;
-    g.span = GT + W + 1;
+    const int cpt = columns_per_thread(gs, W);
+    const int tws = cpt * GT;
+    g.span = tws + W + 1;
     g.sp = (int)round16((size_t)g.span);
     g.nr = W + 1;
     size_t off = round16((size_t)g.nr * g.sp);
     g.off_v = (uint32_t)off;
     off = round16(off + (size_t)g.span * sizeof(uint2));
     g.off_d = (uint32_t)off;
-    off += 2 * GT * sizeof(uint2);
+    off += 2 * (size_t)tws * sizeof(uint2);
     g.off_p = (uint32_t)off;
     off += (size_t)std::max(nh, 1) * kPRow * sizeof(uint2);
     const size_t smem = off;
@@ -532,7 +581,7 @@ int launch_gs(const uint8_t *d_src, size_t src_pitch, int h, int w, int ch, int 
     rc = set_attributes(dev);
     if (rc != BNZ_OK)
         return rc;
-    const void *fn = kernel_for(ch, rule, gs);
+    const void *fn = kernel_for(ch, rule, gs, cpt);
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, GT, smem);
     if (e != cudaSuccess)
         return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(gs kernel)");
@@ -541,7 +590,7 @@ int launch_gs(const uint8_t *d_src, size_t src_pitch, int h, int w, int ch, int 
     // segments: as many CTAs as the SMs hold at once (one wave: a second,
     // partial wave would double the time), each at least 64 rows tall (a
     // segment's W - 1 rows of warm-up only add rows: no row sums, no decisions)
-    const int strips = (w + GT - 1) / GT;
+    const int strips = (w + tws - 1) / tws;
     const long long target = (long long)sms * occ;
     int segs = (int)std::min<long long>(target / strips, (h + 63) / 64);
     segs = std::max(segs, 1);
