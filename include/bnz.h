@@ -39,14 +39,15 @@
  *     return BNZ_ENODEV.
  *   - Statistics (optional, `d_stats`): device pointer to 4 unsigned 64-bit
  *     counters that the kernels add to (the caller zeroes them):
- *       [0] pixels re-evaluated in fp64 (inside the fp32 margin),
+ *       [0] pixels re-evaluated past the fp32 filter (inside its proven
+ *           margin: double-float, then the fp64 definition near a tie),
  *       [1] ties: pixels with |f - t| < 1e-9,
  *       [2] bounded waits that timed out: a CTA that gives up writes no output
  *           of its part of the page.  The synchronous host-pointer calls
  *           return BNZ_ETIMEOUT then; asynchronous callers read this counter;
  *           the serving engine fails the requests of such a step with
  *           BNZ_ETIMEOUT,
- *       [3] reserved, 0.
+ *       [3] bnz_dual_dev: ties of the Niblack mask; 0 for the other calls.
  */
 #ifndef BNZ_H
 #define BNZ_H
