@@ -399,6 +399,7 @@ def run_ours(args):
         torch.cuda.empty_cache()
         result["config1"] = config1_latency(bnz, dev)
         result["config3"] = config3_large(bnz, dev)
+        result["out_of_core"] = out_of_core(bnz)
         result["batch"] = batch_summary(bnz, dev)
         result["serve"] = serve_summary(bnz, args)
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -583,6 +584,46 @@ def config3_large(bnz, dev):
                        "fused_speedup": round(ms_i / ms_f, 2)}
     del scratch, src, out
     torch.cuda.empty_cache()
+    return res
+
+
+def out_of_core(bnz):
+    """The 16384x16384 gray page (Sauvola W=101 k=0.34 R=128) from pinned host memory to a pinned host mask:
+    the in-core host call (bnz_sauvola: page and mask in device memory, 4 overlapped row bands) against the
+    out-of-core call (bnz_binarize_window) through device windows of 1/4 and 1/16 of the page + mask bytes.
+    Copies inside the timed region (the host link bounds both: 268 MB up, 268 MB down)."""
+    import torch
+    import synth
+    h = w = 16384
+    src = torch.empty((h, w), dtype=torch.uint8, pin_memory=True)
+    synth.page(h, w, 3, synth.VIGNETTE, 1, out=src.numpy())
+    dst = torch.empty((h, w), dtype=torch.uint8, pin_memory=True)
+    lib = bnz.load()
+    sp, dp = src.numpy(), dst.numpy()
+
+    def timed(fn, reps=3):
+        fn()
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            fn()
+            ts.append(time.perf_counter() - t0)
+        return statistics.median(ts)
+
+    def check(rc):
+        if rc != 0:
+            raise RuntimeError(bnz.bnz_last_error())
+    res = {"workload": "16384x16384 gray page, Sauvola W=101 k=0.34 R=128, pinned host page in, pinned host mask out",
+           "h2d_bytes_per_call": h * w, "d2h_bytes_per_call": h * w}
+    t = timed(lambda: check(lib.bnz_sauvola(sp.ctypes.data, h, w, 1, 101, 0.34, 128.0, dp.ctypes.data)))
+    res["in_core"] = {"ms": round(t * 1e3, 2), "Mpixel/s": round(h * w / t / 1e6, 1), "device_bytes": 2 * h * w}
+    ref = dp.copy()
+    for frac in (4, 16):
+        win = 2 * h * w // frac
+        t = timed(lambda: check(lib.bnz_binarize_window(sp.ctypes.data, h, w, 1, 101, bnz.BNZ_SAUVOLA, 0.34, 128.0,
+                                                        dp.ctypes.data, win)))
+        res[f"window_1_{frac}"] = {"ms": round(t * 1e3, 2), "Mpixel/s": round(h * w / t / 1e6, 1), "window_bytes": win,
+                                   "same_mask_as_in_core": bool((dp == ref).all())}
     return res
 
 

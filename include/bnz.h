@@ -122,8 +122,9 @@ BNZ_API int bnz_niblack(const uint8_t *src, int height, int width, int channels,
 /* One page, several settings: binarizes the host page src (as bnz_sauvola)
  * once for every entry of runs, each with its own rule (BNZ_SAUVOLA or
  * BNZ_NIBLACK; R ignored for Niblack), W, k and host output dst (height*width
- * bytes, {0,255}).  The page is copied to the device once, in the row bands
- * bnz_host_bands gives for the largest W; every band's kernels run as soon as
+ * bytes, {0,255}).  The page is copied to the device once, in as many row
+ * bands as bnz_host_bands gives for the largest W, of equal height (several
+ * masks per band make the downloads dominate); every band's kernels run as soon as
  * the rows their windows reach are up, and each mask band comes back while
  * later bands upload and compute.  Each dst equals what bnz_sauvola /
  * bnz_niblack writes for that setting.  1 <= nruns <= 1024.  Blocks until
