@@ -110,9 +110,10 @@ typedef struct {
  * Page-locked host buffers copy fastest.  Pages of a megapixel or more are
  * processed in up to 4 row bands whose uploads, kernels and downloads overlap
  * on the calling thread's library streams; the result is the same as in one
- * piece.  A page whose input and mask would take more than half of the free
- * device memory streams through bnz_binarize_window with that half as the
- * window.  Thread-safe: every calling thread has its own streams and buffers. */
+ * piece.  A page whose input and mask take 256 MiB or more streams through
+ * bnz_binarize_window with a quarter of those bytes as the window (more,
+ * smaller bands overlap the copies better), and one that would take more than
+ * half of the free device memory with that half as the window.  Thread-safe: every calling thread has its own streams and buffers. */
 BNZ_API int bnz_sauvola(const uint8_t *src, int height, int width, int channels, int W, double k, double R,
                 uint8_t *dst);
 

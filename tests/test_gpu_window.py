@@ -57,3 +57,13 @@ def test_window_too_small(bnz):
     img = synth.page(100, 100, 1, synth.DOC, 1)
     with pytest.raises(bnz.BnzError, match="too small"):
         bnz.binarize_window(img, 31, window_bytes=3 * slot_bytes(7, 31, 100, 1))
+
+
+def test_large_page_host_call_streams_through_slots(bnz):
+    """A page of 256 MiB or more (with its mask) goes through the band slots in bnz_sauvola: oracle-exact."""
+    img = synth.page(16384, 8192, 3, synth.VIGNETTE, 1)    # 128 MiB page + 128 MiB mask
+    ref, _ = oracle.binarize(img, 101, oracle.SAUVOLA, 0.34, 128.0, threads=NTHREADS)
+    got = bnz.bnz_sauvola(img, 101, 0.34, 128.0)
+    if not np.array_equal(got, ref):
+        bad = np.argwhere(got != ref)
+        raise AssertionError(f"{len(bad)} mismatches, first at {tuple(bad[0])}")
