@@ -691,12 +691,11 @@ def serve_summary(bnz, args):
         reqs = serve_requests(n, 5, cvs)
         res = {}
         for name, mk in arms.items():
-            serve_once(mk, reqs[:32], None)
-            caps = sorted(serve_once(mk, reqs, None)["pages_per_s"] for _ in range(3))
+            caps = sorted(serve_once(mk, reqs, None, warm=reqs[:48])["pages_per_s"] for _ in range(3))
             res[name] = {"capacity_pages_per_s": round(caps[1], 1), "capacity_runs": [round(c, 1) for c in caps]}
         load = 0.8 * res["batched"]["capacity_pages_per_s"]
         for name, mk in arms.items():
-            st = serve_once(mk, reqs, load)
+            st = serve_once(mk, reqs, load, warm=reqs[:48])
             res[name].update({"offered_pages_per_s": round(load, 1), "pages_per_s": round(st["pages_per_s"], 1),
                               "p50_ms": round(st["p50_ms"], 3), "p99_ms": round(st["p99_ms"], 3)})
         out[mode] = res
@@ -928,10 +927,26 @@ def serve_requests(n, seed, canvases):
     return out
 
 
-def serve_once(make_server, reqs, rate):
-    """Replay `reqs` through a fresh server (rate None: all at once, closed loop); pages/s and latency stats."""
+def serve_once(make_server, reqs, rate, warm=()):
+    """Replay `reqs` through a fresh server (rate None: all at once, closed loop); pages/s and latency stats.
+    `warm` requests go through the same server first (closed loop, waited for, not counted): the measured trace
+    then meets a running server, as in service, not one in its first milliseconds."""
     from paper_1210_3165_gb300.serve import Request
     srv = make_server()
+    base = {}
+    if warm:
+        futs = []
+        for tr, img in warm:
+            r = Request(image=img, W=tr["W"], rule=tr["rule"], k=tr["k"], R=tr["R"])
+            srv.submit(r)
+            futs.append(r.future)
+        for f in futs:
+            f.result()
+        futs = r = None  # their masks go back to the server's host arena
+        while srv.pending():
+            time.sleep(1e-3)
+        base = srv.stats()
+        srv.latencies.clear()  # every warm request has completed: the poller adds no more of theirs
     done_t = []
     t0 = time.perf_counter() + 0.01
     for tr, img in reqs:
@@ -944,9 +959,12 @@ def serve_once(make_server, reqs, rate):
         srv.submit(r)
     srv.stop(drain=True)
     st = srv.stats()
+    for key in ("completed", "steps", "alloc_waits"):
+        if key in base:
+            st[key] -= base[key]
     span = max(done_t) - t0
     st.update(pages_per_s=len(reqs) / span, seconds=span, offered_pages_per_s=rate,
-              mpix_per_s=sum(tr["h"] * tr["w"] for tr, _ in reqs) / span / 1e6)
+              mpix_per_s=sum(tr["h"] * tr["w"] for tr, _ in reqs) / span / 1e6, warm_requests=len(warm))
     return st
 
 
@@ -987,12 +1005,12 @@ def run_serve(args):
             reqs = serve_requests(n, 5, cvs)
             res = {}
             for name, mk in arms.items():
-                serve_once(mk, reqs[:64], None)        # warm-up: tensor maps, pinned pool, clocks
-                res[name] = {"capacity": serve_once(mk, reqs[:min(n, args.serve_capacity)], None), "loads": []}
+                res[name] = {"capacity": serve_once(mk, reqs[:min(n, args.serve_capacity)], None, warm=reqs[:64]),
+                             "loads": []}
             cap_b = res["batched"]["capacity"]["pages_per_s"]
             for name, mk in arms.items():
                 for ld in loads:
-                    st = serve_once(mk, reqs, ld * cap_b)
+                    st = serve_once(mk, reqs, ld * cap_b, warm=reqs[:64])
                     st["load"] = ld
                     res[name]["loads"].append(st)
             modes[mode] = res
