@@ -81,6 +81,7 @@ struct GsParams {
     int a, b, mm;     // window offsets [a, b]; anti-diagonal offsets |d| <= mm
     int span, sp, nr; // span columns (GT + W + 1), their padded bytes, ring rows (W + 1)
     int seg_rows;     // output rows per CTA
+    int small;        // |S'|^2 * 255^2 < 2^32: the variance numerator fits 32 bits
     uint32_t off_v, off_d, off_p; // shared-memory offsets
     FusedParams d;    // h, w, W, output, statistics, decision constants (nW = |S'|)
 };
@@ -170,6 +171,40 @@ __device__ __forceinline__ uint2 seg(const uint2 *P, int i0, int i1)
         r.y += t.y;
     }
     return r;
+}
+
+// Eq. 3 on t' past the fp32 filter: the double-float and fp64 stages, out of
+// line (a few pixels per page reach them).
+template <int RULE>
+__device__ __noinline__ uint32_t gs_decide_exact(uint32_t f, uint32_t n, uint32_t S1, uint32_t S2,
+                                                 const FusedParams &p)
+{
+    return decide_exact<RULE>(f, n, S1, S2, p);
+}
+
+// Eq. 3 on t' for one pixel: the fp32 filter with the constants for n = |S'|
+// when the structure lies whole in the page, with 1/n from rcp.approx
+// otherwise (the margin of decision_margin covers both); small: every
+// n S2 < 2^32, so V is formed and converted in 32 bits.
+template <int RULE>
+__device__ __forceinline__ uint32_t gs_decide(uint32_t f, uint32_t n, uint32_t S1, uint32_t S2, bool whole, int small,
+                                              const FusedParams &p, uint32_t &nfb, uint32_t &nties)
+{
+    float vf;
+    if (small)
+        vf = __uint2float_rn(n * S2 - S1 * S1);
+    else
+        vf = v_to_float((unsigned long long)n * S2 - (unsigned long long)S1 * S1);
+    const float sq = sqrt_approx(vf);
+    const float ff = __uint2float_rn(f), S1f = __uint2float_rn(S1);
+    const float d = whole ? filter_int<RULE>(ff, S1f, sq, p)
+                          : filter_n<RULE>(ff, S1f, sq, rcp_approx(__uint2float_rn(n)), p);
+    if (fabsf(d) >= p.E)
+        return d < 0.0f ? 0u : 255u;
+    const uint32_t r = gs_decide_exact<RULE>(f, n, S1, S2, p);
+    ++nfb;
+    nties += (r >> 9) & 1u;
+    return r & 0xffu;
 }
 
 // CPT output columns per thread (strip = CPT x 256 columns): column c of the
@@ -316,7 +351,6 @@ __global__ void __launch_bounds__(GT, CPT == 1 ? 4 : 3) gs_kernel(const __grid_c
             const uint8_t *rc = ring + back(es, b, nr) * sp; // row y
             const bool y_inner = y + a >= 0 && y + b < p.h;
             const bool ra = (unsigned)(y + a) < (unsigned)p.h, rb = (unsigned)(y + b) < (unsigned)p.h;
-            const int cnt_v = clip_len(y + a, y + b, p.h), cnt_vc = clip_len(y + a + 1, y + b - 1, p.h);
 #pragma unroll
             for (int h = 0; h < CPT; ++h) {
                 const int c = t + h * GT, x = x0 + c;
@@ -375,10 +409,12 @@ __global__ void __launch_bounds__(GT, CPT == 1 ? 4 : 3) gs_kernel(const __grid_c
                     }
                 }
                 uint32_t n;
-                if (x_inner && y_inner) {
+                const bool whole = x_inner && y_inner;
+                if (whole) {
                     n = p.nW; // the whole structure inside the page: |S'|
                 } else {
                     const int cnt_h = clip_len(x + a, x + b, p.w), cnt_hc = clip_len(x + a + 1, x + b - 1, p.w);
+                    const int cnt_v = clip_len(y + a, y + b, p.h), cnt_vc = clip_len(y + a + 1, y + b - 1, p.h);
                     int cnt = 0;
                     if (S::HC)
                         cnt += S::HC_CUT ? cnt_hc : cnt_h;
@@ -394,7 +430,7 @@ __global__ void __launch_bounds__(GT, CPT == 1 ? 4 : 3) gs_kernel(const __grid_c
                     }
                     n = (uint32_t)(cnt - S::CENTRE - nends);
                 }
-                const uint32_t r = decide_pixel<RULE>(f, n, S1, S2, p, nfb, nties);
+                const uint32_t r = gs_decide<RULE>(f, n, S1, S2, whole, g.small, p, nfb, nties);
                 p.dst[(long long)y * p.dst_pitch + x] = (uint8_t)r;
             }
         }
@@ -549,6 +585,7 @@ int launch_gs(const uint8_t *d_src, size_t src_pitch, int h, int w, int ch, int 
     // the fp32 filter's constants for the unclipped structure, n = |S'|
     const double n = (double)structure_size(gs, W);
     g.d.nW = (uint32_t)n;
+    g.small = n <= 256.0 ? 1 : 0;
     g.d.omkn = (float)((1.0 - k) / n);
     g.d.kRn2 = (float)(k / (R * n * n));
     g.d.invn = (float)(1.0 / n);
