@@ -11,14 +11,15 @@
 // converted once each, and the smallest T with the largest q wins (T = 0,
 // every pixel 255, when no T leaves both classes non-empty).
 //
-// Three launches on the caller's stream, no host round trip:
-//   otsu_hist    the histogram: 8 warp-private 256-bin tables in shared memory
-//                per CTA, merged into the caller's scratch with 64-bit atomics;
-//                each thread takes 16 pixels per step (128-bit loads);
-//   otsu_select  one CTA of 256 threads: a block scan gives every thread t the
-//                exact prefixes n0, s0 of the levels below t, thread t
-//                evaluates q(t), a block reduction takes the argmax and stores
-//                T in the scratch;
+// Two launches (and a memset of the scratch) on the caller's stream, no host
+// round trip:
+//   otsu_hist    the histogram: four 256-bin tables per warp in shared memory
+//                (lanes j, j+4, ...), merged into the caller's scratch with
+//                64-bit atomics; each thread takes 16 pixels per step (128-bit
+//                loads).  The last CTA to finish then picks T (select_T): a
+//                block scan gives every thread t the exact prefixes n0, s0 of
+//                the levels below t, thread t evaluates q(t), a block reduction
+//                takes the argmax and stores T in the scratch;
 //   otsu_mask    Eq. 2 with T read from the scratch: byte or packed mask,
 //                16 pixels per thread and step.
 // Both passes over the page are HBM streams (1 or 3 B/px read each, 1 B/px or
@@ -34,6 +35,8 @@ namespace {
 constexpr int kOtsuThreads = 256;
 constexpr int kHistOffset = 0;    // uint64[256] in the scratch
 constexpr int kTOffset = 2048;    // int32 T in the scratch
+constexpr int kDoneOffset = 2052; // uint32 count of histogram CTAs done (the last one picks T)
+constexpr int kCopies = 4;        // shared histogram tables per warp
 
 // Gray values of the 16 pixels starting at column x of row `row` (x a
 // multiple of 16, x + 16 <= w): 16 bytes (gray) or 48 bytes (RGB), 128-bit
@@ -57,6 +60,34 @@ __device__ __forceinline__ void load16(const uint8_t *row, int x, uint32_t (&g)[
     }
 }
 
+// The raw 16 or 48 bytes of a 16-pixel group (loads only: converted later, so
+// the next group's loads are in flight while this one is counted)
+template <int CIN>
+__device__ __forceinline__ void load16_raw(const uint8_t *row, int x, uint4 (&r)[CIN])
+{
+    const uint4 *p = reinterpret_cast<const uint4 *>(row + CIN * x);
+#pragma unroll
+    for (int i = 0; i < CIN; ++i)
+        r[i] = p[i];
+}
+
+template <int CIN>
+__device__ __forceinline__ void gray16(const uint4 (&r)[CIN], uint32_t (&g)[4])
+{
+    if (CIN == 1) {
+        g[0] = r[0].x;
+        g[1] = r[0].y;
+        g[2] = r[0].z;
+        g[3] = r[0].w;
+    } else {
+        const uint4 a = r[0], b = r[1 % CIN], c = r[2 % CIN];
+        g[0] = gray4(a.x, a.y, a.z);
+        g[1] = gray4(a.w, b.x, b.y);
+        g[2] = gray4(b.z, b.w, c.x);
+        g[3] = gray4(c.y, c.z, c.w);
+    }
+}
+
 template <int CIN>
 __device__ __forceinline__ uint32_t gray_at(const uint8_t *row, int x)
 {
@@ -66,54 +97,15 @@ __device__ __forceinline__ uint32_t gray_at(const uint8_t *row, int x)
     return gray1((uint32_t)px[0] | ((uint32_t)px[1] << 8) | ((uint32_t)px[2] << 16));
 }
 
-template <int CIN>
-__global__ void __launch_bounds__(kOtsuThreads)
-    otsu_hist(const uint8_t *src, long long pitch, int h, int w, unsigned long long *hist)
-{
-    __shared__ uint32_t sh[kOtsuThreads / 32][256];
-    const int warp = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < (kOtsuThreads / 32) * 256; i += kOtsuThreads)
-        (&sh[0][0])[i] = 0;
-    __syncthreads();
-    uint32_t *mine = sh[warp];
-    const int groups = (w + 15) / 16; // 16-pixel groups per row
-    const long long total = (long long)groups * h;
-    for (long long gi = (long long)blockIdx.x * kOtsuThreads + threadIdx.x; gi < total;
-         gi += (long long)gridDim.x * kOtsuThreads) {
-        const int y = (int)(gi / groups);
-        const int x = (int)(gi - (long long)y * groups) * 16;
-        const uint8_t *row = src + (long long)y * pitch;
-        if (x + 16 <= w) {
-            uint32_t g[4];
-            load16<CIN>(row, x, g);
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    atomicAdd(&mine[(g[q] >> (8 * j)) & 0xffu], 1u);
-        } else {
-            for (int xx = x; xx < w; ++xx)
-                atomicAdd(&mine[gray_at<CIN>(row, xx)], 1u);
-        }
-    }
-    __syncthreads();
-    for (int b = threadIdx.x; b < 256; b += kOtsuThreads) {
-        unsigned long long c = 0;
-#pragma unroll
-        for (int k = 0; k < kOtsuThreads / 32; ++k)
-            c += sh[k][b];
-        if (c)
-            atomicAdd(&hist[b], c);
-    }
-}
-
-__global__ void __launch_bounds__(kOtsuThreads) otsu_select(const unsigned long long *hist, int *T_out)
+// Otsu's T from the complete histogram, by one CTA of kOtsuThreads = 256
+// threads (one level each).
+__device__ void select_T(const unsigned long long *hist, int *T_out)
 {
     __shared__ unsigned long long wn[kOtsuThreads / 32], ws[kOtsuThreads / 32], tot[2];
     __shared__ double sq[kOtsuThreads / 32];
     __shared__ int st[kOtsuThreads / 32];
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-    const unsigned long long c = hist[t], v = c * (unsigned long long)t;
+    const unsigned long long c = __ldcg(hist + t), v = c * (unsigned long long)t;
     // inclusive block scan of (count, level sum), exact 64-bit (N <= 2^28)
     unsigned long long cn = c, cs = v;
 #pragma unroll
@@ -182,6 +174,94 @@ __global__ void __launch_bounds__(kOtsuThreads) otsu_select(const unsigned long 
 
 template <int CIN>
 __global__ void __launch_bounds__(kOtsuThreads)
+    otsu_hist(const uint8_t *src, long long pitch, int h, int w, unsigned long long *hist, unsigned int *done,
+              int *T_out)
+{
+    // four tables per warp (lanes j, j+4, ...): a page's few dominant levels
+    // would otherwise serialize all 32 lanes of a warp on one shared counter
+    __shared__ uint32_t sh[kOtsuThreads / 32 * kCopies][256];
+    const int warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < (kOtsuThreads / 32) * kCopies * 256; i += kOtsuThreads)
+        (&sh[0][0])[i] = 0;
+    __syncthreads();
+    uint32_t *mine = sh[warp * kCopies + (threadIdx.x & (kCopies - 1))];
+    const int groups = (w + 15) / 16; // 16-pixel groups per row
+    const long long total = (long long)groups * h;
+    // (row, group) of the thread's index, carried by the stride's quotient and
+    // remainder: no 64-bit division per step
+    const long long stride = (long long)gridDim.x * kOtsuThreads;
+    const int sq = (int)(stride / groups), sr = (int)(stride - (long long)sq * groups);
+    const long long g0 = (long long)blockIdx.x * kOtsuThreads + threadIdx.x;
+    int y = (int)(g0 / groups), gx = (int)(g0 - (long long)y * groups);
+    // software pipeline: the raw bytes of the thread's next full group are
+    // loaded before the current one is counted
+    uint4 cur[CIN];
+    bool have = false;
+    auto full = [&](int yy, int xx) { return xx + 16 <= w && yy < h; };
+    if (g0 < total && full(y, gx * 16)) {
+        load16_raw<CIN>(src + (long long)y * pitch, gx * 16, cur);
+        have = true;
+    }
+    for (long long gi = g0; gi < total; gi += stride) {
+        const int x = gx * 16;
+        const uint8_t *row = src + (long long)y * pitch;
+        int ny = y + sq, ngx = gx + sr;
+        if (ngx >= groups) {
+            ngx -= groups;
+            ++ny;
+        }
+        uint4 nxt[CIN];
+        const bool nfull = gi + stride < total && full(ny, ngx * 16);
+        if (nfull)
+            load16_raw<CIN>(src + (long long)ny * pitch, ngx * 16, nxt);
+        if (have) {
+            uint32_t g[4];
+            gray16<CIN>(cur, g);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    atomicAdd(&mine[(g[q] >> (8 * j)) & 0xffu], 1u);
+        } else {
+            for (int xx = x; xx < w; ++xx)
+                atomicAdd(&mine[gray_at<CIN>(row, xx)], 1u);
+        }
+        if (nfull) {
+#pragma unroll
+            for (int i = 0; i < CIN; ++i)
+                cur[i] = nxt[i];
+        }
+        have = nfull;
+        gx = ngx;
+        y = ny;
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < 256; b += kOtsuThreads) {
+        unsigned long long c = 0;
+#pragma unroll
+        for (int k = 0; k < kOtsuThreads / 32 * kCopies; ++k)
+            c += sh[k][b];
+        if (c)
+            atomicAdd(&hist[b], c);
+    }
+    // the last CTA to finish picks T (the histogram is complete once every
+    // CTA's additions are visible: each fences before it counts itself)
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0)
+        s_last = atomicAdd(done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        select_T(hist, T_out);
+        if (threadIdx.x == 0)
+            *done = 0u; // ready for the next call on this scratch
+    }
+}
+
+template <int CIN>
+__global__ void __launch_bounds__(kOtsuThreads)
     otsu_mask(const uint8_t *src, long long pitch, int h, int w, const int *T_in, uint8_t *dst, long long dst_pitch,
               int packed, int vec_ok)
 {
@@ -190,10 +270,14 @@ __global__ void __launch_bounds__(kOtsuThreads)
     const uint32_t T4 = T > 255u ? 0u : T * 0x01010101u;
     const int groups = (w + 15) / 16;
     const long long total = (long long)groups * h;
-    for (long long gi = (long long)blockIdx.x * kOtsuThreads + threadIdx.x; gi < total;
-         gi += (long long)gridDim.x * kOtsuThreads) {
-        const int y = (int)(gi / groups);
-        const int x = (int)(gi - (long long)y * groups) * 16;
+    // (row, group) of the thread's index, carried by the stride's quotient and
+    // remainder: no 64-bit division per step
+    const long long stride = (long long)gridDim.x * kOtsuThreads;
+    const int sq = (int)(stride / groups), sr = (int)(stride - (long long)sq * groups);
+    const long long g0 = (long long)blockIdx.x * kOtsuThreads + threadIdx.x;
+    int y = (int)(g0 / groups), gx = (int)(g0 - (long long)y * groups);
+    for (long long gi = g0; gi < total; gi += stride) {
+        const int x = gx * 16;
         const uint8_t *row = src + (long long)y * pitch;
         uint8_t *drow = dst + (long long)y * dst_pitch;
         if (x + 16 <= w) {
@@ -231,6 +315,12 @@ __global__ void __launch_bounds__(kOtsuThreads)
                     drow[(x >> 3) + 1] = (uint8_t)(bits >> 8);
             }
         }
+        gx += sr;
+        y += sq;
+        if (gx >= groups) {
+            gx -= groups;
+            ++y;
+        }
     }
 }
 
@@ -245,7 +335,9 @@ int launch_otsu(const uint8_t *d_src, size_t src_pitch, int h, int w, int ch, ui
         return rc;
     auto *hist = reinterpret_cast<unsigned long long *>(static_cast<uint8_t *>(d_scratch) + kHistOffset);
     int *T = reinterpret_cast<int *>(static_cast<uint8_t *>(d_scratch) + kTOffset);
-    cudaError_t e = cudaMemsetAsync(hist, 0, 256 * sizeof(unsigned long long), stream);
+    auto *done = reinterpret_cast<unsigned int *>(static_cast<uint8_t *>(d_scratch) + kDoneOffset);
+    // the histogram, T and the CTA counter, contiguous from offset 0
+    cudaError_t e = cudaMemsetAsync(d_scratch, 0, kDoneOffset + sizeof(unsigned int), stream);
     if (e != cudaSuccess)
         return cuda_fail(e, "clear histogram");
     const long long groups = (long long)((w + 15) / 16) * h;
@@ -253,10 +345,9 @@ int launch_otsu(const uint8_t *d_src, size_t src_pitch, int h, int w, int ch, ui
     const int grid = (int)std::max<long long>(1, std::min<long long>((long long)sms * 4,
                                                                       (groups + kOtsuThreads - 1) / kOtsuThreads));
     if (ch == 1)
-        otsu_hist<1><<<grid, kOtsuThreads, 0, stream>>>(d_src, (long long)src_pitch, h, w, hist);
+        otsu_hist<1><<<grid, kOtsuThreads, 0, stream>>>(d_src, (long long)src_pitch, h, w, hist, done, T);
     else
-        otsu_hist<3><<<grid, kOtsuThreads, 0, stream>>>(d_src, (long long)src_pitch, h, w, hist);
-    otsu_select<<<1, kOtsuThreads, 0, stream>>>(hist, T);
+        otsu_hist<3><<<grid, kOtsuThreads, 0, stream>>>(d_src, (long long)src_pitch, h, w, hist, done, T);
     const int vec_ok = ((reinterpret_cast<uintptr_t>(d_dst) | dst_pitch) & 15u) == 0 ? 1 : 0;
     if (ch == 1)
         otsu_mask<1><<<grid, kOtsuThreads, 0, stream>>>(d_src, (long long)src_pitch, h, w, T, d_dst,
