@@ -203,11 +203,12 @@ BNZ_API int bnz_dual_dev(const uint8_t *d_src, size_t src_pitch, int height, int
  * 2^28 pixels.  d_dst: byte or packed mask as bnz_sauvola_dev.  d_scratch:
  * caller-owned device memory of BNZ_OTSU_SCRATCH_BYTES, 16-byte aligned; the
  * call leaves the histogram (256 x uint64) at offset 0 and T (int32) at offset
- * 2048 (bytes 2052..2055 hold a counter the call resets).  A memset and two
+ * 2048 (bytes 2052..2055 hold a counter the call resets; bytes 4096..20479 the
+ * histogram kernel's 16 partial tables).  A memset and two
  * kernels on `stream`, no host synchronization; calls that share a scratch
  * buffer must not overlap on the device.  Errors: BNZ_EINVAL
  * for bad arguments, BNZ_ECUDA for a failed launch. */
-#define BNZ_OTSU_SCRATCH_BYTES 4096
+#define BNZ_OTSU_SCRATCH_BYTES 20480
 BNZ_API int bnz_otsu_dev(const uint8_t *d_src, size_t src_pitch, int height, int width, int channels,
                  uint8_t *d_dst, size_t dst_pitch, int packed, void *d_scratch, void *stream);
 

@@ -317,7 +317,7 @@ def binarize_dual(d_src, W: int, k_sauvola: float = 0.5, R: float = 128.0, k_nib
     return out_s, out_n
 
 
-BNZ_OTSU_SCRATCH_BYTES = 4096
+BNZ_OTSU_SCRATCH_BYTES = 20480
 
 
 def bnz_otsu_dev(d_src, d_dst, d_scratch, packed: bool = False, stream=None) -> None:

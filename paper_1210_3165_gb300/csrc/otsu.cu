@@ -16,7 +16,11 @@
 //   otsu_hist    the histogram: four 256-bin tables per warp in shared memory
 //                (lanes j, j+4, ...), merged into the caller's scratch with
 //                64-bit atomics; each thread takes 16 pixels per step (128-bit
-//                loads).  The last CTA to finish then picks T (select_T): a
+//                loads); each CTA adds its counts into one of 16 partial tables
+//                in the scratch (CTA i into table i mod 16: 16 times fewer
+//                atomic additions per global counter than one shared table).
+//                The last CTA to finish sums the partial tables into the
+//                histogram and picks T (select_T): a
 //                block scan gives every thread t the exact prefixes n0, s0 of
 //                the levels below t, thread t evaluates q(t), a block reduction
 //                takes the argmax and stores T in the scratch;
@@ -36,6 +40,9 @@ constexpr int kOtsuThreads = 256;
 constexpr int kHistOffset = 0;    // uint64[256] in the scratch
 constexpr int kTOffset = 2048;    // int32 T in the scratch
 constexpr int kDoneOffset = 2052; // uint32 count of histogram CTAs done (the last one picks T)
+constexpr int kPartOffset = 4096; // uint32[kParts][256]: the CTAs' partial histograms
+constexpr int kParts = 16;
+static_assert(kPartOffset + kParts * 256 * 4 <= BNZ_OTSU_SCRATCH_BYTES, "Otsu scratch too small");
 constexpr int kCopies = 4;        // shared histogram tables per warp
 
 // Gray values of the 16 pixels starting at column x of row `row` (x a
@@ -98,14 +105,14 @@ __device__ __forceinline__ uint32_t gray_at(const uint8_t *row, int x)
 }
 
 // Otsu's T from the complete histogram, by one CTA of kOtsuThreads = 256
-// threads (one level each).
-__device__ void select_T(const unsigned long long *hist, int *T_out)
+// threads (one level each; c = the count of level threadIdx.x).
+__device__ void select_T(unsigned long long c, int *T_out)
 {
     __shared__ unsigned long long wn[kOtsuThreads / 32], ws[kOtsuThreads / 32], tot[2];
     __shared__ double sq[kOtsuThreads / 32];
     __shared__ int st[kOtsuThreads / 32];
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-    const unsigned long long c = __ldcg(hist + t), v = c * (unsigned long long)t;
+    const unsigned long long v = c * (unsigned long long)t;
     // inclusive block scan of (count, level sum), exact 64-bit (N <= 2^28)
     unsigned long long cn = c, cs = v;
 #pragma unroll
@@ -174,8 +181,8 @@ __device__ void select_T(const unsigned long long *hist, int *T_out)
 
 template <int CIN>
 __global__ void __launch_bounds__(kOtsuThreads)
-    otsu_hist(const uint8_t *src, long long pitch, int h, int w, unsigned long long *hist, unsigned int *done,
-              int *T_out)
+    otsu_hist(const uint8_t *src, long long pitch, int h, int w, unsigned long long *hist, uint32_t *parts,
+              unsigned int *done, int *T_out)
 {
     // four tables per warp (lanes j, j+4, ...): a page's few dominant levels
     // would otherwise serialize all 32 lanes of a warp on one shared counter
@@ -236,13 +243,14 @@ __global__ void __launch_bounds__(kOtsuThreads)
         y = ny;
     }
     __syncthreads();
+    uint32_t *part = parts + (blockIdx.x % kParts) * 256;
     for (int b = threadIdx.x; b < 256; b += kOtsuThreads) {
-        unsigned long long c = 0;
+        uint32_t c = 0;
 #pragma unroll
         for (int k = 0; k < kOtsuThreads / 32 * kCopies; ++k)
             c += sh[k][b];
         if (c)
-            atomicAdd(&hist[b], c);
+            atomicAdd(&part[b], c); // < 2^28 pixels: a partial table's counts fit 32 bits
     }
     // the last CTA to finish picks T (the histogram is complete once every
     // CTA's additions are visible: each fences before it counts itself)
@@ -254,7 +262,12 @@ __global__ void __launch_bounds__(kOtsuThreads)
     __syncthreads();
     if (s_last) {
         __threadfence();
-        select_T(hist, T_out);
+        unsigned long long c = 0; // kOtsuThreads = 256: thread t sums level t over the partial tables
+#pragma unroll
+        for (int k = 0; k < kParts; ++k)
+            c += __ldcg(parts + k * 256 + threadIdx.x);
+        hist[threadIdx.x] = c;
+        select_T(c, T_out);
         if (threadIdx.x == 0)
             *done = 0u; // ready for the next call on this scratch
     }
@@ -336,8 +349,9 @@ int launch_otsu(const uint8_t *d_src, size_t src_pitch, int h, int w, int ch, ui
     auto *hist = reinterpret_cast<unsigned long long *>(static_cast<uint8_t *>(d_scratch) + kHistOffset);
     int *T = reinterpret_cast<int *>(static_cast<uint8_t *>(d_scratch) + kTOffset);
     auto *done = reinterpret_cast<unsigned int *>(static_cast<uint8_t *>(d_scratch) + kDoneOffset);
-    // the histogram, T and the CTA counter, contiguous from offset 0
-    cudaError_t e = cudaMemsetAsync(d_scratch, 0, kDoneOffset + sizeof(unsigned int), stream);
+    auto *parts = reinterpret_cast<uint32_t *>(static_cast<uint8_t *>(d_scratch) + kPartOffset);
+    // the histogram, T, the CTA counter and the partial tables, from offset 0
+    cudaError_t e = cudaMemsetAsync(d_scratch, 0, kPartOffset + kParts * 256 * sizeof(uint32_t), stream);
     if (e != cudaSuccess)
         return cuda_fail(e, "clear histogram");
     const long long groups = (long long)((w + 15) / 16) * h;
@@ -345,9 +359,9 @@ int launch_otsu(const uint8_t *d_src, size_t src_pitch, int h, int w, int ch, ui
     const int grid = (int)std::max<long long>(1, std::min<long long>((long long)sms * 4,
                                                                       (groups + kOtsuThreads - 1) / kOtsuThreads));
     if (ch == 1)
-        otsu_hist<1><<<grid, kOtsuThreads, 0, stream>>>(d_src, (long long)src_pitch, h, w, hist, done, T);
+        otsu_hist<1><<<grid, kOtsuThreads, 0, stream>>>(d_src, (long long)src_pitch, h, w, hist, parts, done, T);
     else
-        otsu_hist<3><<<grid, kOtsuThreads, 0, stream>>>(d_src, (long long)src_pitch, h, w, hist, done, T);
+        otsu_hist<3><<<grid, kOtsuThreads, 0, stream>>>(d_src, (long long)src_pitch, h, w, hist, parts, done, T);
     const int vec_ok = ((reinterpret_cast<uintptr_t>(d_dst) | dst_pitch) & 15u) == 0 ? 1 : 0;
     if (ch == 1)
         otsu_mask<1><<<grid, kOtsuThreads, 0, stream>>>(d_src, (long long)src_pitch, h, w, T, d_dst,
