@@ -40,7 +40,9 @@
  *   - Statistics (optional, `d_stats`): device pointer to 4 unsigned 64-bit
  *     counters that the kernels add to (the caller zeroes them):
  *       [0] pixels re-evaluated past the fp32 filter (inside its proven
- *           margin: double-float, then the fp64 definition near a tie),
+ *           margin: for Niblack a tighter fp32 evaluation of n (f - t) with a
+ *           per-pixel bound, then double-float, then the fp64 definition near
+ *           a tie),
  *       [1] ties: pixels with |f - t| < 1e-9,
  *       [2] bounded waits that timed out: a CTA that gives up writes no output
  *           of its part of the page.  The synchronous host-pointer calls

@@ -164,6 +164,33 @@ __device__ uint32_t decide_exact(uint32_t f, uint32_t n, uint32_t S1, uint32_t S
     return decide_fp64<RULE>(f, n, S1, S2, p);
 }
 
+// Eq. 3 for a pixel inside the fp32 filter's margin.  Niblack first tries a
+// tighter fp32 evaluation of X = n (f - t) = (n f - S1) - k sqrt(V):
+//   A = n f - S1 is an exact integer below 2^24 in magnitude, so exact in fp32;
+//   r = RN(sqrt(RN2(V))) = sqrt(V) (1 + d), |d| <= 2.001u (V to fp32 within 2u,
+//   halved by the root, then the root's own rounding); C = RN(RN(k) r) =
+//   k sqrt(V) (1 + e), |e| <= 4.01u; D = RN(A - C), so |D - X| <= 4.01u |k| sqrt(V)
+//   (1 + u) + u |X|.  With tau = 1e-9 + the fp64 definition's error, |D| > 4.5u
+//   |k| r + 1.01 tau n (p.rk, p.rt) gives |f - t| = |X| / n > tau: no tie in the
+//   definition and the sign of D.  The rest (and every Sauvola pixel, whose t =
+//   m (1 - k + k s / R) scales with m |k| and leaves no such gain) take the
+//   double-float and fp64 stages.
+template <int RULE>
+__device__ __forceinline__ uint32_t decide_refine(uint32_t f, uint32_t n, uint32_t S1, uint32_t S2,
+                                                  const FusedParams &p)
+{
+    if (RULE == BNZ_NIBLACK) {
+        const int A = (int)(n * f) - (int)S1;
+        const unsigned long long V = (unsigned long long)n * S2 - (unsigned long long)S1 * S1;
+        const float r = __fsqrt_rn(v_to_float(V));
+        const float D = __fsub_rn(__int2float_rn(A), __fmul_rn(p.kf, r));
+        const float bnd = __fmaf_rn(p.rk, r, __fmul_rn(p.rt, __uint2float_rn(n)));
+        if (fabsf(D) > bnd)
+            return D < 0.0f ? 0u : 255u;
+    }
+    return decide_exact<RULE>(f, n, S1, S2, p);
+}
+
 } // namespace bnz
 
 namespace bnz {

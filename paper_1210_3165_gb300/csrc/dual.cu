@@ -201,6 +201,8 @@ int launch_dual(const uint8_t *d_src, size_t src_pitch, int h, int w, int ch, in
     pn.kR = dn.kR;
     pn.E = dn.E;
     pn.Tdf = dn.Tdf;
+    pn.rk = dn.rk;
+    pn.rt = dn.rt;
     pn.kh = dn.kh;
     pn.kl = dn.kl;
     pn.c1h = dn.c1h;

@@ -243,6 +243,11 @@ void fill_decision_params(FusedParams *p, int h, int w, int W, int rule, double 
     p->kR = (float)(k / R);
     p->E = decision_margin(rule, k, R);
     p->Tdf = double_float_cut(rule, k, R);
+    {
+        const double u = 1.0 / 16777216.0;
+        p->rk = (float)(4.5 * u * std::fabs(k));
+        p->rt = (float)(1.01 * (1e-9 + fp64_definition_error(rule, k, R)));
+    }
     auto split = [](double x, float *hi, float *lo) {
         *hi = (float)x;
         *lo = (float)(x - (double)*hi);

@@ -75,6 +75,9 @@ struct FusedParams {
     // the second stage decides by the sign of its f - t when |f - t| > Tdf =
     // 1e-9 + its own error bound + the fp64 definition's (double_float_cut)
     float Tdf;
+    // Niblack, first re-decision of a margin pixel: X = n (f - t) = (n f - S1) - k sqrt(V) in fp32 decides
+    // when |X| > rk sqrt(V) + rt n (rk = 4.5 u |k|, rt = 1.01 (1e-9 + the fp64 definition's error))
+    float rk, rt;
     long long timeout_cycles; // limit of every wait but the final drain (<= 0: give up unless already complete)
     long long drain_cycles;   // limit of the TMA issuer's final wait for its copies in flight
 };

@@ -771,7 +771,7 @@ __device__ __forceinline__ void fix_margin(const FusedParams &p, int y, int xg0,
         for (int qq = 1; qq < 4; ++qq)
             if ((t >> 2) == qq)
                 word = fw[qq];
-        const uint32_t r = decide_exact<RULE>(byte_dyn(word, t & 3), clipped_n(p, nr, xg0 + t), S1, S2, p);
+        const uint32_t r = decide_refine<RULE>(byte_dyn(word, t & 3), clipped_n(p, nr, xg0 + t), S1, S2, p);
         ++nfb;
         nties += (r >> 9) & 1u;
         white |= (r & 1u) << t;
