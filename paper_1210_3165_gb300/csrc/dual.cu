@@ -200,6 +200,7 @@ int launch_dual(const uint8_t *d_src, size_t src_pitch, int h, int w, int ch, in
     pn.omk = dn.omk;
     pn.kR = dn.kR;
     pn.E = dn.E;
+    pn.Eint = dn.Eint;
     pn.Tdf = dn.Tdf;
     pn.rk = dn.rk;
     pn.rt = dn.rt;

@@ -173,6 +173,31 @@ float decision_margin(int rule, double k, double R)
     return (float)E;
 }
 
+// The unclipped-window filter (n = W*W; constants rounded once on the host,
+// u each) is tighter.  Niblack, nd = RN(S1 RN(1/n) + RN(RN(k/n) sq - f)) with
+// sq = sqrt.approx(V to fp32 within 2u) = sqrt(V) (1 + e + 1.01u):
+//   S1 RN(1/n) = m (1 + u)                      -> u m
+//   RN(k/n) sq = k s (1 + e + 2.02u)            -> |k| s (e + 2.02u)
+//   rounding of k s - f                         -> u (1.01 |k| s + 255)
+//   final rounding                              -> u (255 + |k| s + 1)
+// so |nd - (t - f)| <= u (766 + 2.01 |k| s) + |k| s (e + 2.02u), s <= 127.5;
+// E_int = 2 that + 1e-6 + 2 (the fp64 definition's error), never above E.
+// A pixel the fast filter might decide wrongly then has |nd| < E_int, and the
+// lane's re-evaluation with the general filter (margin E) flags it.  Sauvola
+// keeps E (its margin pixels are rare).
+float decision_margin_interior(int rule, double k, double R)
+{
+    const float E = decision_margin(rule, k, R);
+    if (rule != BNZ_NIBLACK)
+        return E;
+    const double u = 1.0 / 16777216.0;
+    const double e = kSqrtApproxRelErr;
+    const double ks = std::fabs(k) * 127.5;
+    const double em = u * (766.0 + 2.01 * ks) + ks * (e + 2.02 * u);
+    const double Ei = 2.0 * em + 1e-6 + 2.0 * fp64_definition_error(rule, k, R);
+    return Ei < (double)E ? (float)Ei : E;
+}
+
 // Absolute error of the fp64 sequence of the definition (m = S1/n, s =
 // sqrt(V)/n, then the rule left to right; V exact) against exact arithmetic:
 // each correctly rounded operation adds at most w = 2^-53 of its result, and
@@ -242,6 +267,7 @@ void fill_decision_params(FusedParams *p, int h, int w, int W, int rule, double 
     p->omk = (float)(1.0 - k);
     p->kR = (float)(k / R);
     p->E = decision_margin(rule, k, R);
+    p->Eint = decision_margin_interior(rule, k, R);
     p->Tdf = double_float_cut(rule, k, R);
     {
         const double u = 1.0 / 16777216.0;

@@ -70,6 +70,7 @@ struct FusedParams {
     float omkn, kRn2, invn, kn;
     float kf, omk, kR; // k, 1-k, k/R for windows with a per-pixel n
     float E;           // proven bound on |d32 - (f - t)|, with safety factor
+    float Eint;        // the same for the unclipped-window filter (n = W*W, host constants): <= E
     // double-float constants of the second stage: k, 1-k, k/R as hi + lo
     float kh, kl, c1h, c1l, c2h, c2l;
     // the second stage decides by the sign of its f - t when |f - t| > Tdf =
@@ -112,8 +113,10 @@ int device_err_flag(unsigned int **flag);
 constexpr double kSqrtApproxRelErr = 1.0 / (1 << 21);
 constexpr double kRcpApproxRelErr = 1.0 / (1 << 22);
 
-// fp32 decision margin E (see fused.cu for the derivation).
+// fp32 decision margin E (see fused.cu for the derivation), and the tighter
+// one of the unclipped-window filter.
 float decision_margin(int rule, double k, double R);
+float decision_margin_interior(int rule, double k, double R);
 // Error bounds, for m <= 255 and s <= 127.5, of the double-float evaluation of
 // f - t and of the fp64 definition's t; and the cut Tdf built from them.
 double double_float_error(int rule, double k, double R);

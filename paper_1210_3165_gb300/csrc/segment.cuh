@@ -852,11 +852,13 @@ __device__ __forceinline__ void consume(const FusedParams &p, const Segment &sg,
             uint32_t outw[4];
             float mn = INFINITY; // smallest |nd| of the lane's pixels inside the image
             const bool sm = small_window(p);
+            float Eq = p.E; // the margin of the filter that ran
             if (!__any_sync(0xffffffffu, lane_clip)) {
                 if (sm)
                     decide_lane_int<RULE, true>(p, base1, base2, d1, d2, fw, outw, mn);
                 else
                     decide_lane_int<RULE, false>(p, base1, base2, d1, d2, fw, outw, mn);
+                Eq = p.Eint;
             } else {
                 const float2 *tab = reinterpret_cast<const float2 *>(smem + kTabOffset);
                 if (sm)
@@ -864,7 +866,7 @@ __device__ __forceinline__ void consume(const FusedParams &p, const Segment &sg,
                 else
                     decide_lane_border<RULE, false>(p, tab, y, g.xg0, base1, base2, d1, d2, fw, outw, mn);
             }
-            if (mn < p.E && g.active) { // rare: a value inside the fp32 margin
+            if (mn < Eq && g.active) { // rare: a value inside the fp32 margin
                 uint32_t e1[L], e2[L];
                 lane_sums_again<KO, KI, WM8>(p, g, C1, e1, e2);
                 fix_margin<RULE>(p, y, g.xg0, base1, base2, e1, e2, fw, outw, nfb, nties);
