@@ -106,3 +106,27 @@ def test_many_pixels_take_the_exact_path(bnz, page):
     s = st.cpu().numpy()
     assert_same(got, ref, "sauvola k/R=1000")
     assert s[1] == ties and s[0] > page.shape[0] * page.shape[1] // 100
+
+
+@pytest.mark.parametrize("k", [-0.2, -0.5, 0.3])
+@pytest.mark.parametrize("W", [15, 61])
+def test_niblack_margin_pixels(bnz, k, W):
+    """The usual Niblack settings leave a few pixels in 10^5 inside the fp32 margin; those take the tighter
+    fp32 evaluation of n (f - t), then the double-float and fp64 stages, in the fused kernel (the interior
+    margin for warps whose windows lie inside the page, the general one at the borders) and in the
+    two-rule kernel.  Masks and tie counts equal the oracle's, and the margin path did run."""
+    img = synth.page(1200, 1300, 7 + W, synth.STAINS, 3)
+    img[300:340, 400:700] = 140           # a flat patch: ties of the definition
+    ref, ties = oracle.binarize(img, W, oracle.NIBLACK, k, 1.0, threads=NTHREADS)
+    st = stats_tensor()
+    d = bnz.to_device_pitched(img)
+    got = bnz.binarize(d, W, "niblack", k, d_stats=st).cpu().numpy()
+    s = st.cpu().numpy()
+    assert_same(got, ref, f"niblack W={W} k={k}")
+    assert s[1] == ties and s[2] == 0 and s[0] > 0
+    ref_s, _ = oracle.binarize(img, W, oracle.SAUVOLA, 0.5, 128.0, threads=NTHREADS)
+    st2 = stats_tensor()
+    out_s, out_n = bnz.binarize_dual(d, W, 0.5, 128.0, k, d_stats=st2)
+    assert_same(out_n.cpu().numpy(), ref, f"dual niblack W={W} k={k}")
+    assert_same(out_s.cpu().numpy(), ref_s, f"dual sauvola W={W}")
+    assert int(st2[3].item()) == ties
