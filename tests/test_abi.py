@@ -223,3 +223,17 @@ def test_window_call_checks(lib):
         rc = lib.bnz_binarize_window(src.ctypes.data, 64, 64, 1, 15, bnz.BNZ_SAUVOLA, 0.5, 128.0, dst.ctypes.data,
                                      1 << 20)
         assert rc == bnz.BNZ_ENODEV
+
+
+def test_binding_constants_match_the_header():
+    """Every numeric #define of include/bnz.h that the Python binding also defines has the same value there
+    (buffer sizes such as BNZ_OTSU_SCRATCH_BYTES are allocated from the binding's copy)."""
+    text = open(os.path.join(ROOT, "include", "bnz.h")).read()
+    defs = dict(re.findall(r"^#define\s+(BNZ_[A-Z0-9_]+)\s+([-+0-9.eE]+)\b", text, flags=re.M))
+    assert "BNZ_OTSU_SCRATCH_BYTES" in defs and "BNZ_MAX_W" in defs
+    checked = 0
+    for name, value in defs.items():
+        if hasattr(bnz, name):
+            assert float(getattr(bnz, name)) == float(value), (name, getattr(bnz, name), value)
+            checked += 1
+    assert checked >= 2
