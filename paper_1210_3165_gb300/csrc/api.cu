@@ -872,7 +872,7 @@ int bnz_copy2d_async(void *dst, size_t dst_pitch, const void *src, size_t src_pi
     return e == cudaSuccess ? BNZ_OK : cuda_fail(e, "cudaMemcpy2DAsync");
 }
 
-int bnz_version(void) { return 100; }
+int bnz_version(void) { return 200; } // 0.2.0: the Otsu scratch grew to BNZ_OTSU_SCRATCH_BYTES = 20480
 
 int bnz_fused_plan(int height, int width, int channels, int W, const bnz_tile *tile, size_t *smem_bytes,
                    int *grid_ctas, int *tile_w, int *tile_h)
