@@ -1,0 +1,99 @@
+"""The fp32 error bounds behind the Niblack margin stages, checked on the CPU.
+
+The fused kernel decides a pixel with an fp32 filter and re-decides it exactly
+only when the filter lands inside a proven margin.  These tests emulate, with
+numpy float32 arithmetic (each operation rounded to nearest, as on the device),
+two of those fp32 evaluations and compare them with exact rational arithmetic
+on random and extreme windows:
+
+  - the unclipped-window Niblack filter nd = RN(S1 RN(1/n) + RN(RN(k/n) sq - f)),
+    sq = sqrt.approx(V) with its worst relative error e = 2^-21 either way, must
+    stay within the bound u (766 + 2.01 |k| s) + |k| s (e + 2.02 u) of t - f
+    (the interior margin, half of E_int without the 1e-6);
+  - the refinement D = RN(RN(n f - S1) - RN(RN(k) r)), r = RN(sqrt(RN(V))), must
+    have the sign of X = n (f - t) and |X| / n > 1e-9 whenever
+    |D| > 4.5 u |k| r + 1.01 n 1e-9.
+
+Niblack t = m + k s with m = S1 / n, s = sqrt(V) / n, V = n S2 - S1^2 (Eq. 3 and
+the Niblack rule); the exact X uses integer arithmetic and a 60-digit root."""
+from decimal import Decimal, getcontext
+
+import numpy as np
+
+getcontext().prec = 60
+U = 2.0 ** -24
+E_SQRT = 2.0 ** -21
+F32 = np.float32
+
+
+def rn(x):
+    return F32(x)
+
+
+def v_to_float(V):
+    # high word exact, low word rounded, one more rounding in the fused add (as on the device)
+    hi, lo = V >> 32, V & 0xFFFFFFFF
+    return rn(float(rn(hi)) * 4294967296.0 + float(rn(lo)))
+
+
+def windows(rng, count):
+    """(n, f, S1, S2) of random windows: W x W of random gray levels, plus near-flat and extreme ones."""
+    out = []
+    for i in range(count):
+        W = int(rng.choice([3, 4, 15, 31, 61, 101, 255]))
+        n = W * W
+        kind = i % 4
+        if kind == 0:
+            g = rng.integers(0, 256, n)
+        elif kind == 1:
+            g = np.clip(rng.normal(rng.integers(0, 256), 3, n).round(), 0, 255).astype(np.int64)
+        elif kind == 2:
+            g = np.full(n, rng.integers(0, 256)); g[rng.integers(0, n)] = rng.integers(0, 256)
+        else:
+            g = rng.choice([0, 255], n)
+        S1, S2 = int(g.sum()), int((g.astype(np.int64) ** 2).sum())
+        out.append((n, int(rng.integers(0, 256)), S1, S2))
+    return out
+
+
+def exact_t_minus_f(n, f, S1, S2, k):
+    V = n * S2 - S1 * S1
+    s = Decimal(V).sqrt() / n
+    return Decimal(S1) / n + Decimal(k) * s - f, s, V
+
+
+def test_interior_niblack_filter_bound():
+    rng = np.random.default_rng(5)
+    for k in (-0.2, -0.5, 0.3, -1.5, 150.0):
+        kn, invn_cache = None, {}
+        for n, f, S1, S2 in windows(rng, 600):
+            invn = rn(1.0 / n)
+            kn = rn(k / n)
+            tf, s, V = exact_t_minus_f(n, f, S1, S2, k)
+            for d in (-E_SQRT, 0.0, E_SQRT):
+                sq = rn(float(np.sqrt(np.float64(v_to_float(V)))) * (1.0 + d))
+                y = rn(float(kn) * float(sq) - f)          # fma: one rounding
+                nd = rn(float(S1) * float(invn) + float(y))  # fma: one rounding
+                ks = abs(k) * float(s)
+                bound = U * (766 + 2.01 * ks) + ks * (E_SQRT + 2.02 * U)
+                assert abs(Decimal(float(nd)) - tf) <= Decimal(bound), (k, n, f, S1, S2, d)
+
+
+def test_niblack_refinement_decides_correctly():
+    rng = np.random.default_rng(9)
+    tau = 1e-9
+    decided = 0
+    for k in (-0.2, -0.5, 0.3, -150.0):
+        kf = rn(k)
+        for n, f, S1, S2 in windows(rng, 600):
+            tf, s, V = exact_t_minus_f(n, f, S1, S2, k)
+            X = -tf * n                                   # n (f - t)
+            A = rn(n * f - S1)
+            assert float(A) == n * f - S1                 # exact below 2^24
+            r = rn(np.sqrt(np.float64(v_to_float(V))))    # correctly rounded root of the rounded V
+            D = rn(float(A) - float(rn(float(kf) * float(r))))
+            bnd = rn(float(rn(4.5 * U * abs(k))) * float(r) + float(rn(1.01 * tau)) * n)
+            if abs(float(D)) > float(bnd):
+                decided += 1
+                assert (float(D) > 0) == (X > 0) and abs(X) / n > Decimal(tau), (k, n, f, S1, S2)
+    assert decided > 1000
