@@ -10,6 +10,8 @@ on random and extreme windows:
     sq = sqrt.approx(V) with its worst relative error e = 2^-21 either way, must
     stay within the bound u (766 + 2.01 |k| s) + |k| s (e + 2.02 u) of t - f
     (the interior margin, half of E_int without the 1e-6);
+  - the unclipped-window Sauvola filter nd = RN(S1 RN(omkn + kRn2 sq) - f) must
+    stay within the host's Sauvola bound (half of its margin E without the 1e-6);
   - the refinement D = RN(RN(n f - S1) - RN(RN(k) r)), r = RN(sqrt(RN(V))), must
     have the sign of X = n (f - t) and |X| / n > 1e-9 whenever
     |D| > 4.5 u |k| r + 1.01 n 1e-9.
@@ -97,3 +99,29 @@ def test_niblack_refinement_decides_correctly():
                 decided += 1
                 assert (float(D) > 0) == (X > 0) and abs(X) / n > Decimal(tau), (k, n, f, S1, S2)
     assert decided > 1000
+
+
+def sauvola_em(k, R):
+    """Half the fp32 margin E of Sauvola before its 1e-6 (the host's bound, m <= 255, s <= 127.5)."""
+    m, smax, ak = 255.0, 127.5, abs(k)
+    T = m * (abs(1 - k) + ak * smax / R)
+    return 6 * U * m * abs(1 - k) + m * ak * (smax / R) * (12 * U + E_SQRT) + U * T + U * (255 + T)
+
+
+def test_interior_sauvola_filter_bound():
+    """nd = RN(S1 RN(omkn + kRn2 sq) - f) with omkn = RN((1-k)/n), kRn2 = RN(k/(R n^2)) stays within the
+    host's Sauvola bound of t - f = m (1 + k (s/R - 1)) - f."""
+    rng = np.random.default_rng(11)
+    for k, R in ((0.5, 128.0), (0.34, 128.0), (0.2, 64.0), (-3.0, 128.0), (20.0, 128.0), (0.5, 2.0)):
+        em = sauvola_em(k, R)
+        for n, f, S1, S2 in windows(rng, 400):
+            omkn, kRn2 = rn((1 - k) / n), rn(k / (R * n * n))
+            V = n * S2 - S1 * S1
+            s = Decimal(V).sqrt() / n
+            m = Decimal(S1) / n
+            tf = m * (1 + Decimal(k) * (s / Decimal(R) - 1)) - f
+            for d in (-E_SQRT, 0.0, E_SQRT):
+                sq = rn(float(np.sqrt(np.float64(v_to_float(V)))) * (1.0 + d))
+                x = rn(float(kRn2) * float(sq) + float(omkn))
+                nd = rn(float(S1) * float(x) - f)
+                assert abs(Decimal(float(nd)) - tf) <= Decimal(em), (k, R, n, f, S1, S2, d)
