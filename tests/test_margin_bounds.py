@@ -12,6 +12,8 @@ on random and extreme windows:
     (the interior margin, half of E_int without the 1e-6);
   - the unclipped-window Sauvola filter nd = RN(S1 RN(omkn + kRn2 sq) - f) must
     stay within the host's Sauvola bound (half of its margin E without the 1e-6);
+  - the per-pixel-n filters of border warps, constants from the table of
+    correctly rounded 1/j and 1/j^2, must stay within the host's general bounds;
   - the refinement D = RN(RN(n f - S1) - RN(RN(k) r)), r = RN(sqrt(RN(V))), must
     have the sign of X = n (f - t) and |X| / n > 1e-9 whenever
     |D| > 4.5 u |k| r + 1.01 n 1e-9.
@@ -125,3 +127,52 @@ def test_interior_sauvola_filter_bound():
                 x = rn(float(kRn2) * float(sq) + float(omkn))
                 nd = rn(float(S1) * float(x) - f)
                 assert abs(Decimal(float(nd)) - tf) <= Decimal(em), (k, R, n, f, S1, S2, d)
+
+
+def niblack_em(k):
+    """Half the fp32 margin E of Niblack before its 1e-6 (the host's general bound)."""
+    m, smax, ak = 255.0, 127.5, abs(k)
+    return 4 * U * m + U * 510 + ak * smax * (7 * U + E_SQRT) + U * (510 + ak * smax)
+
+
+def clipped_windows(rng, count):
+    """(nr, nc, f, S1, S2) of windows clipped at the page border: nr x nc pixels, nr, nc in 1..W."""
+    out = []
+    for i in range(count):
+        W = int(rng.choice([3, 15, 31, 101, 255]))
+        nr, nc = int(rng.integers(1, W + 1)), int(rng.integers(1, W + 1))
+        g = rng.integers(0, 256, nr * nc) if i % 2 else np.clip(
+            rng.normal(rng.integers(0, 256), 4, nr * nc).round(), 0, 255).astype(np.int64)
+        out.append((nr, nc, int(rng.integers(0, 256)), int(g.sum()), int((g.astype(np.int64) ** 2).sum())))
+    return out
+
+
+def test_border_filter_bounds():
+    """The per-pixel-n filters of warps at the page border (constants from the table of correctly rounded
+    1/j and 1/j^2: c0 = RN(RN(a RN(1/nr)) RN(1/nc)), c1 likewise) stay within the host's general bounds."""
+    rng = np.random.default_rng(13)
+    for rule, k, R in (("sauvola", 0.5, 128.0), ("sauvola", -3.0, 128.0), ("sauvola", 0.5, 2.0),
+                       ("niblack", -0.2, 1.0), ("niblack", 0.3, 1.0), ("niblack", -150.0, 1.0)):
+        em = sauvola_em(k, R) if rule == "sauvola" else niblack_em(k)
+        for nr, nc, f, S1, S2 in clipped_windows(rng, 400):
+            n = nr * nc
+            tr = (rn(1.0 / nr), rn(1.0 / (nr * nr)))
+            tc = (rn(1.0 / nc), rn(1.0 / (nc * nc)))
+            V = n * S2 - S1 * S1
+            s = Decimal(V).sqrt() / n
+            m = Decimal(S1) / n
+            if rule == "sauvola":
+                r0, r1 = rn(float(rn(1 - k)) * float(tr[0])), rn(float(rn(k / R)) * float(tr[1]))
+                c0, c1 = rn(float(r0) * float(tc[0])), rn(float(r1) * float(tc[1]))
+                tf = m * (1 + Decimal(k) * (s / Decimal(R) - 1)) - f
+            else:
+                r0, r1 = tr[0], rn(float(rn(k)) * float(tr[0]))
+                c0, c1 = rn(float(r0) * float(tc[0])), rn(float(r1) * float(tc[0]))
+                tf = m + Decimal(k) * s - f
+            for d in (-E_SQRT, 0.0, E_SQRT):
+                q = rn(float(np.sqrt(np.float64(v_to_float(V)))) * (1.0 + d))
+                if rule == "sauvola":
+                    nd = rn(float(S1) * float(rn(float(c1) * float(q) + float(c0))) - f)
+                else:
+                    nd = rn(float(S1) * float(c0) + float(rn(float(c1) * float(q) - f)))
+                assert abs(Decimal(float(nd)) - tf) <= Decimal(em), (rule, k, R, nr, nc, f, S1, S2, d)
