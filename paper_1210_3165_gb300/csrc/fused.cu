@@ -174,17 +174,18 @@ float decision_margin(int rule, double k, double R)
 }
 
 // The unclipped-window filter (n = W*W; constants rounded once on the host,
-// u each) is tighter.  Niblack, nd = RN(S1 RN(1/n) + RN(RN(k/n) sq - f)) with
+// u each) is tighter.  Niblack, nd = RN(x), x = S1 RN(1/n) + RN(RN(k/n) sq - f),
 // sq = sqrt.approx(V to fp32 within 2u) = sqrt(V) (1 + e + 1.01u):
 //   S1 RN(1/n) = m (1 + u)                      -> u m
 //   RN(k/n) sq = k s (1 + e + 2.02u)            -> |k| s (e + 2.02u)
 //   rounding of k s - f                         -> u (1.01 |k| s + 255)
-//   final rounding                              -> u (255 + |k| s + 1)
-// so |nd - (t - f)| <= u (766 + 2.01 |k| s) + |k| s (e + 2.02u), s <= 127.5;
-// E_int = 2 that + 1e-6 + 2 (the fp64 definition's error), never above E.
-// A pixel the fast filter might decide wrongly then has |nd| < E_int, and the
-// lane's re-evaluation with the general filter (margin E) flags it.  Sauvola
-// keeps E (its margin pixels are rare).
+// so |x - (t - f)| <= em = u (510 + 1.01 |k| s) + |k| s (e + 2.02u), s <= 127.5.
+// The last rounding keeps the sign of x and |x| >= |nd| / (1 + u), so
+// |nd| >= E_int = 2 em + 1e-6 + 2 (the fp64 definition's error) gives the sign of
+// t - f and no tie.  A lane with a pixel below E_int is re-evaluated with the
+// general filter (margin E): a pixel it leaves alone has |t - f| > E/2, beyond
+// the interior filter's whole error (em + u (255 + |k| s + 1) <= E/2), so its
+// fast result stands.  Sauvola keeps E (its margin pixels are rare).
 float decision_margin_interior(int rule, double k, double R)
 {
     const float E = decision_margin(rule, k, R);
@@ -193,7 +194,7 @@ float decision_margin_interior(int rule, double k, double R)
     const double u = 1.0 / 16777216.0;
     const double e = kSqrtApproxRelErr;
     const double ks = std::fabs(k) * 127.5;
-    const double em = u * (766.0 + 2.01 * ks) + ks * (e + 2.02 * u);
+    const double em = u * (510.0 + 1.01 * ks) + ks * (e + 2.02 * u);
     const double Ei = 2.0 * em + 1e-6 + 2.0 * fp64_definition_error(rule, k, R);
     return Ei < (double)E ? (float)Ei : E;
 }

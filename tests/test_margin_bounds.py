@@ -176,3 +176,54 @@ def test_border_filter_bounds():
                 else:
                     nd = rn(float(S1) * float(c0) + float(rn(float(c1) * float(q) - f)))
                 assert abs(Decimal(float(nd)) - tf) <= Decimal(em), (rule, k, R, nr, nc, f, S1, S2, d)
+
+
+def fp64_definition_error(k):
+    """The host's bound on the fp64 definition's own error, Niblack (w = 2^-53 per operation)."""
+    return 8.0 * 2.0 ** -53 * (255.0 + abs(k) * 127.5)
+
+
+def interior_niblack_margin(k):
+    """The interior Niblack margin E_int: the fast filter's rounding before its last operation is at most
+    u (510 + 1.01 |k| s) + |k| s (e + 2.02 u), s <= 127.5; the last rounding keeps the sign."""
+    ks = abs(k) * 127.5
+    em = U * (510 + 1.01 * ks) + ks * (E_SQRT + 2.02 * U)
+    return 2 * em + 1e-6 + 2 * fp64_definition_error(k)
+
+
+def near_tie_windows(rng, k, count):
+    """Windows whose Niblack threshold lies within 3e-4 of an integer gray level f (the hard cases)."""
+    out = []
+    for _ in range(20):
+        if len(out) >= count:
+            break
+        W = int(rng.choice([3, 4, 5, 7]))
+        g = rng.integers(0, 256, (20000, W * W)).astype(np.int64)
+        n = W * W
+        S1, S2 = g.sum(1), (g * g).sum(1)
+        t = S1 / n + k * np.sqrt(np.maximum(n * S2 - S1 * S1, 0)) / n
+        f = np.clip(np.round(t), 0, 255)
+        for i in np.nonzero(np.abs(t - f) < 3e-4)[0][: count - len(out)]:
+            out.append((n, int(f[i]), int(S1[i]), int(S2[i])))
+    return out
+
+
+def test_interior_niblack_decision_rule():
+    """Outside E_int the fast filter's sign is the sign of t - f and |t - f| is no tie (> 1e-9): on random
+    windows and on windows whose threshold lies within 3e-4 of the pixel's level."""
+    rng = np.random.default_rng(17)
+    near = 0
+    for k in (-0.2, -0.5, 0.3, -1.5, 150.0):
+        Ei = interior_niblack_margin(k)
+        for n, f, S1, S2 in windows(rng, 300) + near_tie_windows(rng, k, 60):
+            invn, kn = rn(1.0 / n), rn(k / n)
+            tf, s, V = exact_t_minus_f(n, f, S1, S2, k)
+            for d in (-E_SQRT, 0.0, E_SQRT):
+                sq = rn(float(np.sqrt(np.float64(v_to_float(V)))) * (1.0 + d))
+                y = rn(float(kn) * float(sq) - f)
+                nd = rn(float(S1) * float(invn) + float(y))
+                if abs(float(nd)) >= Ei:
+                    assert (float(nd) > 0) == (tf > 0) and abs(tf) > Decimal(1e-9), (k, n, f, S1, S2, d)
+                else:
+                    near += 1
+    assert near > 0
