@@ -89,7 +89,7 @@ def test_niblack_refinement_decides_correctly():
     decided = 0
     for k in (-0.2, -0.5, 0.3, -150.0):
         kf = rn(k)
-        for n, f, S1, S2 in windows(rng, 600):
+        for n, f, S1, S2 in windows(rng, 600) + near_tie_windows(rng, k, 60):
             tf, s, V = exact_t_minus_f(n, f, S1, S2, k)
             X = -tf * n                                   # n (f - t)
             A = rn(n * f - S1)
