@@ -468,6 +468,15 @@ BNZ_API int bnz_version(void);
 BNZ_API int bnz_fused_plan(int height, int width, int channels, int W, const bnz_tile *tile, size_t *smem_bytes,
                    int *grid_ctas, int *tile_w, int *tile_h);
 
+/* The fused kernel's decision margins for (rule, k, R), computed on the host
+ * as for a launch: *E, the fp32 filter's margin for any window; *E_int, the
+ * tighter one of Niblack windows inside the page (E for Sauvola); *Tdf, the
+ * double-float stage's cut.  The paper has no counterpart: this exposes the
+ * fp32 error analysis to tests that check it against exact arithmetic.  Host
+ * only (no device needed).  Returns BNZ_EINVAL for a null pointer, an unknown
+ * rule, or k, R outside the accepted range. */
+BNZ_API int bnz_decision_margins(int rule, double k, double R, float *E, float *E_int, float *Tdf);
+
 /* Device self-test of the hardware square-root approximation the fused
  * kernel's fp32 margin assumes (relative error <= 2^-21): writes to
  * *max_rel_err an upper bound on |sqrt.approx(x) - sqrt(x)| / sqrt(x) over

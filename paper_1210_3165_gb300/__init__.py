@@ -85,10 +85,13 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.bnz_last_error.restype = ctypes.c_char_p
     lib.bnz_last_error.argtypes = []
     lib.bnz_version.argtypes = []
+    lib.bnz_decision_margins.argtypes = [i, d, d, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
+                                         ctypes.POINTER(ctypes.c_float)]
     lib.bnz_fused_plan.argtypes = [i, i, i, i, P, ctypes.POINTER(sz), ctypes.POINTER(i), ctypes.POINTER(i),
                                    ctypes.POINTER(i)]
     for name in ("bnz_sauvola", "bnz_niblack", "bnz_sauvola_dev", "bnz_niblack_dev", "bnz_binarize_dev",
-                 "bnz_dual_dev", "bnz_otsu_dev", "bnz_host_bands", "bnz_version", "bnz_fused_plan"):
+                 "bnz_dual_dev", "bnz_otsu_dev", "bnz_host_bands", "bnz_version", "bnz_fused_plan",
+                 "bnz_decision_margins"):
         getattr(lib, name).restype = ctypes.c_int
     _optional_symbols(lib)
     _lib = lib
@@ -150,6 +153,16 @@ def bnz_last_error() -> str:
 
 def bnz_version() -> int:
     return load().bnz_version()
+
+
+def bnz_decision_margins(rule, k: float, R: float = 128.0) -> tuple:
+    """(E, E_int, Tdf): the fused kernel's decision margins for these parameters (host computation)."""
+    if isinstance(rule, str):
+        rule = {"sauvola": BNZ_SAUVOLA, "niblack": BNZ_NIBLACK}[rule.lower()]
+    E, Ei, T = ctypes.c_float(), ctypes.c_float(), ctypes.c_float()
+    _check(load().bnz_decision_margins(int(rule), float(k), float(R), ctypes.byref(E), ctypes.byref(Ei),
+                                       ctypes.byref(T)))
+    return E.value, Ei.value, T.value
 
 
 def _check(rc: int):

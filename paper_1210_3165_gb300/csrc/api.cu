@@ -872,6 +872,24 @@ int bnz_copy2d_async(void *dst, size_t dst_pitch, const void *src, size_t src_pi
     return e == cudaSuccess ? BNZ_OK : cuda_fail(e, "cudaMemcpy2DAsync");
 }
 
+int bnz_decision_margins(int rule, double k, double R, float *E, float *E_int, float *Tdf)
+{
+    if (!E || !E_int || !Tdf)
+        return fail(BNZ_EINVAL, "null output pointer");
+    if (rule != BNZ_SAUVOLA && rule != BNZ_NIBLACK)
+        return fail(BNZ_EINVAL, "rule must be BNZ_SAUVOLA or BNZ_NIBLACK (got %d)", rule);
+    if (!(std::fabs(k) <= BNZ_MAX_ABS_K))
+        return fail(BNZ_EINVAL, "k must be finite with |k| <= %g (got %g)", BNZ_MAX_ABS_K, k);
+    if (rule == BNZ_SAUVOLA && !(R >= BNZ_MIN_R && std::isfinite(R)))
+        return fail(BNZ_EINVAL, "R must be finite and >= %g for Sauvola (got %g)", BNZ_MIN_R, R);
+    if (rule == BNZ_NIBLACK)
+        R = 1.0;
+    *E = decision_margin(rule, k, R);
+    *E_int = decision_margin_interior(rule, k, R);
+    *Tdf = double_float_cut(rule, k, R);
+    return BNZ_OK;
+}
+
 int bnz_version(void) { return 200; } // 0.2.0: the Otsu scratch grew to BNZ_OTSU_SCRATCH_BYTES = 20480
 
 int bnz_fused_plan(int height, int width, int channels, int W, const bnz_tile *tile, size_t *smem_bytes,

@@ -23,6 +23,9 @@ the Niblack rule); the exact X uses integer arithmetic and a 60-digit root."""
 from decimal import Decimal, getcontext
 
 import numpy as np
+import pytest
+
+import paper_1210_3165_gb300 as bnz
 
 getcontext().prec = 60
 U = 2.0 ** -24
@@ -191,6 +194,27 @@ def interior_niblack_margin(k):
     return 2 * em + 1e-6 + 2 * fp64_definition_error(k)
 
 
+def sauvola_fp64_error(k, R):
+    return 16.0 * 2.0 ** -53 * (255.0 + 255.0 * abs(1 - k) + 255.0 * abs(k) * (127.5 / R + 1.0))
+
+
+@pytest.mark.parametrize("rule,k,R", [("niblack", -0.2, 1.0), ("niblack", 0.3, 1.0), ("niblack", -150.0, 1.0),
+                                      ("niblack", 1e6, 1.0), ("sauvola", 0.5, 128.0), ("sauvola", 20.0, 128.0),
+                                      ("sauvola", 0.5, 1e-3)])
+def test_library_margins_are_these_bounds(rule, k, R):
+    """The margins the library computes for a launch (bnz_decision_margins, host code) are the bounds these
+    tests check: E = 2 em + 1e-6 + 2 (fp64 error) with the general em of each rule, E_int the interior
+    Niblack margin (E for Sauvola), each rounded once to fp32."""
+    E, Ei, _ = bnz.bnz_decision_margins(rule, k, R)
+    if rule == "niblack":
+        want_E = 2 * niblack_em(k) + 1e-6 + 2 * fp64_definition_error(k)
+        want_Ei = min(interior_niblack_margin(k), float(np.float32(want_E)))
+    else:
+        want_E = 2 * sauvola_em(k, R) + 1e-6 + 2 * sauvola_fp64_error(k, R)
+        want_Ei = want_E
+    assert abs(E - want_E) <= 2e-7 * want_E and abs(Ei - want_Ei) <= 2e-7 * want_Ei, (E, want_E, Ei, want_Ei)
+
+
 def near_tie_windows(rng, k, count):
     """Windows whose Niblack threshold lies within 3e-4 of an integer gray level f (the hard cases)."""
     out = []
@@ -214,7 +238,7 @@ def test_interior_niblack_decision_rule():
     rng = np.random.default_rng(17)
     near = 0
     for k in (-0.2, -0.5, 0.3, -1.5, 150.0):
-        Ei = interior_niblack_margin(k)
+        Ei = bnz.bnz_decision_margins("niblack", k)[1]   # the library's margin, as a launch uses it
         for n, f, S1, S2 in windows(rng, 300) + near_tie_windows(rng, k, 60):
             invn, kn = rn(1.0 / n), rn(k / n)
             tf, s, V = exact_t_minus_f(n, f, S1, S2, k)
