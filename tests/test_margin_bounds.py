@@ -14,6 +14,7 @@ on random and extreme windows:
     stay within the host's Sauvola bound (half of its margin E without the 1e-6);
   - the per-pixel-n filters of border warps, constants from the table of
     correctly rounded 1/j and 1/j^2, must stay within the host's general bounds;
+  - the double-float stage's f - t must stay within the host's double_float_error;
   - the refinement D = RN(RN(n f - S1) - RN(RN(k) r)), r = RN(sqrt(RN(V))), must
     have the sign of X = n (f - t) and |X| / n > 1e-9 whenever
     |D| > 4.5 u |k| r + 1.01 n 1e-9.
@@ -251,3 +252,107 @@ def test_interior_niblack_decision_rule():
                 else:
                     near += 1
     assert near > 0
+
+
+# ---- the double-float stage (pairs of fp32 words), emulated operation by operation ----
+
+def add(a, b):
+    return rn(float(a) + float(b))
+
+
+def sub(a, b):
+    return rn(float(a) - float(b))
+
+
+def mul(a, b):
+    return rn(float(a) * float(b))
+
+
+def fma(a, b, c):
+    return rn(float(a) * float(b) + float(c))  # the product of two fp32 is exact in fp64
+
+
+def two_sum(a, b):
+    s = add(a, b)
+    bb = sub(s, a)
+    return s, add(sub(a, sub(s, bb)), sub(b, bb))
+
+
+def fast_two_sum(a, b):
+    s = add(a, b)
+    return s, sub(b, sub(s, a))
+
+
+def df_add(a, b):
+    s = two_sum(a[0], b[0])
+    return fast_two_sum(s[0], add(s[1], add(a[1], b[1])))
+
+
+def df_mul(a, b):
+    p = mul(a[0], b[0])
+    e = fma(a[0], b[0], -p)
+    e = fma(a[0], b[1], fma(a[1], b[0], e))
+    return fast_two_sum(p, e)
+
+
+def df_div_int(x, nf):
+    q = rn(np.float32(x[0]) / np.float32(nf))
+    r = fma(-q, nf, x[0])
+    return fast_two_sum(q, rn(np.float32(add(r, x[1])) / np.float32(nf)))
+
+
+def df_sqrt_v(V):
+    h, lo = V >> 32, V & 0xFFFFFFFF
+    a = two_sum(mul(rn(h), 4294967296.0), mul(rn(lo >> 16), 65536.0))
+    v = fast_two_sum(a[0], add(a[1], rn(lo & 0xFFFF)))
+    if v[0] == 0:
+        return F32(0), F32(0)
+    sh = rn(np.sqrt(np.float32(v[0])))
+    p = mul(sh, sh)
+    pe = fma(sh, sh, -p)
+    r = add(sub(sub(v[0], p), pe), v[1])
+    return fast_two_sum(sh, rn(np.float32(r) / np.float32(mul(2.0, sh))))
+
+
+def split(x):
+    hi = rn(x)
+    return hi, rn(x - float(hi))
+
+
+def double_float_error(rule, k, R):
+    u2, m, s, ak = 2.0 ** -48, 255.0, 127.5, abs(k)
+    if rule == "sauvola":
+        et = 12 * u2 * m * abs(1 - k) + 24 * u2 * m * s * ak / R
+        T = m * abs(1 - k) + m * s * ak / R
+    else:
+        et = 4 * u2 * m + 17 * u2 * ak * s
+        T = m + ak * s
+    return 2 * (et + 3 * u2 * (255 + T))
+
+
+@pytest.mark.parametrize("rule,k,R", [("sauvola", 0.5, 128.0), ("sauvola", 0.34, 128.0), ("sauvola", 20.0, 128.0),
+                                      ("sauvola", 0.5, 0.5), ("niblack", -0.2, 1.0), ("niblack", -150.0, 1.0)])
+def test_double_float_stage_bound(rule, k, R):
+    """The second stage's f - t (double-float: pairs of fp32 with error-free sums and products, correctly
+    rounded division and root) stays within the host's double_float_error of the exact f - t; the
+    library's cut Tdf covers that bound, the fp64 definition's error and the 1e-9 tie width."""
+    rng = np.random.default_rng(23)
+    dfe = double_float_error(rule, k, R)
+    Tdf = bnz.bnz_decision_margins(rule, k, R)[2]
+    assert Tdf >= 1e-9 + dfe
+    kd, c1, c2 = split(k), split(1 - k), split(k / R)
+    for n, f, S1, S2 in windows(rng, 200) + (near_tie_windows(rng, k, 40) if rule == "niblack" else []):
+        V = n * S2 - S1 * S1
+        nf = rn(n)
+        m = df_div_int((rn(S1), F32(0)), nf)
+        sd = df_div_int(df_sqrt_v(V), nf)
+        if rule == "sauvola":
+            t = df_add(df_mul(m, c1), df_mul(df_mul(m, sd), c2))
+            s_ex = Decimal(V).sqrt() / n
+            t_ex = Decimal(S1) / n * (1 + Decimal(k) * (s_ex / Decimal(R) - 1))
+        else:
+            t = df_add(m, df_mul(kd, sd))
+            t_ex = Decimal(S1) / n + Decimal(k) * Decimal(V).sqrt() / n
+        d = df_add((rn(f), F32(0)), (-t[0], -t[1]))
+        dv = Decimal(float(d[0])) + Decimal(float(d[1]))
+        assert abs(dv - (f - t_ex)) <= Decimal(dfe), (rule, k, R, n, f, S1, S2)
