@@ -356,3 +356,20 @@ def test_double_float_stage_bound(rule, k, R):
         d = df_add((rn(f), F32(0)), (-t[0], -t[1]))
         dv = Decimal(float(d[0])) + Decimal(float(d[1]))
         assert abs(dv - (f - t_ex)) <= Decimal(dfe), (rule, k, R, n, f, S1, S2)
+
+
+def test_integer_ranges_of_the_window_sums():
+    """The kernel's integer widths: S1 = sum f < 2^24 for every W <= 255 (exact in fp32 and int32),
+    S2 = sum f^2 < 2^32, n f - S1 within (-2^24, 2^24); the variance numerator V = n S2 - S1^2 <= n^2 255^2 / 4
+    fits 32 bits exactly up to W = 22 (the kernel's 32-bit path) and needs 64 bits from W = 23 on, and
+    stays below 2^48 (the conversion to fp32 from two 32-bit words) for W <= 255."""
+    W = 255
+    n = W * W
+    assert n * 255 < 2 ** 24 and n * 255 * 255 < 2 ** 32
+    vmax = lambda W: (W * W) ** 2 * 255 ** 2 // 4
+    assert vmax(22) < 2 ** 32 <= vmax(23)
+    assert vmax(255) < 2 ** 48
+    # the bound is reached: half the window 0, half 255 (n even) gives V = n^2 255^2 / 4
+    n = 22 * 22
+    S1, S2 = (n // 2) * 255, (n // 2) * 255 * 255
+    assert n * S2 - S1 * S1 == vmax(22)
