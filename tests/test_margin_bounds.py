@@ -14,6 +14,9 @@ on random and extreme windows:
     stay within the host's Sauvola bound (half of its margin E without the 1e-6);
   - the per-pixel-n filters of border warps, constants from the table of
     correctly rounded 1/j and 1/j^2, must stay within the host's general bounds;
+  - the single-pixel filters (whole-set constants, or a per-pixel n through
+    rcp.approx) of the reduced-set kernel and of the margin re-evaluation must
+    stay within the general margins;
   - the double-float stage's f - t must stay within the host's double_float_error;
   - the refinement D = RN(RN(n f - S1) - RN(RN(k) r)), r = RN(sqrt(RN(V))), must
     have the sign of X = n (f - t) and |X| / n > 1e-9 whenever
@@ -373,3 +376,57 @@ def test_integer_ranges_of_the_window_sums():
     n = 22 * 22
     S1, S2 = (n // 2) * 255, (n // 2) * 255 * 255
     assert n * S2 - S1 * S1 == vmax(22)
+
+
+E_RCP = 2.0 ** -22
+
+
+def set_windows(rng, count):
+    """(n, f, S1, S2) over point sets of the reduced-set sizes (2W-1, 4W-3, 4W-4, 6W-9) with random levels."""
+    out = []
+    for i in range(count):
+        W = int(rng.choice([3, 15, 31, 101, 255]))
+        n = int(rng.choice([2 * W - 1, 4 * W - 3, 4 * W - 4, max(6 * W - 9, 1)]))
+        g = rng.integers(0, 256, n) if i % 2 else np.clip(
+            rng.normal(rng.integers(0, 256), 4, n).round(), 0, 255).astype(np.int64)
+        out.append((n, int(rng.integers(0, 256)), int(g.sum()), int((g.astype(np.int64) ** 2).sum())))
+    return out
+
+
+@pytest.mark.parametrize("rule,k,R", [("sauvola", 0.5, 128.0), ("sauvola", -3.0, 128.0), ("sauvola", 0.5, 2.0),
+                                      ("niblack", -0.2, 1.0), ("niblack", 0.3, 1.0), ("niblack", -150.0, 1.0)])
+def test_general_filters_bound(rule, k, R):
+    """The single-pixel filters of the reduced-set kernel and of the margin re-evaluation: d = f - t with the
+    whole-set constants (host-rounded for n) or with a per-pixel n through rcp.approx (worst relative error
+    2^-22 either way), sqrt.approx at its worst error either way, stay within half the library's general
+    margin E less its 1e-6 and the fp64 definition's share."""
+    rng = np.random.default_rng(29)
+    E = bnz.bnz_decision_margins(rule, k, R)[0]
+    fp64e = sauvola_fp64_error(k, R) if rule == "sauvola" else fp64_definition_error(k)
+    em = (E - 1e-6) / 2 - fp64e
+    kf, omk, kR = rn(k), rn(1 - k), rn(k / R)
+    for n, f, S1, S2 in set_windows(rng, 300):
+        V = n * S2 - S1 * S1
+        s_ex = Decimal(V).sqrt() / n
+        m_ex = Decimal(S1) / n
+        if rule == "sauvola":
+            t_ex = m_ex * (1 + Decimal(k) * (s_ex / Decimal(R) - 1))
+        else:
+            t_ex = m_ex + Decimal(k) * s_ex
+        ff, S1f = rn(f), rn(S1)
+        for ds in (-E_SQRT, E_SQRT):
+            sq = rn(float(np.sqrt(np.float64(v_to_float(V)))) * (1.0 + ds))
+            # whole set: constants rounded once on the host
+            if rule == "sauvola":
+                d_whole = fma(-S1f, fma(rn(k / (R * n * n)), sq, rn((1 - k) / n)), ff)
+            else:
+                d_whole = fma(-rn(k / n), sq, fma(-rn(1.0 / n), S1f, ff))
+            ds_ = [d_whole]
+            for dr in (-E_RCP, E_RCP):
+                invn = rn(rn(1.0 / n) * (1.0 + dr))
+                if rule == "sauvola":
+                    ds_.append(fma(-S1f, fma(mul(mul(kR, invn), invn), sq, mul(omk, invn)), ff))
+                else:
+                    ds_.append(fma(-mul(kf, invn), sq, fma(-invn, S1f, ff)))
+            for d in ds_:
+                assert abs(Decimal(float(d)) - (f - t_ex)) <= Decimal(em), (rule, k, R, n, f, S1, S2, ds)
